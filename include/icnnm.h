@@ -1,0 +1,180 @@
+/*
+ * icnnm.h — C ABI of the GB300 (sm_103a) ICNNM library (libicnnm.so).
+ *
+ * ICNNM (Inductive Convolution Nuclear Norm Minimization, arxiv 2604.17001) solves
+ * tensor completion with arbitrary sampling (Definition 1, Sec. I): recover
+ * L0 (H x W x T) from the entries P_Omega(L0) at an arbitrary sampling set Omega.
+ * It solves, for a fixed orthogonal k x k matrix V of pre-learned convolution
+ * eigenvectors (the paper's K),
+ *
+ *     min_L ||A_k(L) V||_{2,1}  s.t. P_Omega(L) = P_Omega(M)          (Eq. InductiveCNNM)
+ *  or min_L ||A_k(L) V||_{2,1} + (lambda k / 2)||P_Omega(L - M)||_F^2  (Eq. admm)
+ *
+ * by ADMM (Sec. III-D), and learns V from reference tensors (Sec. III-C, Eq. A).
+ *
+ * Conventions shared by every call
+ *  - A tensor of dims {H, W, T} is a float array of m = H*W*T entries, w fastest:
+ *    index i = (t*H + h)*W + w. An image (ndim = 2) has T = 1 and kdims[2] = 1.
+ *  - Kernel dims {k1, k2, k3} run along (h, w, t); k = k1*k2*k3; tap index
+ *    s = (st*k1 + sh)*k2 + sw. The convolution is circular in every dimension
+ *    (Sec. II-B), and every dim must be at least the kernel's (H >= k1, ...).
+ *  - V is k*k doubles, column-major: V[i*k + s] is tap s of eigenvector i
+ *    (eigenvector i contiguous), orthonormal to 1e-6.
+ *  - Pointer arguments may be host or device memory of the context's device; the
+ *    library detects which. The caller owns every buffer. Inputs are copied before
+ *    icnnm_solve / icnnm_submit return; outputs are written before the call that
+ *    fills them returns.
+ *  - Calls never abort the process; every failure is a status code, and
+ *    icnnm_last_error() returns a message describing the last failure on the
+ *    calling thread's context.
+ */
+#ifndef ICNNM_H_
+#define ICNNM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct icnnm_ctx icnnm_ctx;
+
+typedef enum {
+  ICNNM_OK = 0,
+  ICNNM_EINVAL = 1,      /* invalid argument: shapes, V, mask, params, non-finite input */
+  ICNNM_ENOMEM = 2,      /* the job's device state exceeds the context's HBM budget */
+  ICNNM_EAGAIN = 3,      /* icnnm_poll: the job is queued or running */
+  ICNNM_ENOTFOUND = 4,   /* unknown job id (or its result was already collected) */
+  ICNNM_ECUDA = 5,       /* a CUDA runtime/driver call or a kernel failed */
+  ICNNM_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  ICNNM_ECANCELED = 7,   /* the job was cancelled */
+  ICNNM_EUNSUPPORTED = 8 /* a valid request this build does not implement */
+} icnnm_status;
+
+typedef enum {
+  ICNNM_FP32 = 0,        /* every product in FP32 on CUDA cores (the plain baseline) */
+  ICNNM_BF16 = 1         /* A_k(.)V and A_k^*(. V^T) on tcgen05 tensor cores: BF16
+                            operands, FP32 accumulation; L, norms and updates in FP32 */
+} icnnm_precision;
+
+typedef struct {
+  int32_t ndim;          /* 2 (image) or 3 (video) */
+  int64_t dims[3];       /* {H, W, T}; T = 1 when ndim == 2 */
+  int64_t kdims[3];      /* {k1, k2, k3}; k3 = 1 when ndim == 2 */
+} icnnm_shape;
+
+typedef struct {
+  double lambda;         /* INFINITY: exact projection P_Omega(L) = P_Omega(M) (Eq.
+                            InductiveCNNM); finite > 0: penalised form (Eq. admm, the
+                            paper uses 1000) */
+  double theta0;         /* initial penalty; <= 0 selects 1/||A_k(P_Omega M) V||_{2,inf} */
+  double rho;            /* penalty growth theta <- min(rho*theta, theta_max), rho >= 1 */
+  double theta_max;
+  int32_t max_iters;     /* iteration cap (>= 1) */
+  double tol;            /* stop when ||Z - A_k(L)V||_F/(sqrt(k)||L||_F) <= tol; 0: run
+                            exactly max_iters iterations */
+  int32_t check_every;   /* residual cadence when tol > 0 (>= 1) */
+  int32_t prec;          /* icnnm_precision */
+} icnnm_params;
+
+typedef struct {
+  int32_t iters;         /* iterations run */
+  double residual;       /* ||Z - A_k(L)V||_F/(sqrt(k)||L||_F) at the last check */
+  double objective;      /* ||A_k(L)V||_{2,1} of the returned L */
+  double theta;          /* final penalty */
+  double seconds;        /* device time of the solve (CUDA events) */
+} icnnm_stats;
+
+/* Fill *p with the defaults: lambda = INFINITY, theta0 = 0 (automatic), rho = 1.1,
+ * theta_max = 1e10, max_iters = 100, tol = 0, check_every = 10, prec = ICNNM_BF16. */
+icnnm_status icnnm_params_default(icnnm_params* p);
+
+/* Create a context on CUDA device `device`. `hbm_budget_bytes` caps the device
+ * memory of job state (0: 90% of the free memory at creation). `cuda_stream` is a
+ * cudaStream_t the context orders its work on (NULL: the context creates its own).
+ * ENOMEM if the budget cannot be reserved, ECUDA on device errors. */
+icnnm_status icnnm_create(icnnm_ctx** out, int device, size_t hbm_budget_bytes,
+                          void* cuda_stream);
+
+/* Wait for running jobs to finish, cancel queued ones, free everything. NULL-safe. */
+void icnnm_destroy(icnnm_ctx* ctx);
+
+/* Static message of a status code. */
+const char* icnnm_strerror(icnnm_status st);
+
+/* Message of the last failure of a call on this context ("" if none). */
+const char* icnnm_last_error(icnnm_ctx* ctx);
+
+/*
+ * Learn V from b reference tensors (Sec. III-C, Definition 3, Eq. A): V's columns
+ * are the eigenvectors of A^T A, A = [A_k(L_1); ...; A_k(L_b)], by decreasing
+ * eigenvalue. A^T A is accumulated on the GPU (FP32 products, FP64 sums) and its
+ * eigendecomposition is computed in FP64 on the GPU. Each column's largest-|.|
+ * entry is made positive (ties: lowest index).
+ *   kdims   : {k1, k2, k3}
+ *   shapes  : b shapes (dims may differ between tensors; kdims in them are ignored)
+ *   tensors : b pointers to float tensors (host or device)
+ *   V_out   : k*k doubles, column-major as above (caller-owned, host or device)
+ *   eig_out : k doubles, the eigenvalues (the ensemble convolution eigenvalues
+ *             sigma_i of Definition 3), or NULL
+ * EINVAL: b < 1, k < 1, k > 1024, a dim smaller than the kernel, non-finite entry.
+ */
+icnnm_status icnnm_learn_V(icnnm_ctx* ctx, const int64_t kdims[3], int32_t b,
+                           const icnnm_shape* shapes, const float* const* tensors,
+                           double* V_out, double* eig_out);
+
+/*
+ * Solve one completion problem and block until done (Sec. III-D).
+ *   shape  : dims and kernel dims
+ *   M      : m floats; only entries with mask = 1 are read
+ *   mask   : m bytes, 1 = observed (in Omega), 0 = missing
+ *   V      : k*k doubles as above
+ *   params : NULL for the defaults
+ *   L_out  : m floats, the completed tensor; with lambda = INFINITY its observed
+ *            entries are bit-identical copies of M
+ *   stats  : may be NULL
+ * EINVAL: bad shape, V not orthonormal to 1e-6, empty Omega, non-finite M at an
+ * observed entry, bad params. ENOMEM: the job's state does not fit the budget.
+ */
+icnnm_status icnnm_solve(icnnm_ctx* ctx, const icnnm_shape* shape, const float* M,
+                         const uint8_t* mask, const double* V, const icnnm_params* params,
+                         float* L_out, icnnm_stats* stats);
+
+/*
+ * Solve n independent problems of any dims that share kernel dims and V, stepping
+ * all of them together (one launch per pass for the whole batch). Arrays hold n
+ * entries each; params (NULL: defaults) apply to every problem.
+ */
+icnnm_status icnnm_solve_batch(icnnm_ctx* ctx, int32_t n, const icnnm_shape* shapes,
+                               const float* const* M, const uint8_t* const* mask,
+                               const double* V, const icnnm_params* params,
+                               float* const* L_out, icnnm_stats* stats);
+
+/*
+ * Serving. icnnm_submit validates and copies the inputs, queues the job and returns
+ * at once with its id. A serving thread admits queued jobs while their device state
+ * fits the HBM budget, keeps admitted jobs resident, and steps all admitted jobs that
+ * share (kdims, V, precision) together, admitting new ones as others finish
+ * (continuous batching). ENOMEM only if the job alone exceeds the whole budget.
+ */
+icnnm_status icnnm_submit(icnnm_ctx* ctx, const icnnm_shape* shape, const float* M,
+                          const uint8_t* mask, const double* V, const icnnm_params* params,
+                          uint64_t* job_id);
+
+/* EAGAIN while queued or running. On completion copies L into L_out (m floats,
+ * may be NULL to drop it), fills stats (may be NULL), forgets the job, returns OK
+ * (or the job's failure status). ENOTFOUND for unknown ids. */
+icnnm_status icnnm_poll(icnnm_ctx* ctx, uint64_t job_id, float* L_out, icnnm_stats* stats);
+
+/* Like icnnm_poll, but waits up to timeout_ms (< 0: forever) for completion. */
+icnnm_status icnnm_wait(icnnm_ctx* ctx, uint64_t job_id, int64_t timeout_ms,
+                        float* L_out, icnnm_stats* stats);
+
+/* Cancel a queued or running job; a later poll returns ECANCELED. */
+icnnm_status icnnm_cancel(icnnm_ctx* ctx, uint64_t job_id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICNNM_H_ */
