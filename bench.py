@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ICNNM library on the video-prediction workload.
+
+Workload (synthetic stand-in for the paper's CDNet 2014 prediction experiment,
+Sec. V-C): one 128x128x32 video (sinusoids + moving blobs), frames 24..31 missing,
+kernel 9x9x5 (k = 405), V learned from 64 reference tensors, 500 ADMM iterations.
+
+A step is one complete solve (all 500 iterations of the forward pass, the shrinkage,
+the adjoint pass and the projection) with V fixed; learning V is timed separately and
+reported under "learn_V". `value` is BF16 solves/s with the inputs resident in HBM;
+"e2e" is the same through the C ABI with host buffers (copies inside the timed
+region); "fp32_plain" is the plain FP32 path, one solve at a time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ICNNM solves/s & p50/p99 latency at ≤1e-3 rel err: served BF16 vs plain FP32"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "prediction_128x128x32_k9x9x5.npz")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+KDIMS = (9, 9, 5)
+ITERS = 500
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learn", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_inputs():
+    from paper_2604_17001_gb300 import synth
+    return synth.workload(2)
+
+
+# -- clocks -----------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -- reference arm: the FP64 oracle on the host cores ---------------------------
+def oracle_iteration_seconds(w, V, n_iter=1):
+    from oracle import icnnm_oracle as O
+    L, Y, th = O.icnnm_init(w["M"], w["mask"], V, w["kdims"])
+    Q = O.conv_matrix_times(L, V, w["kdims"])
+    ts = []
+    for _ in range(n_iter):
+        t0 = time.perf_counter()
+        L, Y, Z, Q = O.icnnm_iteration(L, Y, th, w["M"], w["mask"], V, w["kdims"], np.inf, Q)
+        ts.append(time.perf_counter() - t0)
+        th *= 1.1
+    return ts
+
+
+def load_V(w):
+    if os.path.exists(GOLDEN):
+        g = np.load(GOLDEN)
+        return g["V"], g
+    return None, None
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    w = workload_inputs()
+    V, _ = load_V(w)
+    if V is None:
+        from oracle import icnnm_oracle as O
+        V, _ = O.learn_V(w["refs"][:4], w["kdims"])
+    for _ in range(args.warmup):
+        oracle_iteration_seconds(w, V, 1)
+    ts = [oracle_iteration_seconds(w, V, 1)[0] for _ in range(args.steps)]
+    t_solve = statistics.mean(ts) * args.iters
+    value = 1.0 / t_solve
+    cores = os.cpu_count()
+    sample = f"1 of {args.iters} ADMM iterations of the 128x128x32 k=405 solve per step, scaled to a solve"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "prediction_128x128x32_k9x9x5", "iters": args.iters},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# -- our arm ----------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_tc.cu", "ptx_sm100.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2604_17001_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2604_17001_gb300 import icnnm
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload_inputs()
+    H, W, T = w["dims"]
+    m = H * W * T
+    k = int(np.prod(KDIMS))
+    stream = torch.cuda.current_stream(dev)
+    ctx = icnnm.Context(local, stream=stream.cuda_stream)
+    V, golden = load_V(w)
+    learn = None
+    refs_d = [torch.from_numpy(r).to(dev) for r in w["refs"]]
+    if not args.no_learn or V is None:
+        ctx.icnnm_learn_V(refs_d[:2], KDIMS)                       # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        V_gpu, _ = ctx.icnnm_learn_V(refs_d, KDIMS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        learn = {"seconds": e0.elapsed_time(e1) / 1e3, "refs": len(refs_d), "k": k,
+                 "gram": "autocorrelation lags, FP32 products / FP64 sums", "eig": "FP64 parallel cyclic Jacobi"}
+        if V is None:
+            V = V_gpu
+    Md = torch.from_numpy(w["M"]).to(dev)
+    Kd = torch.from_numpy(w["mask"]).to(dev)
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(dev)
+    Ld = torch.zeros_like(Md)
+
+    def solve(prec, Mx=Md, Kx=Kd, Vx=Vd, Lx=Ld):
+        return ctx.icnnm_solve(Mx, Kx, Vx, KDIMS, L_out=Lx, max_iters=args.iters, prec=prec)
+
+    for _ in range(args.warmup):
+        solve("bf16")
+    torch.cuda.synchronize()
+    ctx.lib.icnnm_profile_enable(ctx.h, 1)
+    clocks = Clocks(local)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        solve("bf16")
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    total_ms = max_over_ranks(total_ms, ws)
+    value = ws * args.steps / (total_ms / 1e3)
+
+    import ctypes as C
+    prof = {}
+    for p, name in ((0, "forward"), (1, "adjoint"), (2, "gather"), (3, "other")):
+        ms, n = C.c_double(), C.c_int64()
+        ctx.lib.icnnm_profile_read(ctx.h, p, C.byref(ms), C.byref(n))
+        prof[name] = (ms.value, n.value)
+    nall = C.c_int64()
+    ctx.lib.icnnm_profile_read(ctx.h, -1, None, C.byref(nall))
+    ctx.lib.icnnm_profile_enable(ctx.h, 0)
+
+    # accuracy against the stored FP64 oracle run (same V, same inputs)
+    L = Ld.cpu().numpy()
+    rel_err = None
+    if golden is not None and int(golden["iters"]) == args.iters:
+        Lo = L.astype(np.float64).copy()
+        Lo[golden["frames"]] = golden["L_missing"]
+        rel_err = float(np.linalg.norm(L - Lo) / np.linalg.norm(Lo))
+
+    # roofline of the dominant pass (algorithmic bytes and flops per launch)
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tfl = peaks.get("bf16_tflops", 1900.0)
+    src = "measured" if peaks else "fallback"
+    dom = max(("forward", "adjoint"), key=lambda n: prof[n][0])
+    ms, n = prof[dom]
+    per_ms = ms / max(n, 1)
+    # forward: U read + U' write (bf16) and 2mk^2 flops; adjoint: U read and 2mk^2 flops
+    alg_bytes = (4 if dom == "forward" else 2) * m * k
+    alg_flops = 2.0 * m * k * k
+    gbs = alg_bytes / (per_ms * 1e-3) / 1e9
+    tfs = alg_flops / (per_ms * 1e-3) / 1e12
+    traffic = None
+    if os.path.exists(TRAFFIC):
+        tj = json.load(open(TRAFFIC))
+        ent = tj.get(dom)
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            traffic = ent.get("bytes_per_launch")
+    if gbs / hbm >= tfs / tfl:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+    else:
+        roof = {"bound": "tensor", "achieved": tfs, "peak": tfl, "unit": "TFLOP/s", "frac": tfs / tfl}
+    roof.update({"traffic": traffic, "kernel": dom, "peak_source": src, "ms_per_launch": per_ms,
+                 "hbm_gbs_alg": gbs, "tensor_tflops_alg": tfs,
+                 "share_of_step": {k_: prof[k_][0] / sum(v[0] for v in prof.values()) for k_ in prof}})
+
+    # end to end through the C ABI with host buffers
+    Mh, Kh, Vh = w["M"], w["mask"], np.ascontiguousarray(V)
+    Lh = np.zeros_like(Mh)
+    ctx.icnnm_solve(Mh, Kh, Vh, KDIMS, L_out=Lh, max_iters=args.iters, prec="bf16")
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.icnnm_solve(Mh, Kh, Vh, KDIMS, L_out=Lh, max_iters=args.iters, prec="bf16")
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": ws * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": m * 4 + m + k * k * 8,
+           "d2h_bytes_per_step": m * 4}
+
+    # plain FP32, one solve at a time
+    fp32 = None
+    if args.fp32_steps > 0:
+        solve("fp32")
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp32_steps):
+            solve("fp32")
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / args.fp32_steps
+        Lf = Ld.cpu().numpy()
+        fe = None
+        if golden is not None and int(golden["iters"]) == args.iters:
+            fe = float(np.linalg.norm(Lf - Lo) / np.linalg.norm(Lo))
+        fp32 = {"value": 1e3 / fms, "unit": "solves/s", "ms_per_solve": fms, "steps": args.fp32_steps,
+                "rel_err_vs_oracle": fe}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ts = oracle_iteration_seconds(w, V, 1)
+        cpu = {"value": 1.0 / (ts[0] * args.iters), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"1 of {args.iters} ADMM iterations (FP64 numpy, explicit A_k rows) of the same solve, "
+                         f"scaled to a solve; init not counted"}
+
+    ctx.close()
+    if rank != 0:
+        return
+    lat_sorted = sorted(lat)
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "prediction_128x128x32_k9x9x5", "dims_HWT": [H, W, T], "kdims": list(KDIMS),
+                   "iters": args.iters, "mask": "frames 24..31 missing", "V": "64 reference tensors",
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (U alone is 0.44 GB per solve)"},
+        "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99)),
+                       "mean": float(np.mean(lat_sorted))},
+        "rel_err_vs_oracle": rel_err,
+        "fp32_plain": fp32,
+        "e2e": e2e,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": int(nall.value),
+        "learn_V": learn,
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

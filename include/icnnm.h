@@ -174,6 +174,20 @@ icnnm_status icnnm_wait(icnnm_ctx* ctx, uint64_t job_id, int64_t timeout_ms,
 /* Cancel a queued or running job; a later poll returns ECANCELED. */
 icnnm_status icnnm_cancel(icnnm_ctx* ctx, uint64_t job_id);
 
+/*
+ * Diagnostics (no counterpart in the paper). While profiling is enabled the library
+ * brackets each pass of the blocking solves with CUDA events on the context's stream
+ * and counts every kernel it launches.
+ *   icnnm_profile_enable : enable (1) or disable (0); either resets the counters.
+ *   icnnm_profile_read   : pass 0 = forward pass A_k(X)V fused with the U update,
+ *                          1 = adjoint pass (V D)U^T with col2im, 2 = gather/projection
+ *                          (L-update), 3 = everything else; ms_total = summed device
+ *                          time, launches = kernels of that pass (pass -1: all kernels,
+ *                          ms_total = 0). EINVAL for other pass ids.
+ */
+icnnm_status icnnm_profile_enable(icnnm_ctx* ctx, int32_t enable);
+icnnm_status icnnm_profile_read(icnnm_ctx* ctx, int32_t pass, double* ms_total, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,21 @@ __all__ = [
 ]
 
 CHUNK_ROWS = 8192
+_IDX_CACHE: dict = {}
+_IDX_CACHE_MAX_BYTES = 4 << 30
+
+
+def _chunk_index(dims_thw, kdims, r0, r1):
+    """conv_index for rows [r0, r1), memoised (int32) so that repeated products with
+    the same tensor shape do not recompute the index arithmetic."""
+    key = (tuple(dims_thw), tuple(kdims), r0, r1)
+    idx = _IDX_CACHE.get(key)
+    if idx is None:
+        idx = conv_index(dims_thw, kdims, np.arange(r0, r1))
+        if idx.size * 4 + sum(v.nbytes for v in _IDX_CACHE.values()) <= _IDX_CACHE_MAX_BYTES:
+            idx = idx.astype(np.int32)
+            _IDX_CACHE[key] = idx
+    return idx
 
 
 # ----------------------------------------------------------------------------------
@@ -88,8 +103,8 @@ def conv_matrix_times(L: np.ndarray, V: np.ndarray, kdims) -> np.ndarray:
     out = np.empty((m, V.shape[1]), dtype=np.float64)
     Lf = np.asarray(L, dtype=np.float64).ravel()
     for r0 in range(0, m, CHUNK_ROWS):
-        rows = np.arange(r0, min(m, r0 + CHUNK_ROWS))
-        out[rows] = Lf[conv_index((T, H, W), kdims, rows)] @ V
+        r1 = min(m, r0 + CHUNK_ROWS)
+        out[r0:r1] = Lf[_chunk_index((T, H, W), kdims, r0, r1)] @ V
     return out
 
 
@@ -119,9 +134,9 @@ def adjoint_of_product(Wm: np.ndarray, V: np.ndarray, dims_thw, kdims) -> np.nda
     out = np.zeros(m, dtype=np.float64)
     Vt = np.asarray(V, dtype=np.float64).T
     for r0 in range(0, m, CHUNK_ROWS):
-        rows = np.arange(r0, min(m, r0 + CHUNK_ROWS))
-        idx = conv_index(dims_thw, kdims, rows)
-        out += np.bincount(idx.ravel(), weights=(Wm[rows] @ Vt).ravel(), minlength=m)
+        r1 = min(m, r0 + CHUNK_ROWS)
+        idx = _chunk_index(dims_thw, kdims, r0, r1)
+        out += np.bincount(idx.ravel(), weights=(Wm[r0:r1] @ Vt).ravel(), minlength=m)
     return out.reshape(T, H, W)
 
 
@@ -157,8 +172,7 @@ def gram(refs, kdims) -> np.ndarray:
         m = T * H * W
         Lf = np.asarray(Lj, dtype=np.float64).ravel()
         for r0 in range(0, m, CHUNK_ROWS):
-            rows = np.arange(r0, min(m, r0 + CHUNK_ROWS))
-            A = Lf[conv_index((T, H, W), kdims, rows)]
+            A = Lf[_chunk_index((T, H, W), kdims, r0, min(m, r0 + CHUNK_ROWS))]
             Gm += A.T @ A
     return Gm
 

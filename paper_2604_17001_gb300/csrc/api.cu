@@ -1,0 +1,984 @@
+// C ABI of libicnnm (include/icnnm.h): contexts, validation, the job engine that steps
+// any set of completion jobs sharing (kernel dims, V, precision) together, learn_V,
+// the blocking solves, and the continuous-batching serving thread.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/icnnm.h"
+#include "icnnm_internal.h"
+#include "tc_api.h"
+
+using namespace icnnm;
+
+namespace {
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(x)                                      \
+  do {                                             \
+    cudaError_t e__ = (x);                         \
+    if (e__ != cudaSuccess) throw CudaFail{e__, #x}; \
+  } while (0)
+
+struct StatusFail {
+  icnnm_status st;
+  std::string msg;
+};
+
+[[noreturn]] void fail(icnnm_status st, const std::string& msg) { throw StatusFail{st, msg}; }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------------
+// Shared per-V device data
+// ---------------------------------------------------------------------------------
+struct VData {
+  int k1, k2, k3, k, kc;
+  std::vector<double> V64;   // column-major k x k
+  float* dVf = nullptr;      // [k][kc]
+  TcVData tc;                // BF16 images (tc_api.h)
+  bool tc_ready = false;
+};
+
+// ---------------------------------------------------------------------------------
+// Jobs
+// ---------------------------------------------------------------------------------
+enum Phase { QUEUED = 0, ADMITTED, RUNNING, DONE, FAILED, CANCELED };
+
+struct Job {
+  uint64_t id = 0;
+  int H = 0, W = 0, T = 0;
+  long long m = 0;
+  icnnm_params p{};
+  VData* vd = nullptr;
+  std::vector<float> hM;        // host copies (serving) of the inputs
+  std::vector<uint8_t> hmask;
+  const float* srcM = nullptr;  // caller's buffers (blocking solves)
+  const uint8_t* srcmask = nullptr;
+  bool src_dev = false;
+  void* block = nullptr;        // one device allocation for all of the job's state
+  size_t bytes = 0;
+  JobDev dev{};
+  Phase phase = QUEUED;
+  icnnm_status st = ICNNM_OK;
+  std::string err;
+  int iters = 0;
+  bool converged = false;
+  double resid = NAN;
+  icnnm_stats stats{};
+  std::vector<float> result;    // serving: copied-out L
+  std::chrono::steady_clock::time_point t_admit;
+  std::atomic<bool> cancel{false};
+};
+
+size_t job_bytes(int H, int W, int T, int k, int kc, int prec, int nrp, const TcGeom* tg) {
+  const long long m = (long long)H * W * T;
+  const int ntiles = ((H + TH - 1) / TH) * ((W + TW - 1) / TW) * T;
+  size_t b = 0;
+  auto add = [&](size_t n) { b += (n + 255) / 256 * 256; };
+  add(sizeof(JobScal));
+  add(m * 4);            // M
+  add(m);                // mask
+  add(m * 4);            // L
+  add(m * 4);            // X
+  add((size_t)ntiles * kc * 4);   // part
+  add((size_t)ntiles * nrp * 4);  // rpart
+  add((size_t)ntiles * 4);        // lpart
+  add((size_t)NSEG * kc * 8);     // colseg
+  add(kc * 4);           // s
+  add(kc * 4);           // D
+  if (prec == ICNNM_FP32) {
+    add(m * kc * 4);     // U
+    add((size_t)k * m * 4);  // G^T
+  } else {
+    add(m * kc * 2);     // U (bf16)
+    b += tc_job_extra_bytes(H, W, T, *tg);
+  }
+  return b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------
+struct icnnm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  size_t used = 0;
+  std::recursive_mutex mu;         // serialises device work of API calls and the server
+  std::mutex err_mu;
+  std::string last_err;
+  std::map<std::string, std::unique_ptr<VData>> vcache;
+  // serving
+  std::mutex qmu;
+  std::condition_variable qcv;
+  std::deque<std::shared_ptr<Job>> queue;            // submitted, not admitted
+  std::map<uint64_t, std::shared_ptr<Job>> jobs;     // all known (until collected)
+  std::vector<std::shared_ptr<Job>> active;          // admitted (server thread only)
+  std::thread server;
+  bool stop = false;
+  uint64_t next_id = 1;
+  // diagnostics
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  std::vector<std::pair<int, size_t>> pending;   // (pass, index of the start event)
+  double pass_ms[4] = {0, 0, 0, 0};
+  long long pass_n[5] = {0, 0, 0, 0, 0};
+  // engine scratch
+  JobDev* dlist = nullptr;
+  int* dtile0 = nullptr;
+  int list_cap = 0;
+};
+
+namespace {
+
+void set_err(icnnm_ctx* c, const std::string& s) {
+  std::lock_guard<std::mutex> g(c->err_mu);
+  c->last_err = s;
+}
+
+// Diagnostics: bracket a pass with events when profiling, and count launches.
+cudaEvent_t pool_event(icnnm_ctx* c) {
+  if (c->evnext == c->evpool.size()) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->evpool.push_back(e);
+  }
+  return c->evpool[c->evnext++];
+}
+
+struct PassScope {
+  icnnm_ctx* c;
+  int pass;
+  size_t idx = 0;
+  PassScope(icnnm_ctx* c_, int pass_, int nkernels) : c(c_), pass(pass_) {
+    c->pass_n[pass] += nkernels;
+    c->pass_n[4] += nkernels;
+    if (c->prof) {
+      idx = c->evnext;
+      CK(cudaEventRecord(pool_event(c), c->stream));
+    }
+  }
+  ~PassScope() noexcept(false) {
+    if (c->prof) {
+      CK(cudaEventRecord(pool_event(c), c->stream));
+      c->pending.emplace_back(pass, idx);
+    }
+  }
+};
+
+// After a stream synchronisation: fold the recorded pass times into the totals.
+void flush_prof(icnnm_ctx* c) {
+  for (auto& pr : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->evpool[pr.second], c->evpool[pr.second + 1]) == cudaSuccess)
+      c->pass_ms[pr.first] += ms;
+  }
+  c->pending.clear();
+  c->evnext = 0;
+}
+
+icnnm_status report(icnnm_ctx* c, const StatusFail& f) {
+  set_err(c, f.msg);
+  return f.st;
+}
+icnnm_status report(icnnm_ctx* c, const CudaFail& f) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %d (%s) at %s", (int)f.e, cudaGetErrorString(f.e), f.what);
+  set_err(c, buf);
+  return ICNNM_ECUDA;
+}
+
+// Validation ------------------------------------------------------------------------
+void validate_shape(const icnnm_shape* s, int& H, int& W, int& T, int& k1, int& k2, int& k3) {
+  if (!s) fail(ICNNM_EINVAL, "shape is NULL");
+  if (s->ndim != 2 && s->ndim != 3) fail(ICNNM_EINVAL, "ndim must be 2 or 3");
+  H = (int)s->dims[0]; W = (int)s->dims[1]; T = s->ndim == 3 ? (int)s->dims[2] : 1;
+  k1 = (int)s->kdims[0]; k2 = (int)s->kdims[1]; k3 = s->ndim == 3 ? (int)s->kdims[2] : 1;
+  if (s->ndim == 2 && ((s->dims[2] != 1 && s->dims[2] != 0) || (s->kdims[2] != 1 && s->kdims[2] != 0)))
+    fail(ICNNM_EINVAL, "an image (ndim 2) has T = 1 and k3 = 1");
+  if (H < 1 || W < 1 || T < 1 || k1 < 1 || k2 < 1 || k3 < 1) fail(ICNNM_EINVAL, "dims and kdims must be >= 1");
+  if (s->dims[0] > (1 << 20) || s->dims[1] > (1 << 20) || s->dims[2] > (1 << 20))
+    fail(ICNNM_EINVAL, "dims too large");
+  if (H < k1 || W < k2 || T < k3) fail(ICNNM_EINVAL, "every dim must be at least the kernel's (Sec. II-B)");
+  if ((long long)k1 * k2 * k3 > 1024) fail(ICNNM_EINVAL, "k = k1*k2*k3 must be <= 1024");
+}
+
+void validate_params(const icnnm_params& p) {
+  if (!(p.lambda > 0)) fail(ICNNM_EINVAL, "lambda must be > 0 (INFINITY for the exact projection)");
+  if (!(p.rho >= 1.0) || !isfinite(p.rho)) fail(ICNNM_EINVAL, "rho must be finite and >= 1");
+  if (!(p.theta_max > 0)) fail(ICNNM_EINVAL, "theta_max must be > 0");
+  if (p.max_iters < 1) fail(ICNNM_EINVAL, "max_iters must be >= 1");
+  if (!(p.tol >= 0) || !isfinite(p.tol)) fail(ICNNM_EINVAL, "tol must be finite and >= 0");
+  if (p.check_every < 1) fail(ICNNM_EINVAL, "check_every must be >= 1");
+  if (p.prec != ICNNM_FP32 && p.prec != ICNNM_BF16) fail(ICNNM_EINVAL, "unknown precision");
+  if (!isfinite(p.theta0) && p.theta0 > 0) fail(ICNNM_EINVAL, "theta0 must be finite");
+}
+
+std::string v_key(const double* V, int k1, int k2, int k3) {
+  // FNV-1a over the bytes of V plus the kernel dims.
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(V);
+  const size_t n = sizeof(double) * (size_t)k1 * k2 * k3 * k1 * k2 * k3;
+  for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+  char buf[96];
+  snprintf(buf, sizeof buf, "%d_%d_%d_%016llx", k1, k2, k3, (unsigned long long)h);
+  return buf;
+}
+
+VData* get_vdata(icnnm_ctx* c, const double* V, int k1, int k2, int k3, int prec) {
+  if (!V) fail(ICNNM_EINVAL, "V is NULL");
+  const int k = k1 * k2 * k3;
+  std::vector<double> hv((size_t)k * k);
+  if (is_device_ptr(V)) CK(cudaMemcpy(hv.data(), V, hv.size() * 8, cudaMemcpyDeviceToHost));
+  else memcpy(hv.data(), V, hv.size() * 8);
+  const std::string key = v_key(hv.data(), k1, k2, k3);
+  auto it = c->vcache.find(key);
+  VData* vd;
+  if (it == c->vcache.end()) {
+    for (double x : hv)
+      if (!isfinite(x)) fail(ICNNM_EINVAL, "V has a non-finite entry");
+    // orthonormality: max |V^T V - I| <= 1e-6
+    double worst = 0.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = i; j < k; ++j) {
+        double d = 0.0;
+        const double* a = hv.data() + (size_t)i * k;
+        const double* b = hv.data() + (size_t)j * k;
+        for (int s = 0; s < k; ++s) d += a[s] * b[s];
+        worst = std::max(worst, fabs(d - (i == j ? 1.0 : 0.0)));
+      }
+    if (worst > 1e-6) fail(ICNNM_EINVAL, "V is not orthonormal to 1e-6");
+    auto nv = std::make_unique<VData>();
+    nv->k1 = k1; nv->k2 = k2; nv->k3 = k3; nv->k = k; nv->kc = round_up(k, 16);
+    nv->V64 = std::move(hv);
+    std::vector<float> vf((size_t)k * nv->kc, 0.f);
+    for (int s = 0; s < k; ++s)
+      for (int ch = 0; ch < k; ++ch) vf[(size_t)s * nv->kc + ch] = (float)nv->V64[(size_t)ch * k + s];
+    CK(cudaMalloc(&nv->dVf, vf.size() * 4));
+    CK(cudaMemcpy(nv->dVf, vf.data(), vf.size() * 4, cudaMemcpyHostToDevice));
+    vd = nv.get();
+    c->vcache[key] = std::move(nv);
+  } else {
+    vd = it->second.get();
+  }
+  return vd;
+}
+
+void ensure_tc(VData* vd, int prec) {
+  const int k1 = vd->k1, k2 = vd->k2, k3 = vd->k3;
+  if (prec == ICNNM_BF16 && !vd->tc_ready) {
+    std::string why;
+    if (!tc_supported(k1, k2, k3, &why)) fail(ICNNM_EUNSUPPORTED, "BF16 path: " + why);
+    CK(tc_build_vdata(vd->V64.data(), k1, k2, k3, vd->kc, &vd->tc));
+    vd->tc_ready = true;
+  }
+}
+
+// Engine ---------------------------------------------------------------------------
+void alloc_job(icnnm_ctx* c, Job& j) {
+  VData* vd = j.vd;
+  const int k = vd->k, kc = vd->kc;
+  const int nrp = std::max(fwd_fp32_nrp(k), tc_nrp(k));
+  j.bytes = job_bytes(j.H, j.W, j.T, k, kc, j.p.prec, nrp, &vd->tc.g);
+  if (c->used + j.bytes > c->budget) fail(ICNNM_ENOMEM, "job state exceeds the HBM budget");
+  CK(cudaMalloc(&j.block, j.bytes));
+  c->used += j.bytes;
+  char* b = static_cast<char*>(j.block);
+  size_t off = 0;
+  auto take = [&](size_t n) { void* p = b + off; off += (n + 255) / 256 * 256; return p; };
+  const long long m = j.m;
+  JobDev& d = j.dev;
+  d = JobDev{};
+  d.H = j.H; d.W = j.W; d.T = j.T;
+  d.nth = (j.H + TH - 1) / TH; d.ntw = (j.W + TW - 1) / TW;
+  d.ntiles = d.nth * d.ntw * j.T;
+  d.m = m;
+  d.lam = j.p.lambda; d.rho = j.p.rho; d.theta_max = j.p.theta_max;
+  d.sc = (JobScal*)take(sizeof(JobScal));
+  d.M = (const float*)take(m * 4);
+  d.mask = (const uint8_t*)take(m);
+  d.L = (float*)take(m * 4);
+  d.X = (float*)take(m * 4);
+  d.part = (float*)take((size_t)d.ntiles * kc * 4);
+  d.rpart = (float*)take((size_t)d.ntiles * nrp * 4);
+  d.lpart = (float*)take((size_t)d.ntiles * 4);
+  d.colseg = (double*)take((size_t)NSEG * kc * 8);
+  d.s = (float*)take(kc * 4);
+  d.D = (float*)take(kc * 4);
+  if (j.p.prec == ICNNM_FP32) {
+    d.U = take(m * kc * 4);
+    d.G = (float*)take((size_t)k * m * 4);
+  } else {
+    d.U = take(m * kc * 2);
+    CK(tc_carve_job(&d, vd->tc, b, off, j.bytes));
+  }
+  CK(cudaMemsetAsync(d.sc, 0, sizeof(JobScal), c->stream));
+  CK(cudaMemsetAsync(d.U, 0, (size_t)m * kc * (j.p.prec == ICNNM_FP32 ? 4 : 2), c->stream));
+  CK(cudaMemsetAsync(d.part, 0, (size_t)d.ntiles * kc * 4, c->stream));
+  CK(cudaMemsetAsync(d.rpart, 0, (size_t)d.ntiles * nrp * 4, c->stream));
+  // inputs
+  const float* srcM = j.srcM ? j.srcM : j.hM.data();
+  const uint8_t* srcK = j.srcmask ? j.srcmask : j.hmask.data();
+  CK(cudaMemcpyAsync((void*)d.M, srcM, m * 4, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync((void*)d.mask, srcK, m, cudaMemcpyDefault, c->stream));
+}
+
+void free_job(icnnm_ctx* c, Job& j) {
+  if (j.block) {
+    cudaFree(j.block);
+    c->used -= j.bytes;
+    j.block = nullptr;
+  }
+}
+
+struct List {
+  Shared sh{};
+};
+
+// Upload a launch list of jobs (all sharing vd and precision) and fill the Shared view.
+Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js) {
+  const int n = (int)js.size();
+  if (n > c->list_cap) {
+    if (c->dlist) cudaFree(c->dlist);
+    if (c->dtile0) cudaFree(c->dtile0);
+    c->list_cap = std::max(n, 64);
+    CK(cudaMalloc(&c->dlist, sizeof(JobDev) * c->list_cap));
+    CK(cudaMalloc(&c->dtile0, sizeof(int) * (c->list_cap + 1)));
+  }
+  std::vector<JobDev> hd(n);
+  std::vector<int> t0(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    hd[i] = js[i]->dev;
+    t0[i + 1] = t0[i] + js[i]->dev.ntiles;
+  }
+  CK(cudaMemcpyAsync(c->dlist, hd.data(), sizeof(JobDev) * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->dtile0, t0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+  // pageable sources: make sure the copies have consumed them before they go away
+  CK(cudaStreamSynchronize(c->stream));
+  const VData* vd = js[0]->vd;
+  Shared sh{};
+  sh.k1 = vd->k1; sh.k2 = vd->k2; sh.k3 = vd->k3; sh.k = vd->k; sh.kc = vd->kc;
+  sh.nrp = js[0]->p.prec == ICNNM_FP32 ? fwd_fp32_nrp(vd->k) : tc_nrp(vd->k);
+  sh.Vf = vd->dVf;
+  sh.VtImg = vd->tc_ready ? vd->tc.VtImg : nullptr;
+  sh.njobs = n;
+  sh.jobs = c->dlist;
+  sh.job_tile0 = c->dtile0;
+  sh.total_tiles = t0[n];
+  return sh;
+}
+
+void run_fwd(icnnm_ctx* c, const Shared& sh, int prec, int mode, const TcVData* tcv) {
+  PassScope ps(c, 0, 1);
+  if (prec == ICNNM_FP32 || mode == 0 || mode == 4) CK(launch_fwd_fp32(sh, mode, c->stream));
+  else CK(tc_launch_fwd(sh, *tcv, mode, c->stream));
+}
+
+#define OTHER(n, expr)            \
+  do {                            \
+    PassScope ps__(c, 3, (n));    \
+    CK(expr);                     \
+  } while (0)
+
+// Initial state: L = P_Omega M, theta0, U0 = -theta0 A_k(L)V and its column norms.
+// theta0's column norms always come from the FP32 forward pass.
+void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
+  const int prec = js[0]->p.prec;
+  const TcVData* tcv = &js[0]->vd->tc;
+  Shared sh = upload_list(c, js);
+  OTHER(1, launch_init_L(sh, c->stream));
+  run_fwd(c, sh, ICNNM_FP32, 0, tcv);
+  OTHER(1, launch_reduce_cols(sh, 0, c->stream));
+  OTHER(1, launch_theta0(sh, js[0]->p.theta0, c->stream));
+  OTHER(1, launch_scale_X(sh, c->stream));
+  if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
+  run_fwd(c, sh, prec, 2, tcv);
+  OTHER(1, launch_reduce_cols(sh, 0, c->stream));
+}
+
+// One ADMM iteration for every job of the list. `check` (per list) adds the residual.
+void engine_step(icnnm_ctx* c, const Shared& sh, int prec, const TcVData* tcv, bool check) {
+  OTHER(1, launch_scalars(sh, c->stream));
+  {
+    PassScope ps(c, 1, prec == ICNNM_FP32 ? 1 : 2);
+    if (prec == ICNNM_FP32) CK(launch_adj_gemm_fp32(sh, c->stream));
+    else CK(tc_launch_adj(sh, *tcv, c->stream));
+  }
+  {
+    PassScope ps(c, 2, 1);
+    if (prec == ICNNM_FP32) CK(launch_gather_fp32(sh, c->stream));
+    else CK(tc_launch_gather(sh, *tcv, c->stream));
+  }
+  if (check) {
+    if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/1, c->stream));
+    run_fwd(c, sh, prec, 3, tcv);
+    OTHER(1, launch_finish(sh, 1, c->stream));
+  }
+  if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
+  run_fwd(c, sh, prec, 1, tcv);
+  OTHER(1, launch_reduce_cols(sh, 1, c->stream));
+}
+
+void engine_objective(icnnm_ctx* c, const Shared& sh) {
+  run_fwd(c, sh, ICNNM_FP32, 4, nullptr);
+  OTHER(1, launch_reduce_cols(sh, 0, c->stream));
+  OTHER(1, launch_finish(sh, 2, c->stream));
+}
+
+JobScal read_scal(Job& j, cudaStream_t st) {
+  JobScal s;
+  CK(cudaMemcpyAsync(&s, j.dev.sc, sizeof s, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+double resid_of(const JobScal& s, int k) {
+  return sqrt(s.rsq) / (sqrt((double)k) * std::max(sqrt(s.lsq), 1e-300));
+}
+
+// Run a fixed set of jobs to completion (blocking solves).
+void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
+  const int prec = js[0]->p.prec;
+  const TcVData* tcv = &js[0]->vd->tc;
+  const int k = js[0]->vd->k;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, c->stream));
+  engine_init(c, js);
+  std::vector<Job*> live = js;
+  Shared sh = upload_list(c, live);
+  int it = 0;
+  const icnnm_params& p = js[0]->p;
+  while (!live.empty()) {
+    ++it;
+    const bool last = it >= p.max_iters;
+    const bool check = last || (p.tol > 0 && it % p.check_every == 0);
+    engine_step(c, sh, prec, tcv, check);
+    if (check) {
+      std::vector<Job*> keep;
+      for (Job* j : live) {
+        JobScal s = read_scal(*j, c->stream);
+        j->resid = resid_of(s, k);
+        j->iters = it;
+        const bool conv = p.tol > 0 && j->resid <= p.tol && it % p.check_every == 0;
+        if (conv || last) j->converged = conv;
+        else keep.push_back(j);
+      }
+      if (keep.size() != live.size()) {
+        live = keep;
+        if (!live.empty()) sh = upload_list(c, live);
+      }
+    }
+  }
+  Shared all = upload_list(c, js);
+  engine_objective(c, all);
+  CK(cudaEventRecord(e1, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  flush_prof(c);
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t i = 0; i < js.size(); ++i) {
+    Job& j = *js[i];
+    JobScal s = read_scal(j, c->stream);
+    if (s.status) fail(ICNNM_ETIMEOUT, "a bounded device-side wait expired");
+    j.stats.iters = j.iters;
+    j.stats.residual = j.resid;
+    j.stats.objective = s.objective;
+    j.stats.theta = s.theta;
+    j.stats.seconds = ms * 1e-3;
+    if (outs && outs[i]) CK(cudaMemcpyAsync(outs[i], j.dev.L, j.m * 4, cudaMemcpyDefault, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+}
+
+void prepare_job(icnnm_ctx* c, Job& j, const icnnm_shape* shape, const float* M, const uint8_t* mask,
+                 const double* V, const icnnm_params& p, bool copy_host) {
+  int H, W, T, k1, k2, k3;
+  validate_shape(shape, H, W, T, k1, k2, k3);
+  validate_params(p);
+  if (!M || !mask) fail(ICNNM_EINVAL, "M and mask must not be NULL");
+  j.H = H; j.W = W; j.T = T; j.m = (long long)H * W * T;
+  j.p = p;
+  j.vd = get_vdata(c, V, k1, k2, k3, p.prec);
+  // observed-entry checks on the device (inputs may be host or device)
+  const bool mdev = is_device_ptr(M), kdev = is_device_ptr(mask);
+  const float* dM = M;
+  const uint8_t* dK = mask;
+  float* tM = nullptr;
+  uint8_t* tK = nullptr;
+  if (!mdev) { CK(cudaMalloc(&tM, j.m * 4)); CK(cudaMemcpy(tM, M, j.m * 4, cudaMemcpyHostToDevice)); dM = tM; }
+  if (!kdev) { CK(cudaMalloc(&tK, j.m)); CK(cudaMemcpy(tK, mask, j.m, cudaMemcpyHostToDevice)); dK = tK; }
+  int* d2;
+  CK(cudaMalloc(&d2, 8));
+  CK(cudaMemset(d2, 0, 8));
+  CK(check_observed(dM, dK, j.m, d2, c->stream));
+  int h2[2];
+  CK(cudaMemcpyAsync(h2, d2, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  cudaFree(d2);
+  if (tM) cudaFree(tM);
+  if (tK) cudaFree(tK);
+  if (h2[1]) fail(ICNNM_EINVAL, "mask entries must be 0/1 and M must be finite on Omega");
+  if (h2[0] == 0) fail(ICNNM_EINVAL, "Omega is empty");
+  ensure_tc(j.vd, p.prec);
+  if (copy_host) {
+    j.hM.resize(j.m);
+    j.hmask.resize(j.m);
+    CK(cudaMemcpy(j.hM.data(), M, j.m * 4, cudaMemcpyDefault));
+    CK(cudaMemcpy(j.hmask.data(), mask, j.m, cudaMemcpyDefault));
+  } else {
+    j.srcM = M;
+    j.srcmask = mask;
+  }
+}
+
+icnnm_params defaults() {
+  icnnm_params p;
+  icnnm_params_default(&p);
+  return p;
+}
+
+// Serving thread ---------------------------------------------------------------------
+void server_loop(icnnm_ctx* c) {
+  CK(cudaSetDevice(c->device));
+  while (true) {
+    std::vector<std::shared_ptr<Job>> admitted;
+    {
+      std::unique_lock<std::mutex> lk(c->qmu);
+      c->qcv.wait(lk, [&] { return c->stop || !c->queue.empty() || !c->active.empty(); });
+      if (c->stop && c->queue.empty() && c->active.empty()) return;
+      // admit in FIFO order while the state fits the budget and the group matches
+      while (!c->queue.empty()) {
+        auto j = c->queue.front();
+        if (j->cancel) { j->phase = CANCELED; j->st = ICNNM_ECANCELED; c->queue.pop_front(); continue; }
+        if (!c->active.empty()) {
+          const Job& a = *c->active[0];
+          if (a.vd != j->vd || a.p.prec != j->p.prec) break;
+        }
+        const int nrp = std::max(fwd_fp32_nrp(j->vd->k), tc_nrp(j->vd->k));
+        const size_t need = job_bytes(j->H, j->W, j->T, j->vd->k, j->vd->kc, j->p.prec, nrp, &j->vd->tc.g);
+        if (c->used + need > c->budget) break;
+        c->queue.pop_front();
+        admitted.push_back(j);
+        c->active.push_back(j);
+        j->phase = ADMITTED;
+      }
+    }
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    try {
+      std::vector<Job*> fresh;
+      for (auto& j : admitted) {
+        try {
+          alloc_job(c, *j);
+          j->t_admit = std::chrono::steady_clock::now();
+          fresh.push_back(j.get());
+        } catch (StatusFail& f) {
+          j->phase = FAILED; j->st = f.st; j->err = f.msg;
+        }
+      }
+      if (!fresh.empty()) {
+        engine_init(c, fresh);
+        for (Job* j : fresh) j->phase = RUNNING;
+      }
+      // one iteration for every running job
+      std::vector<Job*> run, chk;
+      for (auto& j : c->active)
+        if (j->phase == RUNNING) run.push_back(j.get());
+      if (!run.empty()) {
+        const int prec = run[0]->p.prec;
+        const TcVData* tcv = &run[0]->vd->tc;
+        std::vector<Job*> plain;
+        for (Job* j : run) {
+          const int it = j->iters + 1;
+          const bool check = it >= j->p.max_iters || (j->p.tol > 0 && it % j->p.check_every == 0) || j->cancel;
+          (check ? chk : plain).push_back(j);
+        }
+        if (!plain.empty()) engine_step(c, upload_list(c, plain), prec, tcv, false);
+        if (!chk.empty()) engine_step(c, upload_list(c, chk), prec, tcv, true);
+        for (Job* j : run) j->iters += 1;
+        std::vector<Job*> fin;
+        for (Job* j : chk) {
+          JobScal s = read_scal(*j, c->stream);
+          j->resid = resid_of(s, j->vd->k);
+          const bool conv = j->p.tol > 0 && j->resid <= j->p.tol && j->iters % j->p.check_every == 0;
+          if (conv || j->iters >= j->p.max_iters || j->cancel) {
+            j->converged = conv;
+            fin.push_back(j);
+          }
+        }
+        if (!fin.empty()) {
+          engine_objective(c, upload_list(c, fin));
+          for (Job* j : fin) {
+            JobScal s = read_scal(*j, c->stream);
+            j->result.resize(j->m);
+            CK(cudaMemcpyAsync(j->result.data(), j->dev.L, j->m * 4, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            j->stats.iters = j->iters;
+            j->stats.residual = j->resid;
+            j->stats.objective = s.objective;
+            j->stats.theta = s.theta;
+            j->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - j->t_admit).count();
+            free_job(c, *j);
+            if (s.status) { j->st = ICNNM_ETIMEOUT; j->phase = FAILED; }
+            else if (j->cancel) { j->st = ICNNM_ECANCELED; j->phase = CANCELED; }
+            else j->phase = DONE;
+          }
+        }
+      }
+    } catch (CudaFail& f) {
+      report(c, f);
+      std::lock_guard<std::mutex> lk(c->qmu);
+      for (auto& j : c->active) { free_job(c, *j); j->phase = FAILED; j->st = ICNNM_ECUDA; }
+    } catch (StatusFail& f) {
+      report(c, f);
+      std::lock_guard<std::mutex> lk(c->qmu);
+      for (auto& j : c->active) { free_job(c, *j); j->phase = FAILED; j->st = f.st; }
+    }
+    {
+      std::lock_guard<std::mutex> lk(c->qmu);
+      c->active.erase(std::remove_if(c->active.begin(), c->active.end(),
+                                     [](const std::shared_ptr<Job>& j) { return j->phase >= DONE; }),
+                      c->active.end());
+    }
+    c->qcv.notify_all();
+  }
+}
+
+}  // namespace
+
+// =================================================================================
+// Exported entry points
+// =================================================================================
+extern "C" {
+
+icnnm_status icnnm_params_default(icnnm_params* p) {
+  if (!p) return ICNNM_EINVAL;
+  p->lambda = INFINITY;
+  p->theta0 = 0.0;
+  p->rho = 1.1;
+  p->theta_max = 1e10;
+  p->max_iters = 100;
+  p->tol = 0.0;
+  p->check_every = 10;
+  p->prec = ICNNM_BF16;
+  return ICNNM_OK;
+}
+
+const char* icnnm_strerror(icnnm_status st) {
+  switch (st) {
+    case ICNNM_OK: return "ok";
+    case ICNNM_EINVAL: return "invalid argument";
+    case ICNNM_ENOMEM: return "job state exceeds the HBM budget";
+    case ICNNM_EAGAIN: return "job not finished";
+    case ICNNM_ENOTFOUND: return "unknown job id";
+    case ICNNM_ECUDA: return "CUDA error";
+    case ICNNM_ETIMEOUT: return "a bounded device-side wait expired";
+    case ICNNM_ECANCELED: return "job cancelled";
+    case ICNNM_EUNSUPPORTED: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+const char* icnnm_last_error(icnnm_ctx* c) {
+  if (!c) return "";
+  std::lock_guard<std::mutex> g(c->err_mu);
+  return c->last_err.c_str();
+}
+
+icnnm_status icnnm_create(icnnm_ctx** out, int device, size_t budget, void* stream) {
+  if (!out) return ICNNM_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return ICNNM_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return ICNNM_ECUDA;
+  auto* c = new icnnm_ctx();
+  c->device = device;
+  if (stream) c->stream = (cudaStream_t)stream;
+  else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return ICNNM_ECUDA; }
+    c->own_stream = true;
+  }
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  c->budget = budget ? budget : (size_t)(0.9 * fr);
+  if (budget > fr) { if (c->own_stream) cudaStreamDestroy(c->stream); delete c; return ICNNM_ENOMEM; }
+  *out = c;
+  return ICNNM_OK;
+}
+
+void icnnm_destroy(icnnm_ctx* c) {
+  if (!c) return;
+  {
+    std::lock_guard<std::mutex> lk(c->qmu);
+    c->stop = true;
+    for (auto& j : c->queue) j->cancel = true;
+  }
+  c->qcv.notify_all();
+  if (c->server.joinable()) c->server.join();
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->jobs) free_job(c, *kv.second);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  for (auto& kv : c->vcache) {
+    if (kv.second->dVf) cudaFree(kv.second->dVf);
+    if (kv.second->tc_ready) tc_free_vdata(&kv.second->tc);
+  }
+  if (c->dlist) cudaFree(c->dlist);
+  if (c->dtile0) cudaFree(c->dtile0);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+icnnm_status icnnm_learn_V(icnnm_ctx* c, const int64_t kdims[3], int32_t b, const icnnm_shape* shapes,
+                           const float* const* tensors, double* V_out, double* eig_out) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  std::vector<void*> tmp;
+  try {
+    CK(cudaSetDevice(c->device));
+    if (!kdims || b < 1 || !shapes || !tensors || !V_out) fail(ICNNM_EINVAL, "NULL argument or b < 1");
+    const int k1 = (int)kdims[0], k2 = (int)kdims[1], k3 = (int)kdims[2];
+    if (k1 < 1 || k2 < 1 || k3 < 1) fail(ICNNM_EINVAL, "kdims must be >= 1");
+    const long long kk = (long long)k1 * k2 * k3;
+    if (kk > 1024) fail(ICNNM_EINVAL, "k must be <= 1024");
+    if ((long long)(2 * k1 - 1) * (2 * k2 - 1) * (2 * k3 - 1) > learn_max_lags())
+      fail(ICNNM_EUNSUPPORTED, "too many autocorrelation lags for this build");
+    if (learn_smem_bytes(k1, k2, k3) > 220 * 1024) fail(ICNNM_EUNSUPPORTED, "kernel too large for learn_V");
+    const int k = (int)kk;
+    std::vector<const float*> dptr(b);
+    std::vector<int> dims(3 * b);
+    int* dbad;
+    CK(cudaMalloc(&dbad, 4));
+    tmp.push_back(dbad);
+    CK(cudaMemset(dbad, 0, 4));
+    for (int j = 0; j < b; ++j) {
+      const icnnm_shape& s = shapes[j];
+      const int H = (int)s.dims[0], W = (int)s.dims[1], T = s.ndim == 3 ? (int)s.dims[2] : 1;
+      if (s.ndim != 2 && s.ndim != 3) fail(ICNNM_EINVAL, "ndim must be 2 or 3");
+      if (H < k1 || W < k2 || T < k3) fail(ICNNM_EINVAL, "every dim must be at least the kernel's");
+      if (!tensors[j]) fail(ICNNM_EINVAL, "NULL tensor");
+      const long long m = (long long)H * W * T;
+      dims[3 * j] = H; dims[3 * j + 1] = W; dims[3 * j + 2] = T;
+      if (is_device_ptr(tensors[j])) dptr[j] = tensors[j];
+      else {
+        void* p;
+        CK(cudaMalloc(&p, m * 4));
+        tmp.push_back(p);
+        CK(cudaMemcpyAsync(p, tensors[j], m * 4, cudaMemcpyHostToDevice, c->stream));
+        dptr[j] = (const float*)p;
+      }
+      CK(check_finite(dptr[j], m, dbad, c->stream));
+    }
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, dbad, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hbad) fail(ICNNM_EINVAL, "a reference tensor has a non-finite entry");
+    const float** dL;
+    int* ddims;
+    CK(cudaMalloc(&dL, sizeof(float*) * b)); tmp.push_back(dL);
+    CK(cudaMalloc(&ddims, sizeof(int) * 3 * b)); tmp.push_back(ddims);
+    CK(cudaMemcpyAsync(dL, dptr.data(), sizeof(float*) * b, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(ddims, dims.data(), sizeof(int) * 3 * b, cudaMemcpyHostToDevice, c->stream));
+    const int nblk = 16;
+    const long long nlag = (long long)(2 * k1 - 1) * (2 * k2 - 1) * (2 * k3 - 1);
+    double *dpart, *dgram, *dV, *dev, *dVout;
+    int* dinfo;
+    CK(cudaMalloc(&dpart, sizeof(double) * b * nblk * nlag)); tmp.push_back(dpart);
+    CK(cudaMalloc(&dgram, sizeof(double) * k * k)); tmp.push_back(dgram);
+    CK(cudaMalloc(&dV, sizeof(double) * k * k)); tmp.push_back(dV);
+    CK(cudaMalloc(&dVout, sizeof(double) * k * k)); tmp.push_back(dVout);
+    CK(cudaMalloc(&dev, sizeof(double) * k)); tmp.push_back(dev);
+    CK(cudaMalloc(&dinfo, sizeof(int))); tmp.push_back(dinfo);
+    CK(learn_gram(b, dL, ddims, k1, k2, k3, dpart, nblk, dgram, c->stream));
+    CK(learn_eig(dgram, dV, k, dev, dVout, dinfo, c->stream));
+    CK(cudaMemcpyAsync(V_out, dVout, sizeof(double) * k * k, cudaMemcpyDefault, c->stream));
+    if (eig_out) CK(cudaMemcpyAsync(eig_out, dev, sizeof(double) * k, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (void* p : tmp) cudaFree(p);
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    for (void* p : tmp) cudaFree(p);
+    return report(c, f);
+  } catch (CudaFail& f) {
+    for (void* p : tmp) cudaFree(p);
+    return report(c, f);
+  }
+}
+
+icnnm_status icnnm_solve_batch(icnnm_ctx* c, int32_t n, const icnnm_shape* shapes, const float* const* M,
+                               const uint8_t* const* mask, const double* V, const icnnm_params* params,
+                               float* const* L_out, icnnm_stats* stats) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  std::vector<std::unique_ptr<Job>> jobs;
+  try {
+    CK(cudaSetDevice(c->device));
+    if (n < 1 || !shapes || !M || !mask || !L_out) fail(ICNNM_EINVAL, "NULL argument or n < 1");
+    const icnnm_params p = params ? *params : defaults();
+    std::vector<Job*> js;
+    for (int i = 0; i < n; ++i) {
+      jobs.push_back(std::make_unique<Job>());
+      prepare_job(c, *jobs.back(), &shapes[i], M[i], mask[i], V, p, false);
+      if (i > 0 && (shapes[i].kdims[0] != shapes[0].kdims[0] || shapes[i].kdims[1] != shapes[0].kdims[1] ||
+                    shapes[i].kdims[2] != shapes[0].kdims[2]))
+        fail(ICNNM_EINVAL, "all problems of a batch share kernel dims");
+      js.push_back(jobs.back().get());
+    }
+    for (Job* j : js) alloc_job(c, *j);
+    run_jobs(c, js, L_out);
+    if (stats)
+      for (int i = 0; i < n; ++i) stats[i] = js[i]->stats;
+    for (Job* j : js) free_job(c, *j);
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    cudaStreamSynchronize(c->stream);
+    for (auto& j : jobs) free_job(c, *j);
+    return report(c, f);
+  } catch (CudaFail& f) {
+    cudaStreamSynchronize(c->stream);
+    for (auto& j : jobs) free_job(c, *j);
+    return report(c, f);
+  }
+}
+
+icnnm_status icnnm_solve(icnnm_ctx* c, const icnnm_shape* shape, const float* M, const uint8_t* mask,
+                         const double* V, const icnnm_params* params, float* L_out, icnnm_stats* stats) {
+  if (!L_out) {
+    if (c) set_err(c, "L_out is NULL");
+    return ICNNM_EINVAL;
+  }
+  float* outs[1] = {L_out};
+  const float* Ms[1] = {M};
+  const uint8_t* Ks[1] = {mask};
+  return icnnm_solve_batch(c, 1, shape, Ms, Ks, V, params, outs, stats);
+}
+
+icnnm_status icnnm_submit(icnnm_ctx* c, const icnnm_shape* shape, const float* M, const uint8_t* mask,
+                          const double* V, const icnnm_params* params, uint64_t* job_id) {
+  if (!c || !job_id) return ICNNM_EINVAL;
+  auto j = std::make_shared<Job>();
+  try {
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    CK(cudaSetDevice(c->device));
+    const icnnm_params p = params ? *params : defaults();
+    prepare_job(c, *j, shape, M, mask, V, p, true);
+    const int nrp = std::max(fwd_fp32_nrp(j->vd->k), tc_nrp(j->vd->k));
+    if (job_bytes(j->H, j->W, j->T, j->vd->k, j->vd->kc, p.prec, nrp, &j->vd->tc.g) > c->budget)
+      fail(ICNNM_ENOMEM, "the job alone exceeds the HBM budget");
+  } catch (StatusFail& f) {
+    return report(c, f);
+  } catch (CudaFail& f) {
+    return report(c, f);
+  }
+  {
+    std::lock_guard<std::mutex> lk(c->qmu);
+    j->id = c->next_id++;
+    c->jobs[j->id] = j;
+    c->queue.push_back(j);
+    if (!c->server.joinable()) c->server = std::thread(server_loop, c);
+  }
+  c->qcv.notify_all();
+  *job_id = j->id;
+  return ICNNM_OK;
+}
+
+static icnnm_status collect(icnnm_ctx* c, std::shared_ptr<Job> j, float* L_out, icnnm_stats* stats) {
+  if (j->phase == DONE) {
+    if (L_out) {
+      if (cudaMemcpy(L_out, j->result.data(), j->m * 4, cudaMemcpyDefault) != cudaSuccess) return ICNNM_ECUDA;
+    }
+    if (stats) *stats = j->stats;
+    return ICNNM_OK;
+  }
+  if (!j->err.empty()) set_err(c, j->err);
+  return j->st == ICNNM_OK ? ICNNM_ECUDA : j->st;
+}
+
+icnnm_status icnnm_poll(icnnm_ctx* c, uint64_t id, float* L_out, icnnm_stats* stats) {
+  return icnnm_wait(c, id, 0, L_out, stats);
+}
+
+icnnm_status icnnm_wait(icnnm_ctx* c, uint64_t id, int64_t timeout_ms, float* L_out, icnnm_stats* stats) {
+  if (!c) return ICNNM_EINVAL;
+  std::shared_ptr<Job> j;
+  {
+    std::unique_lock<std::mutex> lk(c->qmu);
+    auto it = c->jobs.find(id);
+    if (it == c->jobs.end()) return ICNNM_ENOTFOUND;
+    j = it->second;
+    auto done = [&] { return j->phase >= DONE; };
+    if (timeout_ms < 0) c->qcv.wait(lk, done);
+    else if (timeout_ms > 0) c->qcv.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
+    if (!done()) return ICNNM_EAGAIN;
+    c->jobs.erase(it);
+  }
+  return collect(c, j, L_out, stats);
+}
+
+icnnm_status icnnm_profile_enable(icnnm_ctx* c, int32_t enable) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  c->prof = enable != 0;
+  c->pending.clear();
+  c->evnext = 0;
+  for (int i = 0; i < 4; ++i) c->pass_ms[i] = 0;
+  for (int i = 0; i < 5; ++i) c->pass_n[i] = 0;
+  return ICNNM_OK;
+}
+
+icnnm_status icnnm_profile_read(icnnm_ctx* c, int32_t pass, double* ms_total, int64_t* launches) {
+  if (!c || pass < -1 || pass > 3) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  if (ms_total) *ms_total = pass < 0 ? 0.0 : c->pass_ms[pass];
+  if (launches) *launches = pass < 0 ? c->pass_n[4] : c->pass_n[pass];
+  return ICNNM_OK;
+}
+
+icnnm_status icnnm_cancel(icnnm_ctx* c, uint64_t id) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::mutex> lk(c->qmu);
+  auto it = c->jobs.find(id);
+  if (it == c->jobs.end()) return ICNNM_ENOTFOUND;
+  it->second->cancel = true;
+  c->qcv.notify_all();
+  return ICNNM_OK;
+}
+
+}  // extern "C"

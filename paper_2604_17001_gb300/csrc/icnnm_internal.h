@@ -1,0 +1,150 @@
+// Internal declarations shared by the CUDA translation units of libicnnm.
+//
+// Algorithm (ADMM of Sec. III-D, run in the shifted-multiplier form
+// U = Y - theta*A_k(L)V, which follows from the Z-, L- and Y-updates using
+// V V^T = I and A_k^* A_k = k I):
+//   s_c  = max(0, 1 - 1/||U_c||),  D = diag(1 - s)                  (Z-update)
+//   L'   = P_Omega^perp(L + A_k^*(U D V^T)/(k theta)) + P_Omega(M)   (L-update, lambda = inf)
+//        = (A_k^*(U D V^T)/k + theta L + lambda Theta M)/(lambda Theta + theta)   (finite lambda)
+//   X    = (theta + theta') L' - theta L,  theta' = min(rho theta, theta_max)
+//   U'   = U D - A_k(X) V                                           (Y-update, re-shifted)
+// Per iteration: one "adjoint" pass (G = U (D V^T), then col2im), one gather/projection
+// pass over m voxels, one "forward" pass (E = A_k(X)V fused with the U update and the
+// per-tile column-norm partials of U'), and small per-job reduction/scalar kernels.
+#pragma once
+#include <math.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace icnnm {
+
+// Voxel tile of the forward/adjoint passes: TW (w) x TH (h) x 1 (t) = 128 voxels.
+constexpr int TW = 8;
+constexpr int TH = 16;
+constexpr int TILE_VOX = TW * TH;
+constexpr int NSEG = 32;          // tile segments of the first column-reduction stage
+
+// Mutable per-job scalars (device memory). Kept apart from JobDev so that a job can
+// be listed in several launch lists without its state diverging.
+struct JobScal {
+  double theta;         // current penalty
+  double theta_next;    // penalty of the next iteration
+  double lsq;           // ||L||^2 at the last residual check
+  double rsq;           // ||Z - A_k(L)V||_F^2 at the last residual check
+  double objective;     // ||A_k(L)V||_{2,1} after the run
+  int iter;             // iterations completed
+  int status;           // 0 ok; nonzero: a bounded device-side wait expired
+};
+
+// Per-job device pointers and static info (copied by value into launch lists).
+struct JobDev {
+  int H, W, T;          // dims
+  int nth, ntw;         // voxel tiles along h and w (ceil(H/TH), ceil(W/TW))
+  int ntiles;           // nth * ntw * T
+  long long m;          // H*W*T
+  double lam;           // INFINITY for the exact projection
+  double rho, theta_max;
+  JobScal* sc;
+  const float* M;       // m, observed values (entries off Omega are ignored)
+  const uint8_t* mask;  // m, 1 = observed
+  float* L;             // m, current iterate (FP32)
+  float* X;             // m, operand of the forward pass (FP32 path)
+  __nv_bfloat16* Xc;    // BF16 path: wrap-padded, w-shifted copies of the operand
+  void* U;              // m x kc shifted multiplier, row-major [voxel][channel]:
+                        //   FP32 (FP32 path) or BF16 (BF16 path)
+  float* part;          // per-tile column partial sums of ||.||^2: [ntiles][kc]
+  float* rpart;         // per-tile residual partials: [ntiles][nrp]
+  float* lpart;         // per-tile ||L'||^2 partials: [ntiles]
+  double* colseg;       // first-stage column sums: [NSEG][kc]
+  float* s;             // kc, shrink factors of this iteration
+  float* D;             // kc, 1 - s
+  float* G;             // FP32 path: G^T = (V D) U^T, [k][m]; BF16 path: col2im partials
+  __nv_bfloat16* B2img; // BF16 path: A-operand images of the adjoint pass (V D)
+  const void* tmapX;    // BF16 path: TMA map (CUtensorMap, device memory) of Xc
+  const void* tmapU;    // BF16 path: TMA map of U
+  const int* glist;     // BF16 path: col2im gather lists (see k_tc.cu)
+  int xTp, xHp, xWp;    // BF16 path: dims of each copy in Xc
+};
+
+// Shared (per V / per launch list) constants.
+struct Shared {
+  int k1, k2, k3, k;     // kernel dims along (h, w, t) and k = k1*k2*k3
+  int kc;                // channel stride of U (k rounded up to 16)
+  int nrp;               // residual partials per tile
+  const float* Vf;       // [k taps][kc] FP32, V[s][c] (column c = eigenvector c)
+  const __nv_bfloat16* VtImg;  // BF16 forward-pass A-operand images (see k_tc.cu)
+  int njobs;
+  const JobDev* jobs;    // device array of njobs
+  const int* job_tile0;  // device, njobs + 1 prefix sums of ntiles
+  int total_tiles;
+};
+
+// Binary search: the job that owns global tile `t`.
+__device__ __forceinline__ int job_of_tile(const int* tile0, int njobs, int t) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tile0[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+// L-update of Sec. III-D at voxel v, given Delta = [A_k^*(U D V^T)]_v:
+//   lambda = inf : L' = M on Omega, L + Delta/(k theta) off Omega;
+//   lambda finite: L' = (Delta/k + theta L + lambda Theta M)/(lambda Theta + theta).
+// Also writes the next forward operand X = (theta + theta') L' - theta L. Returns L'.
+__device__ __forceinline__ float l_update(const JobDev& J, int k, long long v, float d) {
+  const float Lo = J.L[v];
+  const double th = J.sc->theta;
+  const bool obs = J.mask[v] != 0;
+  float Ln;
+  if (isinf(J.lam)) {
+    Ln = obs ? J.M[v] : fmaf(d, (float)(1.0 / (k * th)), Lo);
+  } else {
+    const double lt = obs ? J.lam : 0.0;
+    Ln = (float)(((double)d / k + th * (double)Lo + lt * (obs ? (double)J.M[v] : 0.0)) / (lt + th));
+  }
+  J.X[v] = fmaf((float)(th + J.sc->theta_next), Ln, -(float)th * Lo);
+  J.L[v] = Ln;
+  return Ln;
+}
+
+// ---------------------------------------------------------------------------------
+// Launchers (host). All enqueue on `st` and return cudaGetLastError().
+// ---------------------------------------------------------------------------------
+// k_common.cu
+cudaError_t launch_init_L(const Shared& sh, cudaStream_t st);
+cudaError_t launch_reduce_cols(const Shared& sh, int advance, cudaStream_t st);
+cudaError_t launch_theta0(const Shared& sh, double theta0_user, cudaStream_t st);
+cudaError_t launch_scale_X(const Shared& sh, cudaStream_t st);
+cudaError_t launch_scalars(const Shared& sh, cudaStream_t st);
+cudaError_t launch_gather_fp32(const Shared& sh, cudaStream_t st);
+// what: 1 = residual (||L||^2 and residual^2 from the partials), 2 = objective
+cudaError_t launch_finish(const Shared& sh, int what, cudaStream_t st);
+
+// k_fp32.cu
+// mode: 0 = column norms of A_k(X)V only (no U access); 1 = U' = U D - A_k(X)V;
+//       2 = U' = -A_k(X)V (U not read); 3 = residual partials sum (U s/theta + A_k(L)V)^2
+//       (no write); 4 = column norms of A_k(L)V (the objective)
+cudaError_t launch_fwd_fp32(const Shared& sh, int mode, cudaStream_t st);
+cudaError_t launch_adj_gemm_fp32(const Shared& sh, cudaStream_t st);
+int fwd_fp32_nrp(int k);
+
+// k_learn.cu
+cudaError_t learn_gram(int b, const float* const* dL, const int* ddims, int k1, int k2, int k3,
+                       double* dpart, int nblk, double* dgram, cudaStream_t st);
+size_t learn_smem_bytes(int k1, int k2, int k3);
+int learn_max_lags();
+cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo,
+                      cudaStream_t st);
+cudaError_t check_finite(const float* x, long long n, int* dbad, cudaStream_t st);
+cudaError_t check_observed(const float* M, const uint8_t* mask, long long n, int* dcount_bad,
+                           cudaStream_t st);
+
+}  // namespace icnnm

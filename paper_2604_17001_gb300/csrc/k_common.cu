@@ -1,0 +1,229 @@
+// Kernels shared by both arithmetic paths: initial state, the two-stage fixed-order
+// reduction of per-tile column partials, the per-job scalar step (shrink factors,
+// penalty schedule), the FP32 col2im gather with the Omega-projection (L-update),
+// and the end-of-run scalars.
+#include <math.h>
+#include "icnnm_internal.h"
+
+namespace icnnm {
+
+namespace {
+
+struct TileVox {
+  int jb, tile, t, h, w;
+  bool valid;
+};
+
+// Voxel of thread threadIdx.x (< TILE_VOX) in global tile blockIdx.x.
+__device__ __forceinline__ TileVox tile_voxel(const Shared& sh) {
+  TileVox r;
+  const int tile_g = blockIdx.x;
+  r.jb = job_of_tile(sh.job_tile0, sh.njobs, tile_g);
+  const JobDev& J = sh.jobs[r.jb];
+  r.tile = tile_g - sh.job_tile0[r.jb];
+  const int tw = r.tile % J.ntw, th = (r.tile / J.ntw) % J.nth;
+  r.t = r.tile / (J.ntw * J.nth);
+  r.h = th * TH + threadIdx.x / TW;
+  r.w = tw * TW + threadIdx.x % TW;
+  r.valid = r.h < J.H && r.w < J.W;
+  return r;
+}
+
+// L = P_Omega(M) (the initial iterate, a reading: the paper does not state L0); X = L.
+__global__ void init_L_kernel(Shared sh) {
+  const TileVox p = tile_voxel(sh);
+  if (!p.valid) return;
+  const JobDev& J = sh.jobs[p.jb];
+  const long long v = ((long long)p.t * J.H + p.h) * J.W + p.w;
+  const float x = J.mask[v] ? J.M[v] : 0.f;
+  J.L[v] = x;
+  if (J.X) J.X[v] = x;
+}
+
+// First reduction stage: colseg[seg][c] = sum over the tiles of segment seg of
+// part[tile][c], in FP64; warp w adds tiles lo+w, lo+w+8, ... in increasing order and
+// the 8 warp sums are combined in warp order. Block = (job, 32 channels, segment).
+// With `advance`, one block per job moves theta to theta_next and counts the
+// iteration (every kernel of the iteration that reads theta has run by then).
+__global__ void reduce_cols_kernel(Shared sh, int advance) {
+  const JobDev& J = sh.jobs[blockIdx.x];
+  const int c = blockIdx.y * 32 + (threadIdx.x & 31);
+  const int warp = threadIdx.x >> 5;
+  const int seg = blockIdx.z;
+  const int lo = (int)((long long)J.ntiles * seg / NSEG);
+  const int hi = (int)((long long)J.ntiles * (seg + 1) / NSEG);
+  double acc = 0.0;
+  if (c < sh.kc)
+    for (int t = lo + warp; t < hi; t += 8) acc += (double)J.part[(long long)t * sh.kc + c];
+  __shared__ double red[8][32];
+  red[warp][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (warp == 0 && c < sh.kc) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+    J.colseg[(long long)seg * sh.kc + c] = s;
+  }
+  if (advance && blockIdx.y == 0 && seg == 0 && threadIdx.x == 0) {
+    J.sc->theta = J.sc->theta_next;
+    J.sc->iter += 1;
+  }
+}
+
+__device__ __forceinline__ double colsq_of(const JobDev& J, int kc, int c) {
+  double q = 0.0;
+  for (int seg = 0; seg < NSEG; ++seg) q += J.colseg[(long long)seg * kc + c];
+  return q;
+}
+
+// Per-job scalar step at the start of an iteration (the Z-update of Sec. III-D in
+// shifted form): s_c = max(0, 1 - 1/||U_c||) (the column-wise l2,1 shrinkage with
+// threshold 1/theta applied to -U/theta), D_c = 1 - s_c; theta' = min(rho theta, theta_max).
+__global__ void scalars_kernel(Shared sh) {
+  const JobDev& J = sh.jobs[blockIdx.x];
+  for (int c = threadIdx.x; c < sh.kc; c += blockDim.x) {
+    const double n = sqrt(colsq_of(J, sh.kc, c));
+    const double sc = (c < sh.k && n > 1.0) ? 1.0 - 1.0 / n : 0.0;
+    J.s[c] = (float)sc;
+    J.D[c] = (c < sh.k) ? (float)(1.0 - sc) : 0.f;
+  }
+  if (threadIdx.x == 0) J.sc->theta_next = fmin(J.rho * J.sc->theta, J.theta_max);
+}
+
+// theta0 = 1 / max_c ||A_k(P_Omega M) V_c|| unless the caller gives one (a reading: the
+// paper does not state theta0). Column sums come from the norm-only forward pass.
+__global__ void theta0_kernel(Shared sh, double theta0_user) {
+  const JobDev& J = sh.jobs[blockIdx.x];
+  __shared__ double mx[256];
+  double m = 0.0;
+  for (int c = threadIdx.x; c < sh.k; c += blockDim.x) m = fmax(m, colsq_of(J, sh.kc, c));
+  mx[threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int i = 0; i < blockDim.x; ++i) mm = fmax(mm, mx[i]);
+    const double th = theta0_user > 0 ? theta0_user : (mm > 0 ? 1.0 / sqrt(mm) : 1.0);
+    J.sc->theta = th;
+    J.sc->theta_next = th;
+    J.sc->iter = 0;
+  }
+}
+
+__global__ void scale_X_kernel(Shared sh) {
+  const TileVox p = tile_voxel(sh);
+  if (!p.valid) return;
+  const JobDev& J = sh.jobs[p.jb];
+  const long long v = ((long long)p.t * J.H + p.h) * J.W + p.w;
+  J.X[v] = (float)J.sc->theta * J.L[v];
+}
+
+// FP32 path L-update. Delta_j = [A_k^*(G)]_j = sum_s G^T[s][(j + s) mod dims] in tap
+// order (the adjoint of Eq. ak), then
+//   lambda = inf : L'_j = M_j on Omega and L_j + Delta_j/(k theta) off Omega;
+//   lambda finite: L'_j = (Delta_j/k + theta L_j + lambda Theta_j M_j)/(lambda Theta_j + theta);
+// X_j = (theta + theta') L'_j - theta L_j; L <- L'. Per-tile partial of ||L'||^2.
+__global__ void gather_fp32_kernel(Shared sh) {
+  const TileVox p = tile_voxel(sh);
+  const JobDev& J = sh.jobs[p.jb];
+  __shared__ float red[TILE_VOX];
+  float l2 = 0.f;
+  if (p.valid) {
+    const int H = J.H, W = J.W, T = J.T;
+    const long long v = ((long long)p.t * H + p.h) * W + p.w;
+    float d = 0.f;
+    int s = 0;
+    for (int st = 0; st < sh.k3; ++st) {
+      const int tt = wrapi(p.t + st, T);
+      for (int sh_ = 0; sh_ < sh.k1; ++sh_) {
+        const long long rowb = ((long long)tt * H + wrapi(p.h + sh_, H)) * W;
+        for (int sw = 0; sw < sh.k2; ++sw, ++s) d += J.G[(long long)s * J.m + rowb + wrapi(p.w + sw, W)];
+      }
+    }
+    const float Ln = l_update(J, sh.k, v, d);
+    l2 = Ln * Ln;
+  }
+  red[threadIdx.x] = l2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < TILE_VOX; ++i) s += red[i];
+    J.lpart[p.tile] = s;
+  }
+}
+
+// End-of-pass scalars: what = 1: ||L||^2 and the residual sum of squares from the
+// per-tile partials; what = 2: objective sum_c sqrt(colsq_c).
+__global__ void finish_kernel(Shared sh, int what) {
+  const JobDev& J = sh.jobs[blockIdx.x];
+  __shared__ double a[256], b[256];
+  double x = 0.0, y = 0.0;
+  if (what == 2) {
+    for (int c = threadIdx.x; c < sh.k; c += blockDim.x) x += sqrt(colsq_of(J, sh.kc, c));
+  } else {
+    for (int t = threadIdx.x; t < J.ntiles; t += blockDim.x) x += J.lpart[t];
+    for (int t = threadIdx.x; t < J.ntiles * sh.nrp; t += blockDim.x) y += J.rpart[t];
+  }
+  a[threadIdx.x] = x;
+  b[threadIdx.x] = y;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sx = 0, sy = 0;
+    for (int i = 0; i < blockDim.x; ++i) { sx += a[i]; sy += b[i]; }
+    if (what == 2) J.sc->objective = sx;
+    else { J.sc->lsq = sx; J.sc->rsq = sy; }
+  }
+}
+
+__global__ void check_observed_kernel(const float* M, const uint8_t* mask, long long n, int* out) {
+  int cnt = 0, bad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (mask[i] > 1) bad = 1;
+    if (mask[i]) { ++cnt; if (!isfinite(M[i])) bad = 1; }
+  }
+  if (cnt) atomicAdd(out, cnt);
+  if (bad) atomicExch(out + 1, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_init_L(const Shared& sh, cudaStream_t st) {
+  init_L_kernel<<<sh.total_tiles, TILE_VOX, 0, st>>>(sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_cols(const Shared& sh, int advance, cudaStream_t st) {
+  dim3 grid(sh.njobs, (sh.kc + 31) / 32, NSEG);
+  reduce_cols_kernel<<<grid, 256, 0, st>>>(sh, advance);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalars(const Shared& sh, cudaStream_t st) {
+  scalars_kernel<<<sh.njobs, 256, 0, st>>>(sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_theta0(const Shared& sh, double theta0_user, cudaStream_t st) {
+  theta0_kernel<<<sh.njobs, 256, 0, st>>>(sh, theta0_user);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_X(const Shared& sh, cudaStream_t st) {
+  scale_X_kernel<<<sh.total_tiles, TILE_VOX, 0, st>>>(sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_fp32(const Shared& sh, cudaStream_t st) {
+  gather_fp32_kernel<<<sh.total_tiles, TILE_VOX, 0, st>>>(sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const Shared& sh, int what, cudaStream_t st) {
+  finish_kernel<<<sh.njobs, 256, 0, st>>>(sh, what);
+  return cudaGetLastError();
+}
+
+cudaError_t check_observed(const float* M, const uint8_t* mask, long long n, int* d2, cudaStream_t st) {
+  check_observed_kernel<<<256, 256, 0, st>>>(M, mask, n, d2);
+  return cudaGetLastError();
+}
+
+}  // namespace icnnm

@@ -1,0 +1,258 @@
+// Learning V (Sec. III-C, Definition 3, Eq. A): the eigenvectors of A^T A with
+// A = [A_k(L_1); ...; A_k(L_b)].
+//
+// Entry (u, s) of A_k(L)^T A_k(L) is sum_i L[i-u] L[i-s] = R[u - s], the circular
+// autocorrelation R[d] = sum_i L[i] L[i+d] of L at the lag u - s (each coordinate
+// in (-k_j, k_j)). So the Gram needs prod_j (2 k_j - 1) autocorrelation lags per
+// tensor instead of the k^2 dot products of length m of the direct product; the
+// autocorrelations are data-parallel over tensors and voxel bricks (FP32 products,
+// summed in FP32 over 64 voxels, then in FP64).
+//
+// The FP64 eigendecomposition is a parallel cyclic Jacobi method (round-robin pair
+// ordering: every round rotates k/2 disjoint pairs, rows first, then columns).
+#include <math.h>
+#include "icnnm_internal.h"
+
+namespace icnnm {
+
+namespace {
+
+constexpr int BW = 16, BH = 16, BT = 8;      // autocorrelation brick
+constexpr int AC_THREADS = 256;
+constexpr int AC_MAXLAG_PER_THREAD = 16;     // supports up to 4096 lags
+
+struct LearnArgs {
+  int b;
+  const float* const* L;     // device array of b device pointers
+  const int* dims;           // device, 3*b: H, W, T
+  int k1, k2, k3;
+  int nl1, nl2, nl3, nlag;   // 2k-1 per dim and their product
+  int nblk;                  // blocks per tensor
+  double* part;              // [b][nblk][nlag]
+};
+
+// Lag index l <-> (dt, dh, dw) with dt in [-(k3-1), k3-1] etc, l = ((dt+k3-1)*nl1 + dh+k1-1)*nl2 + dw+k2-1.
+__global__ void __launch_bounds__(AC_THREADS) autocorr_kernel(LearnArgs a) {
+  extern __shared__ float sL[];
+  const int j = blockIdx.x;
+  const int H = a.dims[3 * j], W = a.dims[3 * j + 1], T = a.dims[3 * j + 2];
+  const float* L = a.L[j];
+  const int ew = BW + 2 * (a.k2 - 1), eh = BH + 2 * (a.k1 - 1), et = BT + 2 * (a.k3 - 1);
+  const int nbw = (W + BW - 1) / BW, nbh = (H + BH - 1) / BH, nbt = (T + BT - 1) / BT;
+  const int nbr = nbw * nbh * nbt;
+  double acc[AC_MAXLAG_PER_THREAD];
+  int lagoff[AC_MAXLAG_PER_THREAD];
+  int nmy = 0;
+  for (int l = threadIdx.x; l < a.nlag && nmy < AC_MAXLAG_PER_THREAD; l += AC_THREADS) {
+    const int dw = l % a.nl2 - (a.k2 - 1);
+    const int dh = (l / a.nl2) % a.nl1 - (a.k1 - 1);
+    const int dt = l / (a.nl2 * a.nl1) - (a.k3 - 1);
+    lagoff[nmy] = (dt * eh + dh) * ew + dw;
+    acc[nmy] = 0.0;
+    ++nmy;
+  }
+  for (int br = blockIdx.y; br < nbr; br += gridDim.y) {
+    const int bw = br % nbw, bh = (br / nbw) % nbh, bt = br / (nbw * nbh);
+    const int w0 = bw * BW - (a.k2 - 1), h0 = bh * BH - (a.k1 - 1), t0 = bt * BT - (a.k3 - 1);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ew * eh * et; e += AC_THREADS) {
+      const int x = e % ew, y = (e / ew) % eh, z = e / (ew * eh);
+      sL[e] = L[((long long)wrapi(t0 + z, T) * H + wrapi(h0 + y, H)) * W + wrapi(w0 + x, W)];
+    }
+    __syncthreads();
+    const int vw = min(BW, W - bw * BW), vh = min(BH, H - bh * BH), vt = min(BT, T - bt * BT);
+    for (int q = 0; q < nmy; ++q) {
+      float part = 0.f;
+      int cnt = 0;
+      for (int z = 0; z < vt; ++z)
+        for (int y = 0; y < vh; ++y) {
+          const int base = ((z + a.k3 - 1) * eh + (y + a.k1 - 1)) * ew + (a.k2 - 1);
+          for (int x = 0; x < vw; ++x) {
+            part = fmaf(sL[base + x], sL[base + x + lagoff[q]], part);
+            if (++cnt == 64) { acc[q] += (double)part; part = 0.f; cnt = 0; }
+          }
+        }
+      acc[q] += (double)part;
+    }
+  }
+  int q = 0;
+  for (int l = threadIdx.x; l < a.nlag && q < AC_MAXLAG_PER_THREAD; l += AC_THREADS, ++q)
+    a.part[((long long)j * a.nblk + blockIdx.y) * a.nlag + l] = acc[q];
+}
+
+// Gram[u][s] = sum_j sum_blk part[j][blk][lag(u - s)], summed in a fixed order.
+__global__ void gram_kernel(LearnArgs a, double* gram) {
+  const int k = a.k1 * a.k2 * a.k3;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)k * k) return;
+  const int u = (int)(idx / k), s = (int)(idx % k);
+  const int uw = u % a.k2, uh = (u / a.k2) % a.k1, ut = u / (a.k1 * a.k2);
+  const int sw = s % a.k2, shh = (s / a.k2) % a.k1, st = s / (a.k1 * a.k2);
+  const int l = ((ut - st + a.k3 - 1) * a.nl1 + (uh - shh + a.k1 - 1)) * a.nl2 + (uw - sw + a.k2 - 1);
+  double g = 0.0;
+  for (int j = 0; j < a.b; ++j)
+    for (int bb = 0; bb < a.nblk; ++bb) g += a.part[((long long)j * a.nblk + bb) * a.nlag + l];
+  gram[idx] = g;
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 parallel cyclic Jacobi on one thread block. A (k x k, row-major, symmetric) is
+// overwritten; V (k x k) accumulates the rotations. Each sweep runs n-1 rounds of the
+// circle (round-robin) schedule on n = k rounded up to even; index k is a dummy.
+// Stops when the off-diagonal Frobenius norm is <= tol * ||A||_F or after max_sweeps.
+// ---------------------------------------------------------------------------------
+constexpr int EIG_THREADS = 1024;
+constexpr int EIG_MAXK = 1024;
+
+__global__ void __launch_bounds__(EIG_THREADS)
+jacobi_kernel(double* A, double* V, int k, int max_sweeps, double tol, double* evals_out,
+              double* Vout, int* info) {
+  __shared__ double cs[EIG_MAXK / 2], sn[EIG_MAXK / 2];
+  __shared__ int pp[EIG_MAXK / 2], qq[EIG_MAXK / 2];
+  __shared__ double red[EIG_THREADS];
+  __shared__ int order[EIG_MAXK];
+  __shared__ double ev[EIG_MAXK];
+  const int n = (k + 1) & ~1;
+  const int npair = n / 2;
+  for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x)
+    V[e] = (e / k == e % k) ? 1.0 : 0.0;
+  __syncthreads();
+  // ||A||_F for the stopping test
+  double fr = 0.0;
+  for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) fr += A[e] * A[e];
+  red[threadIdx.x] = fr;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double normA = sqrt(red[0]);
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    double off = 0.0;
+    for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x)
+      if (e / k != e % k) off += A[e] * A[e];
+    red[threadIdx.x] = off;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    const double offn = sqrt(red[0]);
+    __syncthreads();
+    if (offn <= tol * normA) break;
+    for (int r = 0; r < n - 1; ++r) {
+      for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+        int p, q;
+        if (i == 0) { p = r; q = n - 1; }
+        else { p = (r + i) % (n - 1); q = (r - i + (n - 1)) % (n - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < k) {
+          const double apq = A[(long long)p * k + q];
+          if (apq != 0.0) {
+            const double app = A[(long long)p * k + p], aqq = A[(long long)q * k + q];
+            const double th = (aqq - app) / (2.0 * apq);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
+      }
+      __syncthreads();
+      // rows: A[p][:], A[q][:] <- c A[p] - s A[q], s A[p] + c A[q]
+      for (long long e = threadIdx.x; e < (long long)npair * k; e += blockDim.x) {
+        const int i = (int)(e / k), col = (int)(e % k);
+        const int p = pp[i], q = qq[i];
+        if (q >= k || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double ap = A[(long long)p * k + col], aq = A[(long long)q * k + col];
+        A[(long long)p * k + col] = c * ap - s * aq;
+        A[(long long)q * k + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns of A and of V
+      for (long long e = threadIdx.x; e < (long long)npair * k; e += blockDim.x) {
+        const int i = (int)(e / k), row = (int)(e % k);
+        const int p = pp[i], q = qq[i];
+        if (q >= k || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double ap = A[(long long)row * k + p], aq = A[(long long)row * k + q];
+        A[(long long)row * k + p] = c * ap - s * aq;
+        A[(long long)row * k + q] = s * ap + c * aq;
+        const double vp = V[(long long)row * k + p], vq = V[(long long)row * k + q];
+        V[(long long)row * k + p] = c * vp - s * vq;
+        V[(long long)row * k + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // Sort by decreasing eigenvalue (stable), canonical sign, write column-major output.
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ev[i] = A[(long long)i * k + i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    int rank = 0;
+    for (int j = 0; j < k; ++j) rank += (ev[j] > ev[i]) || (ev[j] == ev[i] && j < i);
+    order[rank] = i;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < k; o += blockDim.x) {
+    const int i = order[o];
+    int amax = 0;
+    double vmax = -1.0;
+    for (int srow = 0; srow < k; ++srow) {
+      const double a = fabs(V[(long long)srow * k + i]);
+      if (a > vmax) { vmax = a; amax = srow; }
+    }
+    const double sg = V[(long long)amax * k + i] < 0 ? -1.0 : 1.0;
+    for (int srow = 0; srow < k; ++srow) Vout[(long long)o * k + srow] = sg * V[(long long)srow * k + i];
+    evals_out[o] = ev[i];
+  }
+  if (threadIdx.x == 0) info[0] = sweep;
+}
+
+__global__ void finite_check_kernel(const float* x, long long n, int* bad) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) { atomicExch(bad, 1); return; }
+}
+
+}  // namespace
+
+// Host launchers -------------------------------------------------------------------
+cudaError_t learn_gram(int b, const float* const* dL, const int* ddims, int k1, int k2, int k3,
+                       double* dpart, int nblk, double* dgram, cudaStream_t st) {
+  LearnArgs a;
+  a.b = b; a.L = dL; a.dims = ddims; a.k1 = k1; a.k2 = k2; a.k3 = k3;
+  a.nl1 = 2 * k1 - 1; a.nl2 = 2 * k2 - 1; a.nl3 = 2 * k3 - 1;
+  a.nlag = a.nl1 * a.nl2 * a.nl3;
+  a.nblk = nblk; a.part = dpart;
+  const int ew = BW + 2 * (k2 - 1), eh = BH + 2 * (k1 - 1), et = BT + 2 * (k3 - 1);
+  const size_t smem = sizeof(float) * (size_t)ew * eh * et;
+  cudaFuncSetAttribute(autocorr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  autocorr_kernel<<<dim3(b, nblk), AC_THREADS, smem, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long kk = (long long)k1 * k2 * k3;
+  gram_kernel<<<(unsigned)((kk * kk + 255) / 256), 256, 0, st>>>(a, dgram);
+  return cudaGetLastError();
+}
+
+size_t learn_smem_bytes(int k1, int k2, int k3) {
+  return sizeof(float) * (size_t)(BW + 2 * (k2 - 1)) * (BH + 2 * (k1 - 1)) * (BT + 2 * (k3 - 1));
+}
+int learn_max_lags() { return AC_THREADS * AC_MAXLAG_PER_THREAD; }
+
+cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo,
+                      cudaStream_t st) {
+  jacobi_kernel<<<1, EIG_THREADS, 0, st>>>(dA, dV, k, 30, 1e-15, devals, dVout, dinfo);
+  return cudaGetLastError();
+}
+
+cudaError_t check_finite(const float* x, long long n, int* dbad, cudaStream_t st) {
+  finite_check_kernel<<<256, 256, 0, st>>>(x, n, dbad);
+  return cudaGetLastError();
+}
+
+}  // namespace icnnm

@@ -1,0 +1,763 @@
+// BF16 tensor-core path (sm_103a: tcgen05 MMA with TMEM accumulators, TMA loads).
+//
+// Forward pass  E^T = V^T A_k(X)^T  (row i of A_k(X) holds X[i - s] for every tap s,
+// Sec. II-B Eq. ak), fused with U' = U D - E and the per-tile partials of ||U'_c||^2.
+//   M = 128 channels, N = 128 voxels (an 8w x 16h tile of one frame), K = taps.
+//   A = V^T (one channel tile per persistent CTA, resident in shared memory, SW128
+//   K-major). B = A_k(X)^T is never formed: the operand is kept as ncopy = min(k2, 8)
+//   bf16 copies of X, copy c shifted by c along w and wrap-padded, so that every
+//   8-voxel row segment of every tap starts on a 16-byte boundary. A TMA box of all
+//   copies (halo of the tile: Hh = TH + k1 - 1 rows x k3 frames x 8 w) lands in shared
+//   memory as rows of 16 bytes indexed rho = h*k3 + t. For a fixed w-tap sw the taps
+//   (sh, st) then sit at rows rho = g*k3 + r with r = k1*k3 - 1 - (sh*k3 + st), so the
+//   B operand of each MMA is an MN-major no-swizzle matrix whose core matrices overlap:
+//   N-groups (output rows g) are k3 rows apart, K-rows are consecutive rows.
+//   The taps are therefore ordered (sw, then r), each sw-run padded to 8 rows (the
+//   padded taps have zero rows in V^T).
+//
+// Adjoint pass  G^T = (V D) U^T, then col2im  Delta_j = sum_s G[j + s, s]  (the adjoint
+// of Eq. ak), deterministic:
+//   M = 128 taps (the V D image of the job, SW128 K-major), N = 128 voxels (the U tile
+//   by TMA, SW128 K-major, zero-filled beyond the tensor), K = channels.
+//   Each epilogue warp adds its 32 taps' contributions into its own shared-memory
+//   halo buffer, one voxel column at a time (the lanes of one column write distinct
+//   addresses; columns are separated by a warp barrier), the four buffers are summed
+//   in warp order and written as the tile's halo partial; a gather kernel adds, for
+//   every voxel, the partials of all tiles whose halo covers it, in a fixed order.
+//
+// Warp roles in both kernels: warp 0 issues TMA, warp 1 (one lane) issues tcgen05.mma,
+// warps 2-5 run the epilogue from TMEM (warp w reads TMEM lanes 32*(w%4)..+31).
+// Two TMEM accumulators of 128 columns let the epilogue of a tile overlap the MMAs of
+// the next. Every mbarrier wait is bounded (ptx::mbar_wait) and a timeout is reported
+// through the job status instead of hanging.
+#include <cuda.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ptx_sm100.cuh"
+#include "tc_api.h"
+
+namespace icnnm {
+
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int LMAX = 16;             // (tile, offset) pairs per coordinate in the gather
+constexpr int ADJ_STAGES = 4;
+constexpr int CHUNK = 16384;         // one SW128 K-chunk: 128 rows x 128 bytes
+constexpr uint32_t TMEM_COLS = 256;
+constexpr int SMEM_LIMIT = 227 * 1024;
+
+int rup(int x, int a) { return (x + a - 1) / a * a; }
+
+TcGeom make_geom(int k1, int k2, int k3) {
+  TcGeom g{};
+  g.k1 = k1; g.k2 = k2; g.k3 = k3; g.k = k1 * k2 * k3; g.kc = rup(g.k, 16);
+  g.R = k1 * k3; g.R8 = rup(g.R, 8);
+  g.ngrp = k2 * (g.R8 / 8);
+  g.nmma = (g.ngrp + 1) / 2;
+  g.kpad = g.nmma * 16;
+  g.nch_f = (g.kpad + 63) / 64;
+  g.ncopy = std::min(k2, 8);
+  g.nwc = (k2 + 7) / 8;
+  g.Hh = TH + k1 - 1;
+  g.region_bytes = g.Hh * k3 * 16;
+  g.stage_bytes = rup(g.nwc * g.ncopy * g.region_bytes + 8 * 16, 1024);
+  g.nct = (g.k + 127) / 128;
+  g.ntt = (g.k + 127) / 128;
+  g.kcp = rup(g.kc, 64);
+  g.nch_a = g.kcp / 64;
+  g.Hb = TH + k1 - 1;
+  g.Wb = TW + k2 - 1;
+  g.HB = g.Hb * g.Wb * k3;
+  return g;
+}
+
+size_t fwd_smem(const TcGeom& g) { return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + 256; }
+size_t adj_smem(const TcGeom& g) {
+  return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 4 * (size_t)g.HB * 4 + 256;
+}
+
+// Byte offset of forward K-group `grp` (8 taps) inside a halo stage.
+uint32_t group_off(const TcGeom& g, int grp) {
+  const int per = g.R8 / 8;
+  const int sw = grp / per, j = grp % per;
+  return (uint32_t)(((sw / 8) * g.ncopy + sw % 8) * g.region_bytes + j * 128);
+}
+
+struct FwdTab {
+  uint32_t boff[64];
+  uint32_t kstr[64];
+};
+
+struct FwdArgs {
+  Shared sh;
+  TcGeom g;
+  FwdTab tab;
+  int mode;
+};
+
+struct AdjArgs {
+  Shared sh;
+  TcGeom g;
+};
+
+__device__ __forceinline__ uint8_t* align1k(uint8_t* p) {
+  return p + ((1024 - (ptx::smem_u32(p) & 1023)) & 1023);
+}
+
+__device__ __forceinline__ void set_fail(const Shared& sh) {
+  if (sh.njobs > 0) atomicExch(&sh.jobs[0].sc->status, 1);
+}
+
+// ---------------------------------------------------------------------------------
+// Forward pass
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_constant__ FwdArgs a) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = align1k(smraw);
+  const TcGeom& g = a.g;
+  const Shared& sh = a.sh;
+  uint8_t* sA = sm;
+  uint8_t* sH = sm + (size_t)g.nch_f * CHUNK;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + 2 * (size_t)g.stage_bytes);
+  uint64_t* full = bars;        // [2]
+  uint64_t* empty = bars + 2;   // [2]
+  uint64_t* tfull = bars + 4;   // [2]
+  uint64_t* tempty = bars + 6;  // [2]
+  uint64_t* abar = bars + 8;
+  uint64_t* dbar = bars + 9;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 10);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ct = blockIdx.x % g.nct;
+  const int slot = blockIdx.x / g.nct, nslot = gridDim.x / g.nct;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&full[i], 1);
+      ptx::mbar_init(&empty[i], 1);
+      ptx::mbar_init(&tfull[i], 1);
+      ptx::mbar_init(&tempty[i], 4);
+    }
+    ptx::mbar_init(abar, 1);
+    ptx::mbar_init(dbar, 1);
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tslot, TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  // zero rows after the copies of each stage (read by the padded taps, times zero)
+  for (int i = threadIdx.x; i < 2 * 32; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(sH + (i / 32) * g.stage_bytes + g.nwc * g.ncopy * g.region_bytes)[i % 32] = 0u;
+  ptx::fence_proxy_async_smem();
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tbase = *tslot;
+  bool failed = false;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      ptx::mbar_arrive_expect_tx(abar, (uint32_t)g.nch_f * CHUNK);
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.VtImg) + (size_t)ct * g.nch_f * CHUNK;
+      for (int c = 0; c < g.nch_f; ++c) ptx::bulk_g2s(sA + (size_t)c * CHUNK, src + (size_t)c * CHUNK, CHUNK, abar);
+      const uint32_t bytes = (uint32_t)(g.nwc * g.ncopy * g.region_bytes);
+      int it = 0;
+      for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
+        const int s = it & 1;
+        const uint32_t ph = (it >> 1) & 1;
+        if (!ptx::mbar_wait(&empty[s], ph ^ 1)) { failed = true; break; }
+        const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+        const JobDev& J = sh.jobs[jb];
+        const int tile = tg - sh.job_tile0[jb];
+        const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
+        ptx::mbar_arrive_expect_tx(&full[s], bytes);
+        for (int q = 0; q < g.nwc; ++q)
+          ptx::tma_load_4d(sH + (size_t)s * g.stage_bytes + (size_t)q * g.ncopy * g.region_bytes, J.tmapX,
+                           tw * TW + 8 * (g.nwc - 1) - 8 * q, t, th * TH, 0, &full[s]);
+      }
+      // every issued load has landed before the CTA can exit
+      for (int i = (it > 2 ? it - 2 : 0); i < it; ++i)
+        if (!ptx::mbar_wait(&full[i & 1], (i >> 1) & 1)) failed = true;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      if (!ptx::mbar_wait(abar, 0)) failed = true;
+      const uint32_t idesc = ptx::idesc_bf16(128, 128, 0, 1);
+      const uint32_t aB = ptx::smem_u32(sA), hB = ptx::smem_u32(sH);
+      const uint32_t nstride = (uint32_t)g.k3 * 16;
+      int it = 0;
+      for (int tg = slot; !failed && tg < sh.total_tiles; tg += nslot, ++it) {
+        const int s = it & 1, b = it & 1;
+        const uint32_t ph = (it >> 1) & 1;
+        if (!ptx::mbar_wait(&full[s], ph)) { failed = true; break; }
+        if (!ptx::mbar_wait(&tempty[b], ph ^ 1)) { failed = true; break; }
+        ptx::tc_fence_after();
+        const uint32_t d = tbase + (uint32_t)b * 128;
+        const uint32_t hs = hB + (uint32_t)s * g.stage_bytes;
+        for (int i = 0; i < g.nmma; ++i) {
+          const uint64_t ad = ptx::sdesc(aB + (uint32_t)(i >> 2) * CHUNK + (uint32_t)(i & 3) * 32, 16, 1024, 2);
+          const uint64_t bd = ptx::sdesc(hs + a.tab.boff[i], a.tab.kstr[i], nstride, 0);
+          ptx::mma_bf16(d, ad, bd, idesc, i > 0 ? 1u : 0u);
+        }
+        ptx::mma_commit(&empty[s]);
+        ptx::mma_commit(&tfull[b]);
+      }
+      ptx::mma_commit(dbar);
+      if (!ptx::mbar_wait(dbar, 0)) failed = true;
+    }
+  } else {
+    const int q = warp & 3;
+    const int ch = ct * 128 + q * 32 + lane;
+    const int mode = a.mode;
+    int it = 0;
+    for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
+      const int b = it & 1;
+      const uint32_t ph = (it >> 1) & 1;
+      if (!ptx::mbar_wait(&tfull[b], ph)) { failed = true; break; }
+      ptx::tc_fence_after();
+      const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+      const JobDev& J = sh.jobs[jb];
+      const int tile = tg - sh.job_tile0[jb];
+      const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
+      const int h0 = th * TH, w0 = tw * TW;
+      const bool live = ch < sh.kc;
+      const bool real = ch < sh.k;
+      const float Dc = real ? J.D[ch] : 0.f;
+      const float sc = (mode == 3 && real) ? (float)(J.s[ch] / J.sc->theta) : 0.f;
+      __nv_bfloat16* U = reinterpret_cast<__nv_bfloat16*>(J.U);
+      float csum = 0.f, rsum = 0.f;
+      for (int cc = 0; cc < 8; ++cc) {
+        float v[16];
+        ptx::tmem_ld16(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cc * 16, v);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int vox = cc * 16 + e;
+          const int h = h0 + (vox >> 3), w = w0 + (vox & 7);
+          if (!live || h >= J.H || w >= J.W) continue;
+          const size_t idx = (((size_t)t * J.H + h) * J.W + w) * sh.kc + ch;
+          if (mode == 1) {
+            const float u = real ? __bfloat162float(U[idx]) : 0.f;
+            const __nv_bfloat16 ub = __float2bfloat16(fmaf(u, Dc, -v[e]));
+            U[idx] = ub;
+            const float uf = __bfloat162float(ub);
+            csum = fmaf(uf, uf, csum);
+          } else if (mode == 2) {
+            const __nv_bfloat16 ub = __float2bfloat16(-v[e]);
+            U[idx] = ub;
+            const float uf = __bfloat162float(ub);
+            csum = fmaf(uf, uf, csum);
+          } else {
+            const float u = real ? __bfloat162float(U[idx]) : 0.f;
+            const float r = fmaf(u, sc, v[e]);
+            rsum = fmaf(r, r, rsum);
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&tempty[b]);
+      if (mode == 3) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+        if (lane == 0) J.rpart[(size_t)tile * sh.nrp + ct * 4 + q] = rsum;
+      } else if (live) {
+        J.part[(size_t)tile * sh.kc + ch] = csum;
+      }
+    }
+  }
+  if (failed) set_fail(sh);
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tbase, TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint pass
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_constant__ AdjArgs a) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = align1k(smraw);
+  const TcGeom& g = a.g;
+  const Shared& sh = a.sh;
+  uint8_t* sA = sm;
+  uint8_t* sU = sm + (size_t)g.nch_a * CHUNK;
+  float* buf = reinterpret_cast<float*>(sU + (size_t)ADJ_STAGES * CHUNK);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(buf + 4 * (size_t)g.HB);
+  uint64_t* full = bars;                   // [4]
+  uint64_t* empty = bars + 4;              // [4]
+  uint64_t* tfull = bars + 8;              // [2]
+  uint64_t* tempty = bars + 10;            // [2]
+  uint64_t* abar = bars + 12;
+  uint64_t* dbar = bars + 13;
+  uint64_t* sumbar = bars + 14;
+  uint64_t* zbar = bars + 15;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tt = blockIdx.x % g.ntt;
+  const int slot = blockIdx.x / g.ntt, nslot = gridDim.x / g.ntt;
+  const int lo = (int)((long long)sh.total_tiles * slot / nslot);
+  const int hi = (int)((long long)sh.total_tiles * (slot + 1) / nslot);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ADJ_STAGES; ++i) {
+      ptx::mbar_init(&full[i], 1);
+      ptx::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&tfull[i], 1);
+      ptx::mbar_init(&tempty[i], 4);
+    }
+    ptx::mbar_init(abar, 1);
+    ptx::mbar_init(dbar, 1);
+    ptx::mbar_init(sumbar, 4);
+    ptx::mbar_init(zbar, 4);
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tslot, TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  for (int i = threadIdx.x; i < 4 * g.HB; i += blockDim.x) buf[i] = 0.f;
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tbase = *tslot;
+  bool failed = false;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int cnt = 0;
+      for (int tg = lo; tg < hi && !failed; ++tg) {
+        const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+        const JobDev& J = sh.jobs[jb];
+        const int tile = tg - sh.job_tile0[jb];
+        const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
+        for (int c = 0; c < g.nch_a; ++c, ++cnt) {
+          const int s = cnt % ADJ_STAGES;
+          const uint32_t ph = (cnt / ADJ_STAGES) & 1;
+          if (!ptx::mbar_wait(&empty[s], ph ^ 1)) { failed = true; break; }
+          ptx::mbar_arrive_expect_tx(&full[s], CHUNK);
+          ptx::tma_load_4d(sU + (size_t)s * CHUNK, J.tmapU, c * 64, tw * TW, th * TH, t, &full[s]);
+        }
+      }
+      for (int i = (cnt > ADJ_STAGES ? cnt - ADJ_STAGES : 0); i < cnt; ++i)
+        if (!ptx::mbar_wait(&full[i % ADJ_STAGES], (i / ADJ_STAGES) & 1)) failed = true;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = ptx::idesc_bf16(128, 128, 0, 0);
+      const uint32_t aB = ptx::smem_u32(sA), uB = ptx::smem_u32(sU);
+      int cur = -1, cnt = 0, i = 0;
+      uint32_t aph = 0, dph = 0;
+      for (int tg = lo; tg < hi && !failed; ++tg, ++i) {
+        const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+        if (jb != cur) {
+          // the MMAs that read the previous job's image must finish before it is replaced
+          if (cur >= 0) {
+            ptx::mma_commit(dbar);
+            if (!ptx::mbar_wait(dbar, dph)) { failed = true; break; }
+            dph ^= 1;
+          }
+          ptx::mbar_arrive_expect_tx(abar, (uint32_t)g.nch_a * CHUNK);
+          const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.jobs[jb].B2img) + (size_t)tt * g.nch_a * CHUNK;
+          for (int c = 0; c < g.nch_a; ++c) ptx::bulk_g2s(sA + (size_t)c * CHUNK, src + (size_t)c * CHUNK, CHUNK, abar);
+          if (!ptx::mbar_wait(abar, aph)) { failed = true; break; }
+          aph ^= 1;
+          cur = jb;
+        }
+        const int b = i & 1;
+        const uint32_t bph = (i >> 1) & 1;
+        if (!ptx::mbar_wait(&tempty[b], bph ^ 1)) { failed = true; break; }
+        ptx::tc_fence_after();
+        const uint32_t d = tbase + (uint32_t)b * 128;
+        for (int c = 0; c < g.nch_a; ++c, ++cnt) {
+          const int s = cnt % ADJ_STAGES;
+          const uint32_t ph = (cnt / ADJ_STAGES) & 1;
+          if (!ptx::mbar_wait(&full[s], ph)) { failed = true; break; }
+          ptx::tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = ptx::sdesc(aB + (uint32_t)c * CHUNK + kk * 32, 16, 1024, 2);
+            const uint64_t bd = ptx::sdesc(uB + (uint32_t)s * CHUNK + kk * 32, 16, 1024, 2);
+            ptx::mma_bf16(d, ad, bd, idesc, (c | kk) ? 1u : 0u);
+          }
+          ptx::mma_commit(&empty[s]);
+        }
+        if (failed) break;
+        ptx::mma_commit(&tfull[b]);
+      }
+      ptx::mma_commit(dbar);
+      if (!ptx::mbar_wait(dbar, dph)) failed = true;
+    }
+  } else {
+    const int q = warp & 3;
+    const int s = tt * 128 + q * 32 + lane;             // this thread's tap
+    const bool valid = s < sh.k;
+    int base = 0;
+    if (valid) {
+      const int sw = s % g.k2, shh = (s / g.k2) % g.k1, st = s / (g.k1 * g.k2);
+      base = ((g.k3 - 1 - st) * g.Hb + (g.k1 - 1 - shh)) * g.Wb + (g.k2 - 1 - sw);
+    }
+    float* myb = buf + (size_t)q * g.HB;
+    uint32_t sph = 0;
+    int i = 0;
+    for (int tg = lo; tg < hi; ++tg, ++i) {
+      const int b = i & 1;
+      const uint32_t bph = (i >> 1) & 1;
+      if (!ptx::mbar_wait(&tfull[b], bph)) { failed = true; break; }
+      ptx::tc_fence_after();
+      for (int cc = 0; cc < 8; ++cc) {
+        float v[16];
+        ptx::tmem_ld16(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cc * 16, v);
+        ptx::tmem_ld_wait();
+        // Lane (tap) s adds G[s][vox] at base_s + pos(vox). At one column the 32 lanes hit
+        // 32 distinct addresses, but lane A at column e+1 can hit lane B's address of
+        // column e, so the warp steps through the columns with a barrier in between.
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int vox = cc * 16 + e;
+          if (valid) myb[base + (vox >> 3) * g.Wb + (vox & 7)] += v[e];
+          __syncwarp();
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&tempty[b]);
+      // sum the four warp buffers in warp order, write the tile's halo partial, clear
+      if (lane == 0) ptx::mbar_arrive(sumbar);
+      if (!ptx::mbar_wait(sumbar, sph)) { failed = true; break; }
+      const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+      const JobDev& J = sh.jobs[jb];
+      const int tile = tg - sh.job_tile0[jb];
+      float* out = J.G + ((size_t)tile * g.ntt + tt) * g.HB;
+      for (int p = q * 32 + lane; p < g.HB; p += 128) {
+        const float v = ((buf[p] + buf[g.HB + p]) + buf[2 * g.HB + p]) + buf[3 * g.HB + p];
+        out[p] = v;
+        buf[p] = 0.f; buf[g.HB + p] = 0.f; buf[2 * g.HB + p] = 0.f; buf[3 * g.HB + p] = 0.f;
+      }
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(zbar);
+      if (!ptx::mbar_wait(zbar, sph)) { failed = true; break; }
+      sph ^= 1;
+    }
+  }
+  if (failed) set_fail(sh);
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tbase, TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Per-iteration images and gathers
+// ---------------------------------------------------------------------------------
+// A operand of the adjoint: rows = taps of tile tt, K = channels; value bf16(V[s][c] D[c]).
+// SW128 K-major: 16-byte unit j of row r sits at unit j ^ (r % 8) of the 128-byte row.
+__global__ void build_B2_kernel(Shared sh, TcGeom g) {
+  const JobDev& J = sh.jobs[blockIdx.x];
+  const int tt = blockIdx.y / g.nch_a, c = blockIdx.y % g.nch_a;
+  uint8_t* img = reinterpret_cast<uint8_t*>(J.B2img) + ((size_t)tt * g.nch_a + c) * CHUNK;
+  for (int u = threadIdx.x; u < 128 * 8; u += blockDim.x) {
+    const int r = u >> 3, j = u & 7;
+    const int s = tt * 128 + r;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int ch = c * 64 + j * 8 + e;
+      const float x = (s < sh.k && ch < sh.k) ? sh.Vf[(size_t)s * sh.kc + ch] * J.D[ch] : 0.f;
+      v[e] = __float2bfloat16(x);
+    }
+    *reinterpret_cast<uint4*>(img + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) * 16)) =
+        *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// Xc[c][tp][hp][wp] = bf16(src[(tp - (k3-1)) mod T][(hp - (k1-1)) mod H][(wp - 8(nwc-1) - c) mod W])
+__global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
+  const JobDev& J = sh.jobs[blockIdx.y];
+  const float* src = from_L ? J.L : J.X;
+  const long long nunits = (long long)g.ncopy * J.xTp * J.xHp * (J.xWp / 8);
+  const int pw = 8 * (g.nwc - 1);
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < nunits;
+       u += (long long)gridDim.x * blockDim.x) {
+    const int wu = (int)(u % (J.xWp / 8));
+    long long r = u / (J.xWp / 8);
+    const int hp = (int)(r % J.xHp);
+    r /= J.xHp;
+    const int tp = (int)(r % J.xTp);
+    const int c = (int)(r / J.xTp);
+    const long long rowb = ((long long)wrapi(tp - (g.k3 - 1), J.T) * J.H + wrapi(hp - (g.k1 - 1), J.H)) * J.W;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(src[rowb + wrapi(wu * 8 + e - pw - c, J.W)]);
+    *reinterpret_cast<uint4*>(J.Xc + (((long long)c * J.xTp + tp) * J.xHp + hp) * J.xWp + wu * 8) =
+        *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// L-update from the col2im partials: Delta_j = sum of the halo partials of every tile
+// whose halo covers voxel j (taps tiles innermost), in a fixed order; then the same
+// projection as the FP32 path.
+__global__ void gather_tc_kernel(Shared sh, TcGeom g) {
+  const int tile_g = blockIdx.x;
+  const int jb = job_of_tile(sh.job_tile0, sh.njobs, tile_g);
+  const JobDev& J = sh.jobs[jb];
+  const int tile = tile_g - sh.job_tile0[jb];
+  const int tw0 = tile % J.ntw, th0 = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
+  const int h = th0 * TH + threadIdx.x / TW, w = tw0 * TW + threadIdx.x % TW;
+  __shared__ float red[TILE_VOX];
+  float l2 = 0.f;
+  if (h < J.H && w < J.W) {
+    const int* hcnt = J.glist;
+    const int* hent = hcnt + J.H;
+    const int* wcnt = hent + (size_t)J.H * LMAX;
+    const int* went = wcnt + J.W;
+    const int nh = hcnt[h], nw = wcnt[w];
+    float d = 0.f;
+    for (int st = 0; st < g.k3; ++st) {
+      const int tf = wrapi(t + st, J.T);
+      const int bt = g.k3 - 1 - st;
+      for (int ih = 0; ih < nh; ++ih) {
+        const int eh = hent[h * LMAX + ih];
+        const int th = eh >> 8, bh = eh & 255;
+        for (int iw = 0; iw < nw; ++iw) {
+          const int ew = went[w * LMAX + iw];
+          const int tw = ew >> 8, bw = ew & 255;
+          const size_t tl = ((size_t)tf * J.nth + th) * J.ntw + tw;
+          const size_t off = ((size_t)bt * g.Hb + bh) * g.Wb + bw;
+          for (int k = 0; k < g.ntt; ++k) d += J.G[(tl * g.ntt + k) * g.HB + off];
+        }
+      }
+    }
+    const long long v = ((long long)t * J.H + h) * J.W + w;
+    const float Ln = l_update(J, sh.k, v, d);
+    l2 = Ln * Ln;
+  }
+  red[threadIdx.x] = l2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < TILE_VOX; ++i) s += red[i];
+    J.lpart[tile] = s;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------
+bool tc_supported(int k1, int k2, int k3, std::string* why) {
+  const TcGeom g = make_geom(k1, k2, k3);
+  auto no = [&](const char* m) { if (why) *why = m; return false; };
+  if (g.k > 512) return no("k > 512");
+  if (k2 > 16) return no("k2 > 16");
+  if (g.nmma > 64) return no("padded forward K > 1024");
+  if (g.Hh > 256 || k3 > 256) return no("halo box too tall");
+  if (fwd_smem(g) > SMEM_LIMIT) return no("forward shared memory exceeds 227 KiB");
+  if (adj_smem(g) > SMEM_LIMIT) return no("adjoint shared memory exceeds 227 KiB");
+  if (!encoder()) return no("cuTensorMapEncodeTiled unavailable");
+  return true;
+}
+
+cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out) {
+  TcGeom g = make_geom(k1, k2, k3);
+  g.kc = kc;
+  out->g = g;
+  const int k = g.k;
+  const size_t per = (size_t)g.nch_f * CHUNK;
+  std::vector<uint8_t> img((size_t)g.nct * per, 0);
+  const int per8 = g.R8 / 8;
+  for (int ct = 0; ct < g.nct; ++ct)
+    for (int r = 0; r < 128; ++r) {
+      const int ch = ct * 128 + r;
+      if (ch >= k) continue;
+      for (int kap = 0; kap < g.kpad; ++kap) {
+        const int grp = kap / 8, rin = kap % 8;
+        if (grp >= g.ngrp) continue;
+        const int sw = grp / per8, rr = (grp % per8) * 8 + rin;
+        if (rr >= g.R) continue;
+        const int u = g.R - 1 - rr, sh = u / k3, st = u % k3;
+        const int s = (st * k1 + sh) * k2 + sw;
+        const __nv_bfloat16 b = __float2bfloat16((float)V64[(size_t)ch * k + s]);
+        const int chunk = kap / 64, col = kap % 64;
+        const size_t off = (size_t)ct * per + (size_t)chunk * CHUNK + (r / 8) * 1024 + (r % 8) * 128 +
+                           (((col / 8) ^ (r % 8)) * 16) + (col % 8) * 2;
+        memcpy(&img[off], &b, 2);
+      }
+    }
+  for (int i = 0; i < 64; ++i) { out->boff[i] = 0; out->kstr[i] = 0; }
+  for (int i = 0; i < g.nmma; ++i) {
+    out->boff[i] = group_off(g, 2 * i);
+    out->kstr[i] = (2 * i + 1 < g.ngrp) ? group_off(g, 2 * i + 1) - group_off(g, 2 * i) : 0;
+  }
+  cudaError_t e = cudaMalloc(&out->VtImg, img.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(out->VtImg, img.data(), img.size(), cudaMemcpyHostToDevice);
+}
+
+void tc_free_vdata(TcVData* v) {
+  if (v->VtImg) cudaFree(v->VtImg);
+  v->VtImg = nullptr;
+}
+
+int tc_nrp(int k) { return 4 * ((k + 127) / 128); }
+
+static void xc_dims(const TcGeom& g, int H, int W, int T, int& Tp, int& Hp, int& Wp) {
+  const int nth = (H + TH - 1) / TH, ntw = (W + TW - 1) / TW;
+  Tp = T + g.k3 - 1;
+  Hp = nth * TH + g.k1 - 1;
+  Wp = ntw * TW + 8 * (g.nwc - 1);
+}
+
+size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g) {
+  int Tp, Hp, Wp;
+  xc_dims(g, H, W, T, Tp, Hp, Wp);
+  const int ntiles = ((H + TH - 1) / TH) * ((W + TW - 1) / TW) * T;
+  size_t b = 0;
+  auto add = [&](size_t n) { b += (n + 255) / 256 * 256; };
+  add((size_t)g.ncopy * Tp * Hp * Wp * 2);             // Xc
+  add((size_t)ntiles * g.ntt * g.HB * 4);              // col2im partials
+  add((size_t)g.ntt * g.nch_a * CHUNK);                // V D images
+  add(2 * sizeof(CUtensorMap));                        // TMA maps
+  add((size_t)(H + W) * (1 + LMAX) * 4);               // gather lists
+  return b;
+}
+
+cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, size_t total) {
+  const TcGeom& g = v.g;
+  auto take = [&](size_t n) { void* p = base + off; off += (n + 255) / 256 * 256; return p; };
+  int Tp, Hp, Wp;
+  xc_dims(g, d->H, d->W, d->T, Tp, Hp, Wp);
+  d->xTp = Tp; d->xHp = Hp; d->xWp = Wp;
+  d->Xc = (__nv_bfloat16*)take((size_t)g.ncopy * Tp * Hp * Wp * 2);
+  d->G = (float*)take((size_t)d->ntiles * g.ntt * g.HB * 4);
+  d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * CHUNK);
+  CUtensorMap* tm = (CUtensorMap*)take(2 * sizeof(CUtensorMap));
+  int* gl = (int*)take((size_t)(d->H + d->W) * (1 + LMAX) * 4);
+  if (off > total) return cudaErrorInvalidValue;
+  EncodeTiledFn enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap hm[2];
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)Wp, (cuuint64_t)Tp, (cuuint64_t)Hp, (cuuint64_t)g.ncopy};
+    cuuint64_t str[3] = {(cuuint64_t)Hp * Wp * 2, (cuuint64_t)Wp * 2, (cuuint64_t)Tp * Hp * Wp * 2};
+    cuuint32_t box[4] = {8, (cuuint32_t)g.k3, (cuuint32_t)g.Hh, (cuuint32_t)g.ncopy}, es[4] = {1, 1, 1, 1};
+    if (enc(&hm[0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->Xc, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)g.kc, (cuuint64_t)d->W, (cuuint64_t)d->H, (cuuint64_t)d->T};
+    cuuint64_t str[3] = {(cuuint64_t)g.kc * 2, (cuuint64_t)d->W * g.kc * 2, (cuuint64_t)d->H * d->W * g.kc * 2};
+    cuuint32_t box[4] = {64, TW, TH, 1}, es[4] = {1, 1, 1, 1};
+    if (enc(&hm[1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->U, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaMemcpy(tm, hm, sizeof hm, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  d->tmapX = &tm[0];
+  d->tmapU = &tm[1];
+  // gather lists: for each h, the (tile row th, halo row bh) with th*TH - (k1-1) + bh = h (mod H)
+  std::vector<int> hl((size_t)(d->H + d->W) * (1 + LMAX), 0);
+  int* hcnt = hl.data();
+  int* hent = hcnt + d->H;
+  int* wcnt = hent + (size_t)d->H * LMAX;
+  int* went = wcnt + d->W;
+  for (int th = 0; th < d->nth; ++th)
+    for (int bh = 0; bh < g.Hb; ++bh) {
+      const int h = ((th * TH - (g.k1 - 1) + bh) % d->H + d->H) % d->H;
+      if (hcnt[h] >= LMAX) return cudaErrorNotSupported;
+      hent[h * LMAX + hcnt[h]++] = (th << 8) | bh;
+    }
+  for (int tw = 0; tw < d->ntw; ++tw)
+    for (int bw = 0; bw < g.Wb; ++bw) {
+      const int w = ((tw * TW - (g.k2 - 1) + bw) % d->W + d->W) % d->W;
+      if (wcnt[w] >= LMAX) return cudaErrorNotSupported;
+      went[w * LMAX + wcnt[w]++] = (tw << 8) | bw;
+    }
+  e = cudaMemcpy(gl, hl.data(), hl.size() * 4, cudaMemcpyHostToDevice);
+  d->glist = gl;
+  return e;
+}
+
+cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st) {
+  prepare_X_kernel<<<dim3(256, sh.njobs), 256, 0, st>>>(sh, v.g, from_L);
+  return cudaGetLastError();
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st) {
+  FwdArgs a;
+  a.sh = sh;
+  a.g = v.g;
+  for (int i = 0; i < 64; ++i) { a.tab.boff[i] = v.boff[i]; a.tab.kstr[i] = v.kstr[i]; }
+  a.mode = mode;
+  const size_t smem = fwd_smem(v.g);
+  cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int per = std::max(1, std::min(num_sms() / v.g.nct, (sh.total_tiles + 0)));
+  fwd_tc_kernel<<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st) {
+  build_B2_kernel<<<dim3(sh.njobs, v.g.ntt * v.g.nch_a), 256, 0, st>>>(sh, v.g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  AdjArgs a;
+  a.sh = sh;
+  a.g = v.g;
+  const size_t smem = adj_smem(v.g);
+  cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int per = std::max(1, std::min(num_sms() / v.g.ntt, sh.total_tiles));
+  adj_tc_kernel<<<per * v.g.ntt, TC_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st) {
+  gather_tc_kernel<<<sh.total_tiles, TILE_VOX, 0, st>>>(sh, v.g);
+  return cudaGetLastError();
+}
+
+}  // namespace icnnm

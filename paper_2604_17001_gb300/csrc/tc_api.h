@@ -1,0 +1,48 @@
+// Host interface of the BF16 tcgen05 path (k_tc.cu).
+#pragma once
+#include <string>
+#include "icnnm_internal.h"
+
+namespace icnnm {
+
+// Geometry of the tensor-core passes, fixed by the kernel dims.
+struct TcGeom {
+  int k1, k2, k3, k, kc;
+  // forward pass E^T = V^T P(X)^T (M = 128 channels, N = 128 voxels, K = taps)
+  int R, R8;        // taps per w-run (k1*k3) and the run rounded up to 8 rows
+  int ngrp, nmma;   // K-groups of 8 taps, MMAs of K = 16
+  int kpad;         // nmma * 16
+  int nch_f;        // 64-wide SW128 chunks of the forward A image
+  int ncopy, nwc;   // w-shifted copies of the operand (min(k2, 8)) and 8-wide w-chunks
+  int Hh;           // halo height TH + k1 - 1
+  int region_bytes; // one copy's halo: Hh * k3 rows of 16 bytes
+  int stage_bytes;  // one halo stage (all copies and w-chunks + 8 zero rows), 1024-aligned
+  int nct;          // channel tiles of 128
+  // adjoint pass G^T = (V D) U^T (M = 128 taps, N = 128 voxels, K = channels)
+  int ntt;          // tap tiles of 128
+  int kcp;          // channels rounded up to 64
+  int nch_a;        // 64-wide SW128 chunks of the adjoint A image
+  int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*k3
+};
+
+// Per-V device data of the tensor-core path.
+struct TcVData {
+  TcGeom g{};
+  __nv_bfloat16* VtImg = nullptr;   // nct forward A images, nch_f * 16 KiB each
+  uint32_t boff[64];                // forward: byte offset of each MMA's first K-group
+  uint32_t kstr[64];                // forward: byte distance to its second K-group
+};
+
+bool tc_supported(int k1, int k2, int k3, std::string* why);
+cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out);
+void tc_free_vdata(TcVData* v);
+size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g);
+// Carve the tensor-core buffers of a job from its allocation and encode its TMA maps.
+cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, size_t total);
+int tc_nrp(int k);
+cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st);
+cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st);
+cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st);
+cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st);
+
+}  // namespace icnnm

@@ -1,0 +1,189 @@
+"""GPU parity: libicnnm (through the C ABI) against the FP64 oracle on the same seeded
+inputs. Tolerances: relative L2 <= 1e-5 for the FP32 path and <= 1e-3 for the BF16
+path; observed entries bit-exact (lambda = inf)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import icnnm_oracle as O
+from paper_2604_17001_gb300 import icnnm, synth
+from tests.gpu_util import need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16": 1e-3}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = icnnm.Context(0)
+    yield c
+    c.close()
+
+
+def case(dims, kdims, frac=None, last=None, seed=7, nref=3, vdims=None):
+    H, W, T = dims
+    L0 = synth.video(H, W, T, seed=seed)
+    if last is not None:
+        mask = synth.mask_last_frames(H, W, T, last)
+    else:
+        mask = synth.mask_uniform(H, W, T, frac, seed=seed + 1)
+    M = np.where(mask.astype(bool), L0, 0).astype(np.float32)
+    vd = vdims or dims
+    refs = [synth.video(vd[0], vd[1], vd[2], seed=seed + 10 + j) for j in range(nref)]
+    V, _ = O.learn_V(refs, kdims)
+    return M, mask, V, L0
+
+
+CASES = [
+    # (dims H,W,T), kernel, mask, iterations
+    ((32, 32, 8), (5, 5, 3), dict(frac=0.5), 100),          # completion workload shape
+    ((21, 13, 5), (3, 4, 2), dict(frac=0.6), 40),           # ragged vs the 8x16 tile
+    ((24, 16, 10), (9, 9, 5), dict(last=2), 40),            # k = 405, prediction mask
+    ((37, 29, 1), (5, 5, 1), dict(frac=0.5), 60),           # 2-D image
+    ((16, 40, 6), (7, 7, 3), dict(frac=0.4), 50),           # k = 147
+]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("dims,kdims,mk,iters", CASES)
+def test_solve_matches_oracle(ctx, prec, dims, kdims, mk, iters):
+    M, mask, V, _ = case(dims, kdims, **mk)
+    Lo, so = O.icnnm_solve(M, mask, V, kdims, max_iters=iters)
+    try:
+        L, st = ctx.icnnm_solve(M, mask, V, kdims, max_iters=iters, prec=prec)
+    except icnnm.ICNNMError as e:
+        if e.status == icnnm.EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    e = rel(L, Lo)
+    assert e <= TOL[prec], (prec, dims, kdims, e)
+    msk = mask.astype(bool)
+    assert np.array_equal(L[msk], M[msk])                      # P_Omega(L) = P_Omega(M) exactly
+    assert st["iters"] == iters
+    assert abs(st["objective"] - so["objective"]) <= 10 * TOL[prec] * so["objective"]
+    assert abs(st["theta"] - so["theta"]) <= 1e-6 * so["theta"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_penalised_lambda_1000(ctx, prec):
+    # Eq. (admm) with the paper's lambda = 1000: observed entries are not pinned exactly
+    M, mask, V, _ = case((24, 24, 6), (5, 5, 3), frac=0.5)
+    Lo, _ = O.icnnm_solve(M, mask, V, (5, 5, 3), lam=1000.0, max_iters=60)
+    try:
+        L, _ = ctx.icnnm_solve(M, mask, V, (5, 5, 3), lam=1000.0, max_iters=60, prec=prec)
+    except icnnm.ICNNMError as e:
+        if e.status == icnnm.EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    assert rel(L, Lo) <= TOL[prec]
+
+
+def test_tolerance_stopping_matches_oracle(ctx):
+    M, mask, V, _ = case((32, 24, 6), (5, 5, 3), frac=0.5)
+    Lo, so = O.icnnm_solve(M, mask, V, (5, 5, 3), max_iters=300, tol=1e-4, check_every=10)
+    L, st = ctx.icnnm_solve(M, mask, V, (5, 5, 3), max_iters=300, tol=1e-4, check_every=10, prec="fp32")
+    assert st["iters"] == so["iters"] < 300
+    assert rel(L, Lo) <= TOL["fp32"]
+    assert abs(st["residual"] - so["residual"]) <= 2e-2 * so["residual"]   # FP32 sums of a cancelling quantity
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_equals_single_bitwise(ctx, prec):
+    # Uneven problems stepped together give exactly the results of solving each alone
+    # (every reduction has a fixed order that does not depend on the batch).
+    kd = (5, 5, 3)
+    probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 16, 8), 0.5, 1), ((16, 48, 5), 0.3, 2),
+                                                         ((24, 24, 3), 0.7, 3)]]
+    V = probs[0][2]
+    try:
+        outs, stats = ctx.icnnm_solve_batch([p[0] for p in probs], [p[1] for p in probs], V, kd,
+                                            max_iters=30, prec=prec)
+    except icnnm.ICNNMError as e:
+        if e.status == icnnm.EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    for (M, mask, _, _), Lb in zip(probs, outs):
+        Ls, _ = ctx.icnnm_solve(M, mask, V, kd, max_iters=30, prec=prec)
+        assert np.array_equal(Lb, Ls)
+        Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=30)
+        assert rel(Lb, Lo) <= TOL[prec]
+
+
+def test_device_pointers_and_torch_tensors(ctx):
+    import torch
+    M, mask, V, _ = case((32, 32, 4), (3, 3, 2), frac=0.5)
+    Lh, _ = ctx.icnnm_solve(M, mask, V, (3, 3, 2), max_iters=20, prec="fp32")
+    Md, kd_ = torch.from_numpy(M).cuda(), torch.from_numpy(mask).cuda()
+    Ld, _ = ctx.icnnm_solve(Md, kd_, torch.from_numpy(V).cuda(), (3, 3, 2), max_iters=20, prec="fp32")
+    assert np.array_equal(Ld.cpu().numpy(), Lh)
+
+
+def test_invalid_inputs_are_rejected(ctx):
+    M, mask, V, _ = case((16, 16, 4), (3, 3, 2), frac=0.5)
+    with pytest.raises(icnnm.ICNNMError) as e:
+        ctx.icnnm_solve(M, mask, V, (17, 3, 2))                # kernel larger than the tensor
+    assert e.value.status == icnnm.EINVAL
+    with pytest.raises(icnnm.ICNNMError) as e:
+        ctx.icnnm_solve(M, mask, V * 1.01, (3, 3, 2))          # V not orthonormal
+    assert e.value.status == icnnm.EINVAL
+    with pytest.raises(icnnm.ICNNMError) as e:
+        ctx.icnnm_solve(M, np.zeros_like(mask), V, (3, 3, 2))  # empty Omega
+    assert e.value.status == icnnm.EINVAL
+    Mn = M.copy()
+    Mn.reshape(-1)[np.flatnonzero(mask.ravel())[0]] = np.nan
+    with pytest.raises(icnnm.ICNNMError) as e:
+        ctx.icnnm_solve(Mn, mask, V, (3, 3, 2))                # non-finite observed entry
+    assert e.value.status == icnnm.EINVAL
+    with pytest.raises(icnnm.ICNNMError) as e:
+        ctx.icnnm_solve(M, mask, V, (3, 3, 2), rho=0.5)
+    assert e.value.status == icnnm.EINVAL
+
+
+def test_budget_enforced():
+    need_gpu()
+    M, mask, V, _ = case((64, 64, 16), (5, 5, 3), frac=0.5)
+    with icnnm.Context(0, hbm_budget_bytes=1 << 20) as c:
+        with pytest.raises(icnnm.ICNNMError) as e:
+            c.icnnm_solve(M, mask, V, (5, 5, 3), max_iters=2, prec="fp32")
+        assert e.value.status == icnnm.ENOMEM
+
+
+def test_learn_V_matches_oracle(ctx):
+    kd = (5, 5, 3)
+    refs = [synth.video(32, 32, 8, seed=s) for s in range(1001, 1005)] + [synth.video(16, 24, 6, seed=77)]
+    Vo, eo = O.learn_V(refs, kd)
+    G = O.gram(refs, kd)
+    V, e = ctx.icnnm_learn_V(refs, kd)
+    k = 75
+    assert np.max(np.abs(e - eo)) <= 2e-6 * eo[0]                    # FP32 products, FP64 sums
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)       # FP64 Jacobi
+    recon = (V * e[None, :]) @ V.T
+    assert np.linalg.norm(recon - G) <= 2e-6 * np.linalg.norm(G)
+    # well-separated leading eigenvectors agree up to the canonical sign (identical)
+    gaps = np.abs(np.diff(eo))
+    for i in range(8):
+        gap = min(gaps[i], gaps[i - 1] if i > 0 else np.inf)
+        if gap > 1e-3 * eo[0]:
+            assert abs(abs(V[:, i] @ Vo[:, i]) - 1) <= 1e-6, i   # the sign rule can tie
+    for i in range(k):
+        assert V[np.argmax(np.abs(V[:, i])), i] > 0
+
+
+def test_serving_submit_poll_equals_solve(ctx):
+    kd = (5, 5, 3)
+    probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 16, 8), 0.5, 11), ((16, 48, 5), 0.3, 12),
+                                                         ((24, 24, 3), 0.7, 13), ((32, 32, 6), 0.5, 14)]]
+    V = probs[0][2]
+    ids = [ctx.icnnm_submit(M, mask, V, kd, max_iters=25, prec="fp32") for M, mask, _, _ in probs]
+    for (M, mask, _, _), jid in zip(probs, ids):
+        L = np.zeros_like(M)
+        st, stats = ctx.icnnm_wait(jid, L_out=L, timeout_ms=120000)
+        assert st == icnnm.OK and stats["iters"] == 25
+        Ls, _ = ctx.icnnm_solve(M, mask, V, kd, max_iters=25, prec="fp32")
+        assert np.array_equal(L, Ls)
+    with pytest.raises(icnnm.ICNNMError) as e:
+        ctx.icnnm_poll(ids[0])
+    assert e.value.status == icnnm.ENOTFOUND
