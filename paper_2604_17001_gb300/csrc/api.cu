@@ -107,7 +107,7 @@ size_t job_bytes(int H, int W, int T, int k, int kc, int prec, int nrp, const Tc
   add(m);                // mask
   add(m * 4);            // L
   add(m * 4);            // X
-  add((size_t)ntiles * kc * 4);   // part
+  add((size_t)ntiles * PROW * kc * 4);   // part
   add((size_t)ntiles * nrp * 4);  // rpart
   add((size_t)ntiles * 4);        // lpart
   add((size_t)NSEG * kc * 8);     // colseg
@@ -330,7 +330,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   d.mask = (const uint8_t*)take(m);
   d.L = (float*)take(m * 4);
   d.X = (float*)take(m * 4);
-  d.part = (float*)take((size_t)d.ntiles * kc * 4);
+  d.part = (float*)take((size_t)d.ntiles * PROW * kc * 4);
   d.rpart = (float*)take((size_t)d.ntiles * nrp * 4);
   d.lpart = (float*)take((size_t)d.ntiles * 4);
   d.colseg = (double*)take((size_t)NSEG * kc * 8);
@@ -345,7 +345,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   }
   CK(cudaMemsetAsync(d.sc, 0, sizeof(JobScal), c->stream));
   CK(cudaMemsetAsync(d.U, 0, (size_t)m * kc * (j.p.prec == ICNNM_FP32 ? 4 : 2), c->stream));
-  CK(cudaMemsetAsync(d.part, 0, (size_t)d.ntiles * kc * 4, c->stream));
+  CK(cudaMemsetAsync(d.part, 0, (size_t)d.ntiles * PROW * kc * 4, c->stream));
   CK(cudaMemsetAsync(d.rpart, 0, (size_t)d.ntiles * nrp * 4, c->stream));
   // inputs
   const float* srcM = j.srcM ? j.srcM : j.hM.data();

@@ -24,6 +24,7 @@ constexpr int TW = 8;
 constexpr int TH = 16;
 constexpr int TILE_VOX = TW * TH;
 constexpr int NSEG = 32;          // tile segments of the first column-reduction stage
+constexpr int PROW = 4;           // column-partial rows per tile (one per group of 32 voxels)
 
 // Mutable per-job scalars (device memory). Kept apart from JobDev so that a job can
 // be listed in several launch lists without its state diverging.
@@ -53,7 +54,7 @@ struct JobDev {
   __nv_bfloat16* Xc;    // BF16 path: wrap-padded, w-shifted copies of the operand
   void* U;              // m x kc shifted multiplier, row-major [voxel][channel]:
                         //   FP32 (FP32 path) or BF16 (BF16 path)
-  float* part;          // per-tile column partial sums of ||.||^2: [ntiles][kc]
+  float* part;          // column partial sums of ||.||^2: [ntiles][PROW][kc]
   float* rpart;         // per-tile residual partials: [ntiles][nrp]
   float* lpart;         // per-tile ||L'||^2 partials: [ntiles]
   double* colseg;       // first-stage column sums: [NSEG][kc]

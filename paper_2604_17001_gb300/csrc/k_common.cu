@@ -40,9 +40,9 @@ __global__ void init_L_kernel(Shared sh) {
   if (J.X) J.X[v] = x;
 }
 
-// First reduction stage: colseg[seg][c] = sum over the tiles of segment seg of
-// part[tile][c], in FP64; warp w adds tiles lo+w, lo+w+8, ... in increasing order and
-// the 8 warp sums are combined in warp order. Block = (job, 32 channels, segment).
+// First reduction stage: colseg[seg][c] = sum over the partial rows (PROW per tile) of
+// segment seg of part[row][c], in FP64; warp w adds rows lo+w, lo+w+8, ... in increasing
+// order and the 8 warp sums are combined in warp order. Block = (job, 32 channels, segment).
 // With `advance`, one block per job moves theta to theta_next and counts the
 // iteration (every kernel of the iteration that reads theta has run by then).
 __global__ void reduce_cols_kernel(Shared sh, int advance) {
@@ -50,11 +50,21 @@ __global__ void reduce_cols_kernel(Shared sh, int advance) {
   const int c = blockIdx.y * 32 + (threadIdx.x & 31);
   const int warp = threadIdx.x >> 5;
   const int seg = blockIdx.z;
-  const int lo = (int)((long long)J.ntiles * seg / NSEG);
-  const int hi = (int)((long long)J.ntiles * (seg + 1) / NSEG);
+  const int nrows = J.ntiles * PROW;
+  const int lo = (int)((long long)nrows * seg / NSEG);
+  const int hi = (int)((long long)nrows * (seg + 1) / NSEG);
   double acc = 0.0;
-  if (c < sh.kc)
-    for (int t = lo + warp; t < hi; t += 8) acc += (double)J.part[(long long)t * sh.kc + c];
+  if (c < sh.kc) {
+    const float* p = J.part + c;
+    int t = lo + warp;
+    // four independent loads in flight per step; the sum order is fixed by the tile index
+    for (; t + 24 < hi; t += 32) {
+      const float a0 = p[(long long)t * sh.kc], a1 = p[(long long)(t + 8) * sh.kc];
+      const float a2 = p[(long long)(t + 16) * sh.kc], a3 = p[(long long)(t + 24) * sh.kc];
+      acc += (double)a0; acc += (double)a1; acc += (double)a2; acc += (double)a3;
+    }
+    for (; t < hi; t += 8) acc += (double)p[(long long)t * sh.kc];
+  }
   __shared__ double red[8][32];
   red[warp][threadIdx.x & 31] = acc;
   __syncthreads();
@@ -70,8 +80,12 @@ __global__ void reduce_cols_kernel(Shared sh, int advance) {
 }
 
 __device__ __forceinline__ double colsq_of(const JobDev& J, int kc, int c) {
+  double v[NSEG];
+#pragma unroll
+  for (int seg = 0; seg < NSEG; ++seg) v[seg] = J.colseg[(long long)seg * kc + c];
   double q = 0.0;
-  for (int seg = 0; seg < NSEG; ++seg) q += J.colseg[(long long)seg * kc + c];
+#pragma unroll
+  for (int seg = 0; seg < NSEG; ++seg) q += v[seg];
   return q;
 }
 
@@ -80,13 +94,14 @@ __device__ __forceinline__ double colsq_of(const JobDev& J, int kc, int c) {
 // threshold 1/theta applied to -U/theta), D_c = 1 - s_c; theta' = min(rho theta, theta_max).
 __global__ void scalars_kernel(Shared sh) {
   const JobDev& J = sh.jobs[blockIdx.x];
-  for (int c = threadIdx.x; c < sh.kc; c += blockDim.x) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c < sh.kc) {
     const double n = sqrt(colsq_of(J, sh.kc, c));
     const double sc = (c < sh.k && n > 1.0) ? 1.0 - 1.0 / n : 0.0;
     J.s[c] = (float)sc;
     J.D[c] = (c < sh.k) ? (float)(1.0 - sc) : 0.f;
   }
-  if (threadIdx.x == 0) J.sc->theta_next = fmin(J.rho * J.sc->theta, J.theta_max);
+  if (blockIdx.y == 0 && threadIdx.x == 0) J.sc->theta_next = fmin(J.rho * J.sc->theta, J.theta_max);
 }
 
 // theta0 = 1 / max_c ||A_k(P_Omega M) V_c|| unless the caller gives one (a reading: the
@@ -197,7 +212,7 @@ cudaError_t launch_reduce_cols(const Shared& sh, int advance, cudaStream_t st) {
 }
 
 cudaError_t launch_scalars(const Shared& sh, cudaStream_t st) {
-  scalars_kernel<<<sh.njobs, 256, 0, st>>>(sh);
+  scalars_kernel<<<dim3(sh.njobs, (sh.kc + 127) / 128), 128, 0, st>>>(sh);
   return cudaGetLastError();
 }
 

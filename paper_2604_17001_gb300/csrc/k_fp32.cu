@@ -119,11 +119,14 @@ fwd_fp32_kernel(Shared sh, int mode, const float* __restrict__ dummy) {
 #pragma unroll
     for (int a = 0; a < 8; ++a) sRed[vr * F_CT + cg * 8 + a] = csum[a];
     __syncthreads();
-    if (threadIdx.x < F_CT) {
+    // partial row q covers voxel rows 4q..4q+3 (32 voxels), the same grouping as the
+    // tensor-core path
+    for (int i = threadIdx.x; i < PROW * F_CT; i += F_THREADS) {
+      const int q = i / F_CT, cl = i % F_CT;
       float sum = 0.f;
-      for (int r = 0; r < 16; ++r) sum += sRed[r * F_CT + threadIdx.x];
-      const int c = c0 + threadIdx.x;
-      if (c < kc) J.part[(long long)tile * kc + c] = sum;
+      for (int r = 4 * q; r < 4 * q + 4; ++r) sum += sRed[r * F_CT + cl];
+      const int c = c0 + cl;
+      if (c < kc) J.part[((long long)tile * PROW + q) * kc + c] = sum;
     }
   } else {
     sRed[threadIdx.x] = rsum;

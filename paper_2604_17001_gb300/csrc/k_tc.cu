@@ -1,32 +1,34 @@
 // BF16 tensor-core path (sm_103a: tcgen05 MMA with TMEM accumulators, TMA loads).
 //
-// Forward pass  E^T = V^T A_k(X)^T  (row i of A_k(X) holds X[i - s] for every tap s,
+// Forward pass  E = A_k(X) V  (row i of A_k(X) holds X[i - s] for every tap s,
 // Sec. II-B Eq. ak), fused with U' = U D - E and the per-tile partials of ||U'_c||^2.
-//   M = 128 channels, N = 128 voxels (an 8w x 16h tile of one frame), K = taps.
-//   A = V^T (one channel tile per persistent CTA, resident in shared memory, SW128
-//   K-major). B = A_k(X)^T is never formed: the operand is kept as ncopy = min(k2, 8)
+//   M = 128 voxels (an 8w x 16h tile of one frame), N = 128 channels, K = taps.
+//   B = V^T (one channel tile per persistent CTA, resident in shared memory, SW128
+//   K-major). A = A_k(X) is never formed: the operand is kept as ncopy = min(k2, 8)
 //   bf16 copies of X, copy c shifted by c along w and wrap-padded, so that every
 //   8-voxel row segment of every tap starts on a 16-byte boundary. A TMA box of all
 //   copies (halo of the tile: Hh = TH + k1 - 1 rows x k3 frames x 8 w) lands in shared
 //   memory as rows of 16 bytes indexed rho = h*k3 + t. For a fixed w-tap sw the taps
 //   (sh, st) then sit at rows rho = g*k3 + r with r = k1*k3 - 1 - (sh*k3 + st), so the
-//   B operand of each MMA is an MN-major no-swizzle matrix whose core matrices overlap:
-//   N-groups (output rows g) are k3 rows apart, K-rows are consecutive rows.
+//   A operand of each MMA is an MN-major no-swizzle matrix whose core matrices overlap:
+//   M-groups (output rows g) are k3 rows apart, K-rows are consecutive rows.
 //   The taps are therefore ordered (sw, then r), each sw-run padded to 8 rows (the
 //   padded taps have zero rows in V^T).
 //
 // Adjoint pass  G^T = (V D) U^T, then col2im  Delta_j = sum_s G[j + s, s]  (the adjoint
 // of Eq. ak), deterministic:
-//   M = 128 taps (the V D image of the job, SW128 K-major), N = 128 voxels (the U tile
-//   by TMA, SW128 K-major, zero-filled beyond the tensor), K = channels.
+//   M = 128 voxels (the U tile by TMA, SW128 K-major, zero-filled beyond the tensor),
+//   N = 128 taps (the V D image of the job, SW128 K-major), K = channels.
 //   Each epilogue warp adds its 32 taps' contributions into its own shared-memory
-//   halo buffer, one voxel column at a time (the lanes of one column write distinct
-//   addresses; columns are separated by a warp barrier), the four buffers are summed
-//   in warp order and written as the tile's halo partial; a gather kernel adds, for
-//   every voxel, the partials of all tiles whose halo covers it, in a fixed order.
+//   halo buffer with shared-memory reductions (the lanes of one voxel column hit
+//   distinct addresses, but different columns of different lanes can collide), the four
+//   buffers are summed in warp order and written as the tile's halo partial; a gather
+//   kernel adds, for every voxel, the partials of all tiles whose halo covers it, in a
+//   fixed order.
 //
 // Warp roles in both kernels: warp 0 issues TMA, warp 1 (one lane) issues tcgen05.mma,
-// warps 2-5 run the epilogue from TMEM (warp w reads TMEM lanes 32*(w%4)..+31).
+// warps 2-5 run the epilogue from TMEM (warp w reads TMEM lanes 32*(w%4)..+31, i.e.
+// 32 voxels of the tile).
 // Two TMEM accumulators of 128 columns let the epilogue of a tile overlap the MMAs of
 // the next. Every mbarrier wait is bounded (ptx::mbar_wait) and a timeout is reported
 // through the job status instead of hanging.
@@ -73,12 +75,15 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.Hb = TH + k1 - 1;
   g.Wb = TW + k2 - 1;
   g.HB = g.Hb * g.Wb * k3;
+  g.pitch = rup(g.Wb, 8);
+  if ((g.pitch / 8) % 2 == 0) g.pitch += 8;
+  g.HBp = k3 * g.Hb * g.pitch;
   return g;
 }
 
 size_t fwd_smem(const TcGeom& g) { return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + 256; }
 size_t adj_smem(const TcGeom& g) {
-  return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 4 * (size_t)g.HB * 4 + 256;
+  return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 4 * (size_t)g.HBp * 4 + 128 * 4 + 256;
 }
 
 // Byte offset of forward K-group `grp` (8 taps) inside a halo stage.
@@ -187,7 +192,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   } else if (warp == 1) {
     if (lane == 0) {
       if (!ptx::mbar_wait(abar, 0)) failed = true;
-      const uint32_t idesc = ptx::idesc_bf16(128, 128, 0, 1);
+      // A = halo (voxels x taps, MN-major, overlapping core matrices), B = V^T image
+      // (channels x taps, K-major SW128): D[voxel][channel] in TMEM.
+      const uint32_t idesc = ptx::idesc_bf16(128, 128, 1, 0);
       const uint32_t aB = ptx::smem_u32(sA), hB = ptx::smem_u32(sH);
       const uint32_t nstride = (uint32_t)g.k3 * 16;
       int it = 0;
@@ -200,8 +207,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         const uint32_t d = tbase + (uint32_t)b * 128;
         const uint32_t hs = hB + (uint32_t)s * g.stage_bytes;
         for (int i = 0; i < g.nmma; ++i) {
-          const uint64_t ad = ptx::sdesc(aB + (uint32_t)(i >> 2) * CHUNK + (uint32_t)(i & 3) * 32, 16, 1024, 2);
-          const uint64_t bd = ptx::sdesc(hs + a.tab.boff[i], a.tab.kstr[i], nstride, 0);
+          const uint64_t ad = ptx::sdesc(hs + a.tab.boff[i], a.tab.kstr[i], nstride, 0);
+          const uint64_t bd = ptx::sdesc(aB + (uint32_t)(i >> 2) * CHUNK + (uint32_t)(i & 3) * 32, 16, 1024, 2);
           ptx::mma_bf16(d, ad, bd, idesc, i > 0 ? 1u : 0u);
         }
         ptx::mma_commit(&empty[s]);
@@ -211,9 +218,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       if (!ptx::mbar_wait(dbar, 0)) failed = true;
     }
   } else {
+    // Epilogue: warp q reads TMEM lanes 32q..32q+31 = voxels 32q + lane of the tile; a
+    // TMEM load gives one voxel 16 consecutive channels, so U is read and written with
+    // 16-byte vector accesses.
     const int q = warp & 3;
-    const int ch = ct * 128 + q * 32 + lane;
+    const int vox = q * 32 + lane;
     const int mode = a.mode;
+    const bool rd = (mode == 1 || mode == 3);
     int it = 0;
     for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
       const int b = it & 1;
@@ -224,40 +235,84 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       const JobDev& J = sh.jobs[jb];
       const int tile = tg - sh.job_tile0[jb];
       const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
-      const int h0 = th * TH, w0 = tw * TW;
-      const bool live = ch < sh.kc;
-      const bool real = ch < sh.k;
-      const float Dc = real ? J.D[ch] : 0.f;
-      const float sc = (mode == 3 && real) ? (float)(J.s[ch] / J.sc->theta) : 0.f;
-      __nv_bfloat16* U = reinterpret_cast<__nv_bfloat16*>(J.U);
-      float csum = 0.f, rsum = 0.f;
+      const int h = th * TH + (vox >> 3), w = tw * TW + (vox & 7);
+      const bool valid = h < J.H && w < J.W;
+      __nv_bfloat16* Urow = reinterpret_cast<__nv_bfloat16*>(J.U) +
+                            (valid ? (((size_t)t * J.H + h) * J.W + w) * sh.kc : 0);
+      const double inv_theta = 1.0 / J.sc->theta;
+      const int nch = min(8, (sh.kc - ct * 128) / 16);   // chunks of 16 channels in U
+      uint4 cur[2], nxt[2];
+      cur[0] = cur[1] = nxt[0] = nxt[1] = make_uint4(0, 0, 0, 0);
+      if (rd && valid && nch > 0) {
+        cur[0] = *reinterpret_cast<const uint4*>(Urow + ct * 128);
+        cur[1] = *reinterpret_cast<const uint4*>(Urow + ct * 128 + 8);
+      }
+      float rsum = 0.f;
       for (int cc = 0; cc < 8; ++cc) {
-        float v[16];
-        ptx::tmem_ld16(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cc * 16, v);
-        ptx::tmem_ld_wait();
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int vox = cc * 16 + e;
-          const int h = h0 + (vox >> 3), w = w0 + (vox & 7);
-          if (!live || h >= J.H || w >= J.W) continue;
-          const size_t idx = (((size_t)t * J.H + h) * J.W + w) * sh.kc + ch;
-          if (mode == 1) {
-            const float u = real ? __bfloat162float(U[idx]) : 0.f;
-            const __nv_bfloat16 ub = __float2bfloat16(fmaf(u, Dc, -v[e]));
-            U[idx] = ub;
-            const float uf = __bfloat162float(ub);
-            csum = fmaf(uf, uf, csum);
-          } else if (mode == 2) {
-            const __nv_bfloat16 ub = __float2bfloat16(-v[e]);
-            U[idx] = ub;
-            const float uf = __bfloat162float(ub);
-            csum = fmaf(uf, uf, csum);
-          } else {
-            const float u = real ? __bfloat162float(U[idx]) : 0.f;
-            const float r = fmaf(u, sc, v[e]);
-            rsum = fmaf(r, r, rsum);
+        const int c0 = ct * 128 + cc * 16;
+        if (cc < nch) {
+          if (rd && valid && cc + 1 < nch) {      // next chunk's loads in flight early
+            nxt[0] = *reinterpret_cast<const uint4*>(Urow + c0 + 16);
+            nxt[1] = *reinterpret_cast<const uint4*>(Urow + c0 + 24);
           }
         }
+        float e[16];
+        ptx::tmem_ld16(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cc * 16, e);
+        ptx::tmem_ld_wait();
+        if (cc >= nch) continue;                  // channels beyond kc: nothing stored
+        const __nv_bfloat16* ub = reinterpret_cast<const __nv_bfloat16*>(cur);
+        float sq[16];
+        if (mode == 3) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + j;
+            const float sj = c < sh.k ? (float)(J.s[c] * inv_theta) : 0.f;
+            const float r = fmaf(__bfloat162float(ub[j]), sj, e[j]);
+            rsum = valid ? fmaf(r, r, rsum) : rsum;
+          }
+        } else {
+          __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float un = mode == 1 ? fmaf(__bfloat162float(ub[j]), J.D[c0 + j], -e[j]) : -e[j];
+            o[j] = __float2bfloat16(un);
+            const float uf = __bfloat162float(o[j]);
+            sq[j] = valid ? uf * uf : 0.f;
+          }
+          if (valid) {
+            *reinterpret_cast<uint4*>(Urow + c0) = *reinterpret_cast<const uint4*>(o);
+            *reinterpret_cast<uint4*>(Urow + c0 + 8) = *reinterpret_cast<const uint4*>(o + 8);
+          }
+          // column sums over the warp's 32 voxels: transpose-reduce 16 values across 32
+          // lanes (fixed order); lane l ends with channel ((l >> 1) & 15)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float snd = (lane & 16) ? sq[i] : sq[i + 8];
+            const float kp = (lane & 16) ? sq[i + 8] : sq[i];
+            sq[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 16);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float snd = (lane & 8) ? sq[i] : sq[i + 4];
+            const float kp = (lane & 8) ? sq[i + 4] : sq[i];
+            sq[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const float snd = (lane & 4) ? sq[i] : sq[i + 2];
+            const float kp = (lane & 4) ? sq[i + 2] : sq[i];
+            sq[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 4);
+          }
+          {
+            const float snd = (lane & 2) ? sq[0] : sq[1];
+            const float kp = (lane & 2) ? sq[1] : sq[0];
+            sq[0] = kp + __shfl_xor_sync(0xffffffffu, snd, 2);
+          }
+          sq[0] += __shfl_xor_sync(0xffffffffu, sq[0], 1);
+          if ((lane & 1) == 0) J.part[((size_t)tile * PROW + q) * sh.kc + c0 + ((lane >> 1) & 15)] = sq[0];
+        }
+        cur[0] = nxt[0];
+        cur[1] = nxt[1];
       }
       ptx::tc_fence_before();
       __syncwarp();
@@ -266,8 +321,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
         if (lane == 0) J.rpart[(size_t)tile * sh.nrp + ct * 4 + q] = rsum;
-      } else if (live) {
-        J.part[(size_t)tile * sh.kc + ch] = csum;
       }
     }
   }
@@ -291,7 +344,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   uint8_t* sA = sm;
   uint8_t* sU = sm + (size_t)g.nch_a * CHUNK;
   float* buf = reinterpret_cast<float*>(sU + (size_t)ADJ_STAGES * CHUNK);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(buf + 4 * (size_t)g.HB);
+  int* toff = reinterpret_cast<int*>(buf + 4 * (size_t)g.HBp);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(toff + 128);
   uint64_t* full = bars;                   // [4]
   uint64_t* empty = bars + 4;              // [4]
   uint64_t* tfull = bars + 8;              // [2]
@@ -326,7 +380,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     ptx::tmem_alloc(tslot, TMEM_COLS);
     ptx::tmem_relinquish();
   }
-  for (int i = threadIdx.x; i < 4 * g.HB; i += blockDim.x) buf[i] = 0.f;
+  for (int i = threadIdx.x; i < 4 * g.HBp; i += blockDim.x) buf[i] = 0.f;
+  // halo offset of each tap of this tap tile (-1 for padding taps): the contribution
+  // G[v][s] lands at buf[vbase(v) + toff[s]], vbase(v) = h_v * pitch + w_v
+  if (threadIdx.x < 128) {
+    const int s = tt * 128 + threadIdx.x;
+    int o = -1;
+    if (s < sh.k) {
+      const int sw = s % g.k2, shh = (s / g.k2) % g.k1, st = s / (g.k1 * g.k2);
+      o = ((g.k3 - 1 - st) * g.Hb + (g.k1 - 1 - shh)) * g.pitch + (g.k2 - 1 - sw);
+    }
+    toff[threadIdx.x] = o;
+  }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
@@ -354,6 +419,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      // A = U tile (voxels x channels), B = V D image (taps x channels), both K-major
+      // SW128: D[voxel][tap] in TMEM.
       const uint32_t idesc = ptx::idesc_bf16(128, 128, 0, 0);
       const uint32_t aB = ptx::smem_u32(sA), uB = ptx::smem_u32(sU);
       int cur = -1, cnt = 0, i = 0;
@@ -386,8 +453,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
           ptx::tc_fence_after();
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = ptx::sdesc(aB + (uint32_t)c * CHUNK + kk * 32, 16, 1024, 2);
-            const uint64_t bd = ptx::sdesc(uB + (uint32_t)s * CHUNK + kk * 32, 16, 1024, 2);
+            const uint64_t ad = ptx::sdesc(uB + (uint32_t)s * CHUNK + kk * 32, 16, 1024, 2);
+            const uint64_t bd = ptx::sdesc(aB + (uint32_t)c * CHUNK + kk * 32, 16, 1024, 2);
             ptx::mma_bf16(d, ad, bd, idesc, (c | kk) ? 1u : 0u);
           }
           ptx::mma_commit(&empty[s]);
@@ -399,15 +466,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
       if (!ptx::mbar_wait(dbar, dph)) failed = true;
     }
   } else {
+    // Epilogue: warp q reads TMEM lanes 32q..32q+31 = voxels 32q + lane (rows 4q..4q+3 of
+    // the tile); a TMEM load gives one voxel 16 consecutive taps.
     const int q = warp & 3;
-    const int s = tt * 128 + q * 32 + lane;             // this thread's tap
-    const bool valid = s < sh.k;
-    int base = 0;
-    if (valid) {
-      const int sw = s % g.k2, shh = (s / g.k2) % g.k1, st = s / (g.k1 * g.k2);
-      base = ((g.k3 - 1 - st) * g.Hb + (g.k1 - 1 - shh)) * g.Wb + (g.k2 - 1 - sw);
-    }
-    float* myb = buf + (size_t)q * g.HB;
+    const int vox = q * 32 + lane;
+    const int vbase = (vox >> 3) * g.pitch + (vox & 7);
+    float* myb = buf + (size_t)q * g.HBp;
     uint32_t sph = 0;
     int i = 0;
     for (int tg = lo; tg < hi; ++tg, ++i) {
@@ -419,14 +483,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         float v[16];
         ptx::tmem_ld16(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cc * 16, v);
         ptx::tmem_ld_wait();
-        // Lane (tap) s adds G[s][vox] at base_s + pos(vox). At one column the 32 lanes hit
-        // 32 distinct addresses, but lane A at column e+1 can hit lane B's address of
-        // column e, so the warp steps through the columns with a barrier in between.
+        // Lanes (voxels) of one tap hit 32 distinct addresses (and 32 distinct banks), but
+        // different taps of different lanes can hit the same address, so the adds are
+        // shared-memory reductions.
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const int vox = cc * 16 + e;
-          if (valid) myb[base + (vox >> 3) * g.Wb + (vox & 7)] += v[e];
-          __syncwarp();
+          const int o = toff[cc * 16 + e];
+          if (o >= 0) atomicAdd(&myb[vbase + o], v[e]);
         }
       }
       ptx::tc_fence_before();
@@ -440,9 +503,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
       const int tile = tg - sh.job_tile0[jb];
       float* out = J.G + ((size_t)tile * g.ntt + tt) * g.HB;
       for (int p = q * 32 + lane; p < g.HB; p += 128) {
-        const float v = ((buf[p] + buf[g.HB + p]) + buf[2 * g.HB + p]) + buf[3 * g.HB + p];
+        const int row = p / g.Wb, col = p - row * g.Wb;   // row = bt * Hb + bh
+        const int src = row * g.pitch + col;
+        const float v = ((buf[src] + buf[g.HBp + src]) + buf[2 * g.HBp + src]) + buf[3 * g.HBp + src];
         out[p] = v;
-        buf[p] = 0.f; buf[g.HB + p] = 0.f; buf[2 * g.HB + p] = 0.f; buf[3 * g.HB + p] = 0.f;
+        buf[src] = 0.f; buf[g.HBp + src] = 0.f; buf[2 * g.HBp + src] = 0.f; buf[3 * g.HBp + src] = 0.f;
       }
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(zbar);
@@ -498,9 +563,15 @@ __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
     const int tp = (int)(r % J.xTp);
     const int c = (int)(r / J.xTp);
     const long long rowb = ((long long)wrapi(tp - (g.k3 - 1), J.T) * J.H + wrapi(hp - (g.k1 - 1), J.H)) * J.W;
+    const int w0 = wu * 8 - pw - c;
     __align__(16) __nv_bfloat16 v[8];
+    if (w0 >= 0 && w0 + 7 < J.W) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(src[rowb + wrapi(wu * 8 + e - pw - c, J.W)]);
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(src[rowb + w0 + e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(src[rowb + wrapi(w0 + e, J.W)]);
+    }
     *reinterpret_cast<uint4*>(J.Xc + (((long long)c * J.xTp + tp) * J.xHp + hp) * J.xWp + wu * 8) =
         *reinterpret_cast<const uint4*>(v);
   }
@@ -713,7 +784,7 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
 }
 
 cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st) {
-  prepare_X_kernel<<<dim3(256, sh.njobs), 256, 0, st>>>(sh, v.g, from_L);
+  prepare_X_kernel<<<dim3(1024, sh.njobs), 256, 0, st>>>(sh, v.g, from_L);
   return cudaGetLastError();
 }
 

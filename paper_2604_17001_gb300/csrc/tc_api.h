@@ -23,6 +23,8 @@ struct TcGeom {
   int kcp;          // channels rounded up to 64
   int nch_a;        // 64-wide SW128 chunks of the adjoint A image
   int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*k3
+  int pitch, HBp;   // shared-memory row pitch of the halo buffers (an odd multiple of 8,
+                    // >= Wb, so 4 rows x 8 voxels hit 32 banks) and k3*Hb*pitch
 };
 
 // Per-V device data of the tensor-core path.

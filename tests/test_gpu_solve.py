@@ -93,22 +93,24 @@ def test_tolerance_stopping_matches_oracle(ctx):
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_batch_equals_single_bitwise(ctx, prec):
     # Uneven problems stepped together give exactly the results of solving each alone
-    # (every reduction has a fixed order that does not depend on the batch).
+    # (every reduction has a fixed order that does not depend on the batch). 100 iterations:
+    # mid-run the BF16 iterate is still at its transient error level (~1e-3).
     kd = (5, 5, 3)
+    its = 100
     probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 16, 8), 0.5, 1), ((16, 48, 5), 0.3, 2),
                                                          ((24, 24, 3), 0.7, 3)]]
     V = probs[0][2]
     try:
         outs, stats = ctx.icnnm_solve_batch([p[0] for p in probs], [p[1] for p in probs], V, kd,
-                                            max_iters=30, prec=prec)
+                                            max_iters=its, prec=prec)
     except icnnm.ICNNMError as e:
         if e.status == icnnm.EUNSUPPORTED:
             pytest.skip(str(e))
         raise
     for (M, mask, _, _), Lb in zip(probs, outs):
-        Ls, _ = ctx.icnnm_solve(M, mask, V, kd, max_iters=30, prec=prec)
+        Ls, _ = ctx.icnnm_solve(M, mask, V, kd, max_iters=its, prec=prec)
         assert np.array_equal(Lb, Ls)
-        Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=30)
+        Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=its)
         assert rel(Lb, Lo) <= TOL[prec]
 
 
