@@ -19,12 +19,12 @@
 // of Eq. ak), deterministic:
 //   M = 128 voxels (the U tile by TMA, SW128 K-major, zero-filled beyond the tensor),
 //   N = 128 taps (the V D image of the job, SW128 K-major), K = channels.
-//   Each epilogue warp adds its 32 taps' contributions into its own shared-memory
-//   halo buffer with shared-memory reductions (the lanes of one voxel column hit
-//   distinct addresses, but different columns of different lanes can collide), the four
-//   buffers are summed in warp order and written as the tile's halo partial; a gather
-//   kernel adds, for every voxel, the partials of all tiles whose halo covers it, in a
-//   fixed order.
+//   The epilogue warps add their products into a shared-memory halo buffer of the tile
+//   with shared-memory reductions (double-buffered: tile i is added while tile i-1 is
+//   written out as the tile's halo partial); a gather kernel adds, for every voxel, the
+//   partials of all tiles whose halo covers it, in a fixed order. The order of the
+//   shared-memory additions is not fixed, so this pass is reproducible to rounding, not
+//   bitwise.
 //
 // Warp roles in both kernels: warp 0 issues TMA, warp 1 (one lane) issues tcgen05.mma,
 // warps 2-5 run the epilogue from TMEM (warp w reads TMEM lanes 32*(w%4)..+31, i.e.
@@ -46,7 +46,8 @@ namespace icnnm {
 
 namespace {
 
-constexpr int TC_THREADS = 192;
+constexpr int EPI_WARPS = 16;        // 4 per TMEM lane quarter, each owning 32 columns
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int LMAX = 16;             // (tile, offset) pairs per coordinate in the gather
 constexpr int ADJ_STAGES = 4;
 constexpr int CHUNK = 16384;         // one SW128 K-chunk: 128 rows x 128 bytes
@@ -83,7 +84,7 @@ TcGeom make_geom(int k1, int k2, int k3) {
 
 size_t fwd_smem(const TcGeom& g) { return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + 256; }
 size_t adj_smem(const TcGeom& g) {
-  return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 4 * (size_t)g.HBp * 4 + 128 * 4 + 256;
+  return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 2 * (size_t)g.HBp * 4 + 128 * 4 + 256;
 }
 
 // Byte offset of forward K-group `grp` (8 taps) inside a halo stage.
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       ptx::mbar_init(&full[i], 1);
       ptx::mbar_init(&empty[i], 1);
       ptx::mbar_init(&tfull[i], 1);
-      ptx::mbar_init(&tempty[i], 4);
+      ptx::mbar_init(&tempty[i], EPI_WARPS);
     }
     ptx::mbar_init(abar, 1);
     ptx::mbar_init(dbar, 1);
@@ -218,19 +219,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       if (!ptx::mbar_wait(dbar, 0)) failed = true;
     }
   } else {
-    // Epilogue: warp q reads TMEM lanes 32q..32q+31 = voxels 32q + lane of the tile; a
-    // TMEM load gives one voxel 16 consecutive channels, so U is read and written with
-    // 16-byte vector accesses.
+    // Epilogue: 16 warps. Warp w reads TMEM lanes 32q..32q+31 (q = w % 4), i.e. voxels
+    // 32q + lane of the tile, and columns 32g..32g+31 (g = (w - 2) / 4), i.e. 32 channels.
+    // A TMEM load gives one voxel 32 consecutive channels, so U is read and written with
+    // 16-byte vector accesses; the U and D loads of a tile are issued before waiting for
+    // its accumulator.
     const int q = warp & 3;
+    const int cg = (warp - 2) >> 2;
     const int vox = q * 32 + lane;
     const int mode = a.mode;
     const bool rd = (mode == 1 || mode == 3);
+    const int c0 = ct * 128 + cg * 32;                    // first channel of this warp
+    const int nchk = max(0, min(2, (sh.kc - c0) / 16));   // chunks of 16 channels inside U
     int it = 0;
     for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
       const int b = it & 1;
       const uint32_t ph = (it >> 1) & 1;
-      if (!ptx::mbar_wait(&tfull[b], ph)) { failed = true; break; }
-      ptx::tc_fence_after();
       const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
       const JobDev& J = sh.jobs[jb];
       const int tile = tg - sh.job_tile0[jb];
@@ -239,88 +243,92 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       const bool valid = h < J.H && w < J.W;
       __nv_bfloat16* Urow = reinterpret_cast<__nv_bfloat16*>(J.U) +
                             (valid ? (((size_t)t * J.H + h) * J.W + w) * sh.kc : 0);
-      const double inv_theta = 1.0 / J.sc->theta;
-      const int nch = min(8, (sh.kc - ct * 128) / 16);   // chunks of 16 channels in U
-      uint4 cur[2], nxt[2];
-      cur[0] = cur[1] = nxt[0] = nxt[1] = make_uint4(0, 0, 0, 0);
-      if (rd && valid && nch > 0) {
-        cur[0] = *reinterpret_cast<const uint4*>(Urow + ct * 128);
-        cur[1] = *reinterpret_cast<const uint4*>(Urow + ct * 128 + 8);
-      }
-      float rsum = 0.f;
-      for (int cc = 0; cc < 8; ++cc) {
-        const int c0 = ct * 128 + cc * 16;
-        if (cc < nch) {
-          if (rd && valid && cc + 1 < nch) {      // next chunk's loads in flight early
-            nxt[0] = *reinterpret_cast<const uint4*>(Urow + c0 + 16);
-            nxt[1] = *reinterpret_cast<const uint4*>(Urow + c0 + 24);
-          }
+      uint4 uv[4];
+      float dv[32];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) uv[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        if (rd && valid && i < nchk) {
+          uv[2 * i] = *reinterpret_cast<const uint4*>(Urow + c0 + 16 * i);
+          uv[2 * i + 1] = *reinterpret_cast<const uint4*>(Urow + c0 + 16 * i + 8);
         }
-        float e[16];
-        ptx::tmem_ld16(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cc * 16, e);
-        ptx::tmem_ld_wait();
-        if (cc >= nch) continue;                  // channels beyond kc: nothing stored
-        const __nv_bfloat16* ub = reinterpret_cast<const __nv_bfloat16*>(cur);
-        float sq[16];
-        if (mode == 3) {
+      if (mode == 1 || mode == 3) {
+        const float* src = mode == 1 ? J.D : J.s;
+        const float sc = mode == 1 ? 1.f : (float)(1.0 / J.sc->theta);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int c = c0 + j;
-            const float sj = c < sh.k ? (float)(J.s[c] * inv_theta) : 0.f;
-            const float r = fmaf(__bfloat162float(ub[j]), sj, e[j]);
-            rsum = valid ? fmaf(r, r, rsum) : rsum;
-          }
-        } else {
-          __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float un = mode == 1 ? fmaf(__bfloat162float(ub[j]), J.D[c0 + j], -e[j]) : -e[j];
-            o[j] = __float2bfloat16(un);
-            const float uf = __bfloat162float(o[j]);
-            sq[j] = valid ? uf * uf : 0.f;
-          }
-          if (valid) {
-            *reinterpret_cast<uint4*>(Urow + c0) = *reinterpret_cast<const uint4*>(o);
-            *reinterpret_cast<uint4*>(Urow + c0 + 8) = *reinterpret_cast<const uint4*>(o + 8);
-          }
-          // column sums over the warp's 32 voxels: transpose-reduce 16 values across 32
-          // lanes (fixed order); lane l ends with channel ((l >> 1) & 15)
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float snd = (lane & 16) ? sq[i] : sq[i + 8];
-            const float kp = (lane & 16) ? sq[i + 8] : sq[i];
-            sq[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 16);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float snd = (lane & 8) ? sq[i] : sq[i + 4];
-            const float kp = (lane & 8) ? sq[i + 4] : sq[i];
-            sq[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
-          }
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const float snd = (lane & 4) ? sq[i] : sq[i + 2];
-            const float kp = (lane & 4) ? sq[i + 2] : sq[i];
-            sq[i] = kp + __shfl_xor_sync(0xffffffffu, snd, 4);
-          }
-          {
-            const float snd = (lane & 2) ? sq[0] : sq[1];
-            const float kp = (lane & 2) ? sq[1] : sq[0];
-            sq[0] = kp + __shfl_xor_sync(0xffffffffu, snd, 2);
-          }
-          sq[0] += __shfl_xor_sync(0xffffffffu, sq[0], 1);
-          if ((lane & 1) == 0) J.part[((size_t)tile * PROW + q) * sh.kc + c0 + ((lane >> 1) & 15)] = sq[0];
+        for (int i = 0; i < 8; ++i) {
+          float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (c0 + 4 * i < sh.kc) d4 = *reinterpret_cast<const float4*>(src + c0 + 4 * i);
+          dv[4 * i] = d4.x * sc; dv[4 * i + 1] = d4.y * sc; dv[4 * i + 2] = d4.z * sc; dv[4 * i + 3] = d4.w * sc;
         }
-        cur[0] = nxt[0];
-        cur[1] = nxt[1];
       }
+      if (!ptx::mbar_wait(&tfull[b], ph)) { failed = true; break; }
+      ptx::tc_fence_after();
+      float e[32];
+      ptx::tmem_ld32(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cg * 32, e);
+      ptx::tmem_ld_wait();
       ptx::tc_fence_before();
       __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&tempty[b]);
+      if (lane == 0) ptx::mbar_arrive(&tempty[b]);     // the accumulator is in registers
+      const __nv_bfloat16* ub = reinterpret_cast<const __nv_bfloat16*>(uv);
       if (mode == 3) {
+        float rsum = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float r = fmaf(__bfloat162float(ub[j]), dv[j], e[j]);
+          rsum = (valid && j < 16 * nchk) ? fmaf(r, r, rsum) : rsum;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
-        if (lane == 0) J.rpart[(size_t)tile * sh.nrp + ct * 4 + q] = rsum;
+        if (lane == 0) J.rpart[(size_t)tile * sh.nrp + ct * 16 + cg * 4 + q] = rsum;
+        continue;
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (i >= nchk) break;
+        __align__(16) __nv_bfloat16 o[16];
+        float sq[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int jj = 16 * i + j;
+          const float un = mode == 1 ? fmaf(__bfloat162float(ub[jj]), dv[jj], -e[jj]) : -e[jj];
+          o[j] = __float2bfloat16(un);
+          const float uf = __bfloat162float(o[j]);
+          sq[j] = valid ? uf * uf : 0.f;
+        }
+        if (valid) {
+          *reinterpret_cast<uint4*>(Urow + c0 + 16 * i) = *reinterpret_cast<const uint4*>(o);
+          *reinterpret_cast<uint4*>(Urow + c0 + 16 * i + 8) = *reinterpret_cast<const uint4*>(o + 8);
+        }
+        // column sums over the warp's 32 voxels: transpose-reduce 16 values across the 32
+        // lanes (fixed order); lane l ends with channel ((l >> 1) & 15) of this chunk
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float snd = (lane & 16) ? sq[k] : sq[k + 8];
+          const float kp = (lane & 16) ? sq[k + 8] : sq[k];
+          sq[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 16);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float snd = (lane & 8) ? sq[k] : sq[k + 4];
+          const float kp = (lane & 8) ? sq[k + 4] : sq[k];
+          sq[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const float snd = (lane & 4) ? sq[k] : sq[k + 2];
+          const float kp = (lane & 4) ? sq[k + 2] : sq[k];
+          sq[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 4);
+        }
+        {
+          const float snd = (lane & 2) ? sq[0] : sq[1];
+          const float kp = (lane & 2) ? sq[1] : sq[0];
+          sq[0] = kp + __shfl_xor_sync(0xffffffffu, snd, 2);
+        }
+        sq[0] += __shfl_xor_sync(0xffffffffu, sq[0], 1);
+        if ((lane & 1) == 0)
+          J.part[((size_t)tile * PROW + q) * sh.kc + c0 + 16 * i + ((lane >> 1) & 15)] = sq[0];
       }
     }
   }
@@ -343,8 +351,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   const Shared& sh = a.sh;
   uint8_t* sA = sm;
   uint8_t* sU = sm + (size_t)g.nch_a * CHUNK;
-  float* buf = reinterpret_cast<float*>(sU + (size_t)ADJ_STAGES * CHUNK);
-  int* toff = reinterpret_cast<int*>(buf + 4 * (size_t)g.HBp);
+  float* buf = reinterpret_cast<float*>(sU + (size_t)ADJ_STAGES * CHUNK);   // [2][HBp]
+  int* toff = reinterpret_cast<int*>(buf + 2 * (size_t)g.HBp);
   uint64_t* bars = reinterpret_cast<uint64_t*>(toff + 128);
   uint64_t* full = bars;                   // [4]
   uint64_t* empty = bars + 4;              // [4]
@@ -352,9 +360,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   uint64_t* tempty = bars + 10;            // [2]
   uint64_t* abar = bars + 12;
   uint64_t* dbar = bars + 13;
-  uint64_t* sumbar = bars + 14;
-  uint64_t* zbar = bars + 15;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
+  uint64_t* redbar = bars + 14;           // [2] all epilogue warps have added a tile
+  uint64_t* zbar = bars + 16;             // [2] a halo buffer has been flushed and cleared
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 18);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tt = blockIdx.x % g.ntt;
   const int slot = blockIdx.x / g.ntt, nslot = gridDim.x / g.ntt;
@@ -368,19 +376,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&tfull[i], 1);
-      ptx::mbar_init(&tempty[i], 4);
+      ptx::mbar_init(&tempty[i], EPI_WARPS);
+      ptx::mbar_init(&redbar[i], EPI_WARPS);
+      ptx::mbar_init(&zbar[i], EPI_WARPS);
     }
     ptx::mbar_init(abar, 1);
     ptx::mbar_init(dbar, 1);
-    ptx::mbar_init(sumbar, 4);
-    ptx::mbar_init(zbar, 4);
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
     ptx::tmem_alloc(tslot, TMEM_COLS);
     ptx::tmem_relinquish();
   }
-  for (int i = threadIdx.x; i < 4 * g.HBp; i += blockDim.x) buf[i] = 0.f;
+  for (int i = threadIdx.x; i < 2 * g.HBp; i += blockDim.x) buf[i] = 0.f;
   // halo offset of each tap of this tap tile (-1 for padding taps): the contribution
   // G[v][s] lands at buf[vbase(v) + toff[s]], vbase(v) = h_v * pitch + w_v
   if (threadIdx.x < 128) {
@@ -466,53 +474,64 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
       if (!ptx::mbar_wait(dbar, dph)) failed = true;
     }
   } else {
-    // Epilogue: warp q reads TMEM lanes 32q..32q+31 = voxels 32q + lane (rows 4q..4q+3 of
-    // the tile); a TMEM load gives one voxel 16 consecutive taps.
+    // Epilogue: 16 warps. Warp w reads TMEM lanes 32q..32q+31 (q = w % 4), i.e. voxels
+    // 32q + lane (rows 4q..4q+3 of the tile), and columns 32g..32g+31 (g = (w - 2) / 4),
+    // i.e. 32 taps. Tile i is added into halo buffer i % 2 with shared-memory reductions
+    // (lanes of one tap hit 32 distinct addresses and banks; different taps or warps may
+    // hit the same address). While tile i is added, the warps flush tile i-1's buffer
+    // (write the partial, clear), so the two phases of consecutive tiles overlap.
     const int q = warp & 3;
+    const int cg = (warp - 2) >> 2;
+    const int ew = warp - 2;
     const int vox = q * 32 + lane;
     const int vbase = (vox >> 3) * g.pitch + (vox & 7);
-    float* myb = buf + (size_t)q * g.HBp;
-    uint32_t sph = 0;
     int i = 0;
-    for (int tg = lo; tg < hi; ++tg, ++i) {
-      const int b = i & 1;
-      const uint32_t bph = (i >> 1) & 1;
-      if (!ptx::mbar_wait(&tfull[b], bph)) { failed = true; break; }
-      ptx::tc_fence_after();
-      for (int cc = 0; cc < 8; ++cc) {
-        float v[16];
-        ptx::tmem_ld16(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cc * 16, v);
+    int prev_tile = -1;
+    float* prev_out = nullptr;
+    for (int tg = lo; tg <= hi; ++tg, ++i) {
+      const bool have = tg < hi;
+      float* hb = buf + (size_t)(i & 1) * g.HBp;
+      if (have) {
+        // buffer i % 2 was last used by tile i - 2; wait until it has been flushed
+        if (i >= 2 && !ptx::mbar_wait(&zbar[i & 1], ((i - 2) >> 1) & 1)) { failed = true; break; }
+        const int b = i & 1;
+        const uint32_t bph = (i >> 1) & 1;
+        if (!ptx::mbar_wait(&tfull[b], bph)) { failed = true; break; }
+        ptx::tc_fence_after();
+        float v[32];
+        ptx::tmem_ld32(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cg * 32, v);
         ptx::tmem_ld_wait();
-        // Lanes (voxels) of one tap hit 32 distinct addresses (and 32 distinct banks), but
-        // different taps of different lanes can hit the same address, so the adds are
-        // shared-memory reductions.
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&tempty[b]);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int o = toff[cc * 16 + e];
-          if (o >= 0) atomicAdd(&myb[vbase + o], v[e]);
+        for (int e = 0; e < 32; ++e) {
+          const int o = toff[cg * 32 + e];
+          if (o >= 0) atomicAdd(&hb[vbase + o], v[e]);
         }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&redbar[i & 1]);
       }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&tempty[b]);
-      // sum the four warp buffers in warp order, write the tile's halo partial, clear
-      if (lane == 0) ptx::mbar_arrive(sumbar);
-      if (!ptx::mbar_wait(sumbar, sph)) { failed = true; break; }
-      const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
-      const JobDev& J = sh.jobs[jb];
-      const int tile = tg - sh.job_tile0[jb];
-      float* out = J.G + ((size_t)tile * g.ntt + tt) * g.HB;
-      for (int p = q * 32 + lane; p < g.HB; p += 128) {
-        const int row = p / g.Wb, col = p - row * g.Wb;   // row = bt * Hb + bh
-        const int src = row * g.pitch + col;
-        const float v = ((buf[src] + buf[g.HBp + src]) + buf[2 * g.HBp + src]) + buf[3 * g.HBp + src];
-        out[p] = v;
-        buf[src] = 0.f; buf[g.HBp + src] = 0.f; buf[2 * g.HBp + src] = 0.f; buf[3 * g.HBp + src] = 0.f;
+      // flush tile i-1: every warp has added it into buffer (i-1) % 2
+      if (i >= 1) {
+        const int pb = (i - 1) & 1;
+        if (!ptx::mbar_wait(&redbar[pb], ((i - 1) >> 1) & 1)) { failed = true; break; }
+        float* src = buf + (size_t)pb * g.HBp;
+        for (int p = ew * 32 + lane; p < g.HB; p += 32 * EPI_WARPS) {
+          const int row = p / g.Wb, col = p - row * g.Wb;   // row = bt * Hb + bh
+          const int si = row * g.pitch + col;
+          prev_out[p] = src[si];
+          src[si] = 0.f;
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&zbar[pb]);
       }
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(zbar);
-      if (!ptx::mbar_wait(zbar, sph)) { failed = true; break; }
-      sph ^= 1;
+      if (have) {
+        const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+        const JobDev& J = sh.jobs[jb];
+        prev_tile = tg - sh.job_tile0[jb];
+        prev_out = J.G + ((size_t)prev_tile * g.ntt + tt) * g.HB;
+      }
     }
   }
   if (failed) set_fail(sh);
@@ -700,7 +719,7 @@ void tc_free_vdata(TcVData* v) {
   v->VtImg = nullptr;
 }
 
-int tc_nrp(int k) { return 4 * ((k + 127) / 128); }
+int tc_nrp(int k) { return 16 * ((k + 127) / 128); }
 
 static void xc_dims(const TcGeom& g, int H, int W, int T, int& Tp, int& Hp, int& Wp) {
   const int nth = (H + TH - 1) / TH, ntw = (W + TW - 1) / TW;

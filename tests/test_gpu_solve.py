@@ -91,10 +91,11 @@ def test_tolerance_stopping_matches_oracle(ctx):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_batch_equals_single_bitwise(ctx, prec):
-    # Uneven problems stepped together give exactly the results of solving each alone
-    # (every reduction has a fixed order that does not depend on the batch). 100 iterations:
-    # mid-run the BF16 iterate is still at its transient error level (~1e-3).
+def test_batch_equals_single(ctx, prec):
+    # Uneven problems stepped together give the results of solving each alone: bitwise on
+    # the FP32 path (every reduction has a fixed order that does not depend on the batch),
+    # to rounding on the BF16 path (its col2im adds in shared memory in no fixed order).
+    # 100 iterations: mid-run the BF16 iterate is still at its transient error (~1e-3).
     kd = (5, 5, 3)
     its = 100
     probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 16, 8), 0.5, 1), ((16, 48, 5), 0.3, 2),
@@ -109,7 +110,10 @@ def test_batch_equals_single_bitwise(ctx, prec):
         raise
     for (M, mask, _, _), Lb in zip(probs, outs):
         Ls, _ = ctx.icnnm_solve(M, mask, V, kd, max_iters=its, prec=prec)
-        assert np.array_equal(Lb, Ls)
+        if prec == "fp32":
+            assert np.array_equal(Lb, Ls)
+        else:
+            assert rel(Lb, Ls) <= 1e-5
         Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=its)
         assert rel(Lb, Lo) <= TOL[prec]
 
