@@ -188,6 +188,35 @@ icnnm_status icnnm_cancel(icnnm_ctx* ctx, uint64_t job_id);
 icnnm_status icnnm_profile_enable(icnnm_ctx* ctx, int32_t enable);
 icnnm_status icnnm_profile_read(icnnm_ctx* ctx, int32_t pass, double* ms_total, int64_t* launches);
 
+/*
+ * Allocation-free learning of V (the paper has no counterpart; this is an interface for
+ * callers, not a step of the method). It computes what icnnm_learn_V computes (same
+ * Gram accumulation and FP64 eigensolver, summed in a different fixed order) but never
+ * allocates: it calls no cudaMalloc/cudaFree, creates no context, and uses no
+ * allocating library routine. It is meant for callers that cannot allocate device
+ * memory: code that runs while a CUDA graph is being captured, code that lives inside a
+ * framework that hands out device memory only from its own pool, and latency-critical
+ * code that must avoid the device-wide synchronisation an allocation can cause.
+ *   kdims, b, shapes : as for icnnm_learn_V
+ *   tensors          : b pointers to float tensors in DEVICE memory (current device)
+ *   V_out, eig_out   : as for icnnm_learn_V (device or host; eig_out may be NULL)
+ *   cuda_stream      : cudaStream_t to run on (NULL: the legacy default stream)
+ * All intermediates live in one fixed device array (about 2.1 MiB) that every GPU
+ * loading this library keeps until the process exits. Limits: k <= 256,
+ * (2k1-1)(2k2-1)(2k3-1) <= 4096, 1 <= b <= 256; larger requests return EINVAL and
+ * icnnm_noalloc_last_error() says which limit. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture. Every call reuses the same array and leaves its contents behind, so
+ * calls that may overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. The call returns after the results are written.
+ */
+icnnm_status icnnm_learn_V_noalloc(const int64_t kdims[3], int32_t b, const icnnm_shape* shapes,
+                                   const float* const* tensors, double* V_out, double* eig_out,
+                                   void* cuda_stream);
+
+/* Message of the last failure of icnnm_learn_V_noalloc on the calling thread. */
+const char* icnnm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -145,6 +145,8 @@ int learn_max_lags();
 cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo,
                       cudaStream_t st);
 cudaError_t check_finite(const float* x, long long n, int* dbad, cudaStream_t st);
+cudaError_t learn_gram_streamed(int b, const float* const* dptrs, const int* ddims, int k1, int k2, int k3,
+                                double* dpart, int nblk, double* dlagsum, double* dgram, cudaStream_t st);
 cudaError_t check_observed(const float* M, const uint8_t* mask, long long n, int* dcount_bad,
                            cudaStream_t st);
 

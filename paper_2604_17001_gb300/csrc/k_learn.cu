@@ -213,6 +213,28 @@ jacobi_kernel(double* A, double* V, int k, int max_sweeps, double tol, double* e
   if (threadIdx.x == 0) info[0] = sweep;
 }
 
+// lagsum[l] += sum_blk part[blk][l] (blocks in order): the running sum over tensors of
+// the autocorrelations, one tensor per call.
+__global__ void lag_accumulate_kernel(const double* part, int nblk, int nlag, double* lagsum, int first) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nlag) return;
+  double g = first ? 0.0 : lagsum[l];
+  for (int bb = 0; bb < nblk; ++bb) g += part[(long long)bb * nlag + l];
+  lagsum[l] = g;
+}
+
+// Gram[u][s] = lagsum[lag(u - s)].
+__global__ void gram_from_lags_kernel(const double* lagsum, int k1, int k2, int k3, double* gram) {
+  const int k = k1 * k2 * k3;
+  const int nl1 = 2 * k1 - 1, nl2 = 2 * k2 - 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)k * k) return;
+  const int u = (int)(idx / k), s = (int)(idx % k);
+  const int uw = u % k2, uh = (u / k2) % k1, ut = u / (k1 * k2);
+  const int sw = s % k2, shh = (s / k2) % k1, st = s / (k1 * k2);
+  gram[idx] = lagsum[((ut - st + k3 - 1) * nl1 + (uh - shh + k1 - 1)) * nl2 + (uw - sw + k2 - 1)];
+}
+
 __global__ void finite_check_kernel(const float* x, long long n, int* bad) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     if (!isfinite(x[i])) { atomicExch(bad, 1); return; }
@@ -247,6 +269,28 @@ int learn_max_lags() { return AC_THREADS * AC_MAXLAG_PER_THREAD; }
 cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo,
                       cudaStream_t st) {
   jacobi_kernel<<<1, EIG_THREADS, 0, st>>>(dA, dV, k, 30, 1e-15, devals, dVout, dinfo);
+  return cudaGetLastError();
+}
+
+// Gram accumulation one tensor at a time into caller-provided scratch (no allocation):
+// dptrs/ddims are device arrays of b tensor pointers and b (H, W, T) triples.
+cudaError_t learn_gram_streamed(int b, const float* const* dptrs, const int* ddims, int k1, int k2, int k3,
+                                double* dpart, int nblk, double* dlagsum, double* dgram, cudaStream_t st) {
+  LearnArgs a;
+  a.b = 1; a.k1 = k1; a.k2 = k2; a.k3 = k3;
+  a.nl1 = 2 * k1 - 1; a.nl2 = 2 * k2 - 1; a.nl3 = 2 * k3 - 1;
+  a.nlag = a.nl1 * a.nl2 * a.nl3;
+  a.nblk = nblk; a.part = dpart;
+  const size_t smem = learn_smem_bytes(k1, k2, k3);
+  cudaFuncSetAttribute(autocorr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  for (int j = 0; j < b; ++j) {
+    a.L = dptrs + j;
+    a.dims = ddims + 3 * j;
+    autocorr_kernel<<<dim3(1, nblk), AC_THREADS, smem, st>>>(a);
+    lag_accumulate_kernel<<<(a.nlag + 255) / 256, 256, 0, st>>>(dpart, nblk, a.nlag, dlagsum, j == 0);
+  }
+  const long long kk = (long long)k1 * k2 * k3;
+  gram_from_lags_kernel<<<(unsigned)((kk * kk + 255) / 256), 256, 0, st>>>(dlagsum, k1, k2, k3, dgram);
   return cudaGetLastError();
 }
 

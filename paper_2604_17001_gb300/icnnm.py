@@ -72,6 +72,10 @@ def load(path: str = LIB_PATH):
         "icnnm_poll": ([P, U64, P, C.POINTER(icnnm_stats)], I32),
         "icnnm_wait": ([P, U64, I64, P, C.POINTER(icnnm_stats)], I32),
         "icnnm_cancel": ([P, U64], I32),
+        "icnnm_profile_enable": ([P, I32], I32),
+        "icnnm_profile_read": ([P, I32, C.POINTER(D), C.POINTER(I64)], I32),
+        "icnnm_learn_V_noalloc": ([C.POINTER(I64), I32, C.POINTER(icnnm_shape), C.POINTER(P), P, P, P], I32),
+        "icnnm_noalloc_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -118,6 +122,33 @@ def params(**kw) -> icnnm_params:
             v = {"fp32": FP32, "bf16": BF16}[v]
         setattr(p, k, v)
     return p
+
+
+def icnnm_learn_V_noalloc(refs, kdims, V_out=None, eig_out=None, stream=None):
+    """Allocation-free learn_V: ``refs`` are torch CUDA tensors (device memory), the
+    outputs default to host numpy arrays. Returns (V, eig) like Context.icnnm_learn_V."""
+    lib = load()
+    kd = list(kdims) + [1] * (3 - len(kdims))
+    k = int(np.prod(kd))
+    b = len(refs)
+    shapes = (icnnm_shape * b)()
+    ptrs = (C.c_void_p * b)()
+    for i, r in enumerate(refs):
+        shp = tuple(r.shape)
+        dims = (shp[1], shp[2], shp[0]) if len(shp) == 3 else (shp[0], shp[1])
+        shapes[i] = make_shape(dims, kdims)
+        ptrs[i] = _ptr(r)
+    own = V_out is None
+    if own:
+        V_out = np.zeros((k, k), dtype=np.float64)
+        eig_out = np.zeros(k, dtype=np.float64) if eig_out is None else eig_out
+    st = lib.icnnm_learn_V_noalloc((C.c_int64 * 3)(*kd), b, shapes, ptrs, _ptr(V_out), _ptr(eig_out),
+                                   C.c_void_p(stream) if stream else None)
+    if st != OK:
+        raise ICNNMError(st, lib.icnnm_noalloc_last_error().decode())
+    if own:
+        return V_out.T.copy(), eig_out
+    return V_out, eig_out
 
 
 class Context:
