@@ -430,8 +430,9 @@ void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
 // One ADMM iteration for every job of the list. `check` (per list) adds the residual.
 void engine_step(icnnm_ctx* c, const Shared& sh, int prec, const TcVData* tcv, bool check) {
   OTHER(1, launch_scalars(sh, c->stream));
+  if (prec == ICNNM_BF16) OTHER(1, tc_launch_build_B2(sh, *tcv, c->stream));
   {
-    PassScope ps(c, 1, prec == ICNNM_FP32 ? 1 : 2);
+    PassScope ps(c, 1, 1);
     if (prec == ICNNM_FP32) CK(launch_adj_gemm_fp32(sh, c->stream));
     else CK(tc_launch_adj(sh, *tcv, c->stream));
   }
@@ -481,10 +482,51 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   Shared sh = upload_list(c, live);
   int it = 0;
   const icnnm_params& p = js[0]->p;
+  // Runs of plain (non-check) iterations are replayed from a CUDA graph of GRAPH_ITERS
+  // iterations, captured after one direct iteration (which sets kernel attributes).
+  // The legacy default stream cannot be captured; there every iteration is launched directly.
+  constexpr int GRAPH_ITERS = 25;
+  const bool graphs = c->stream != cudaStreamLegacy && c->stream != nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_counts[5] = {0, 0, 0, 0, 0};
+  auto is_check = [&](int i) { return i >= p.max_iters || (p.tol > 0 && i % p.check_every == 0); };
+  auto plain_run = [&](int from) {          // plain iterations from..from+n-1
+    int n = 0;
+    while (from + n <= p.max_iters && !is_check(from + n)) ++n;
+    return n;
+  };
   while (!live.empty()) {
+    if (graphs && !c->prof && it >= 1 && plain_run(it + 1) >= GRAPH_ITERS) {
+      if (!gexec) {
+        long long before[5];
+        for (int i = 0; i < 5; ++i) before[i] = c->pass_n[i];
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+          for (int i = 0; i < GRAPH_ITERS; ++i) engine_step(c, sh, prec, tcv, false);
+        } catch (...) {
+          cudaStreamEndCapture(c->stream, &graph);   // leave the stream usable
+          if (graph) cudaGraphDestroy(graph);
+          cudaGetLastError();
+          throw;
+        }
+        CK(cudaStreamEndCapture(c->stream, &graph));
+        const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        for (int i = 0; i < 5; ++i) {
+          graph_counts[i] = c->pass_n[i] - before[i];
+          c->pass_n[i] = before[i];
+        }
+      }
+      CK(cudaGraphLaunch(gexec, c->stream));
+      for (int i = 0; i < 5; ++i) c->pass_n[i] += graph_counts[i];
+      it += GRAPH_ITERS;
+      continue;
+    }
     ++it;
     const bool last = it >= p.max_iters;
-    const bool check = last || (p.tol > 0 && it % p.check_every == 0);
+    const bool check = is_check(it);
     engine_step(c, sh, prec, tcv, check);
     if (check) {
       std::vector<Job*> keep;
@@ -498,10 +540,14 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
       }
       if (keep.size() != live.size()) {
         live = keep;
-        if (!live.empty()) sh = upload_list(c, live);
+        if (!live.empty()) {
+          sh = upload_list(c, live);
+          if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        }
       }
     }
   }
+  if (gexec) cudaGraphExecDestroy(gexec);
   Shared all = upload_list(c, js);
   engine_objective(c, all);
   CK(cudaEventRecord(e1, c->stream));

@@ -23,7 +23,7 @@ namespace icnnm {
 constexpr int TW = 8;
 constexpr int TH = 16;
 constexpr int TILE_VOX = TW * TH;
-constexpr int NSEG = 32;          // tile segments of the first column-reduction stage
+constexpr int NSEG = 128;         // row segments of the first column-reduction stage
 constexpr int PROW = 4;           // column-partial rows per tile (one per group of 32 voxels)
 
 // Mutable per-job scalars (device memory). Kept apart from JobDev so that a job can

@@ -80,12 +80,14 @@ __global__ void reduce_cols_kernel(Shared sh, int advance) {
 }
 
 __device__ __forceinline__ double colsq_of(const JobDev& J, int kc, int c) {
-  double v[NSEG];
-#pragma unroll
-  for (int seg = 0; seg < NSEG; ++seg) v[seg] = J.colseg[(long long)seg * kc + c];
   double q = 0.0;
+  for (int s0 = 0; s0 < NSEG; s0 += 32) {
+    double v[32];
 #pragma unroll
-  for (int seg = 0; seg < NSEG; ++seg) q += v[seg];
+    for (int i = 0; i < 32; ++i) v[i] = J.colseg[(long long)(s0 + i) * kc + c];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) q += v[i];
+  }
   return q;
 }
 

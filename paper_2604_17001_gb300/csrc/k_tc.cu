@@ -7,8 +7,9 @@
 //   K-major). A = A_k(X) is never formed: the operand is kept as ncopy = min(k2, 8)
 //   bf16 copies of X, copy c shifted by c along w and wrap-padded, so that every
 //   8-voxel row segment of every tap starts on a 16-byte boundary. A TMA box of all
-//   copies (halo of the tile: Hh = TH + k1 - 1 rows x k3 frames x 8 w) lands in shared
-//   memory as rows of 16 bytes indexed rho = h*k3 + t. For a fixed w-tap sw the taps
+//   copies (halo of the tile: Hh = TH + k1 - 1 rows x k3 frames x 8 w; the copies are
+//   stored with the k3 frames of a w-segment adjacent) lands in shared memory as rows of
+//   16 bytes indexed rho = h*k3 + t. For a fixed w-tap sw the taps
 //   (sh, st) then sit at rows rho = g*k3 + r with r = k1*k3 - 1 - (sh*k3 + st), so the
 //   A operand of each MMA is an MN-major no-swizzle matrix whose core matrices overlap:
 //   M-groups (output rows g) are k3 rows apart, K-rows are consecutive rows.
@@ -37,6 +38,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ptx_sm100.cuh"
@@ -79,6 +81,7 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.pitch = rup(g.Wb, 8);
   if ((g.pitch / 8) % 2 == 0) g.pitch += 8;
   g.HBp = k3 * g.Hb * g.pitch;
+  g.cs = (g.ntt == 2 || g.ntt == 4) ? g.ntt : 1;
   return g;
 }
 
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         ptx::mbar_arrive_expect_tx(&full[s], bytes);
         for (int q = 0; q < g.nwc; ++q)
           ptx::tma_load_4d(sH + (size_t)s * g.stage_bytes + (size_t)q * g.ncopy * g.region_bytes, J.tmapX,
-                           tw * TW + 8 * (g.nwc - 1) - 8 * q, t, th * TH, 0, &full[s]);
+                           t * 8, th * TH, tw + (g.nwc - 1) - q, 0, &full[s]);
       }
       // every issued load has landed before the CTA can exit
       for (int i = (it > 2 ? it - 2 : 0); i < it; ++i)
@@ -366,13 +369,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tt = blockIdx.x % g.ntt;
   const int slot = blockIdx.x / g.ntt, nslot = gridDim.x / g.ntt;
+  // cluster of g.cs CTAs (consecutive tap tiles, same voxel tiles): each loads 1/cs of
+  // every U chunk (16/cs rows of the tile) and multicasts it to all members
+  const int cs = g.cs;
+  const int crank = tt % cs;
+  const uint16_t cmask = (uint16_t)((1u << cs) - 1u);
   const int lo = (int)((long long)sh.total_tiles * slot / nslot);
   const int hi = (int)((long long)sh.total_tiles * (slot + 1) / nslot);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < ADJ_STAGES; ++i) {
       ptx::mbar_init(&full[i], 1);
-      ptx::mbar_init(&empty[i], 1);
+      ptx::mbar_init(&empty[i], cs);       // released by the MMAs of every member
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&tfull[i], 1);
@@ -402,6 +410,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   }
   ptx::tc_fence_before();
   __syncthreads();
+  if (cs > 1) ptx::cluster_sync();          // every member's barriers exist before use
   ptx::tc_fence_after();
   const uint32_t tbase = *tslot;
   bool failed = false;
@@ -419,7 +428,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
           const uint32_t ph = (cnt / ADJ_STAGES) & 1;
           if (!ptx::mbar_wait(&empty[s], ph ^ 1)) { failed = true; break; }
           ptx::mbar_arrive_expect_tx(&full[s], CHUNK);
-          ptx::tma_load_4d(sU + (size_t)s * CHUNK, J.tmapU, c * 64, tw * TW, th * TH, t, &full[s]);
+          if (cs == 1) {
+            ptx::tma_load_4d(sU + (size_t)s * CHUNK, J.tmapU, c * 64, tw * TW, th * TH, t, &full[s]);
+          } else {
+            const int rows = TH / cs;
+            ptx::tma_load_4d_mc(sU + (size_t)s * CHUNK + (size_t)crank * rows * TW * 128, J.tmapU, c * 64, tw * TW,
+                                th * TH + crank * rows, t, &full[s], cmask);
+          }
         }
       }
       for (int i = (cnt > ADJ_STAGES ? cnt - ADJ_STAGES : 0); i < cnt; ++i)
@@ -465,7 +480,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
             const uint64_t bd = ptx::sdesc(aB + (uint32_t)c * CHUNK + kk * 32, 16, 1024, 2);
             ptx::mma_bf16(d, ad, bd, idesc, (c | kk) ? 1u : 0u);
           }
-          ptx::mma_commit(&empty[s]);
+          if (cs == 1) ptx::mma_commit(&empty[s]);
+          else ptx::mma_commit_mc(&empty[s], cmask);
         }
         if (failed) break;
         ptx::mma_commit(&tfull[b]);
@@ -537,6 +553,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   if (failed) set_fail(sh);
   ptx::tc_fence_before();
   __syncthreads();
+  if (cs > 1) ptx::cluster_sync();          // no member exits while others may still write it
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tbase, TMEM_COLS);
@@ -567,20 +584,24 @@ __global__ void build_B2_kernel(Shared sh, TcGeom g) {
   }
 }
 
-// Xc[c][tp][hp][wp] = bf16(src[(tp - (k3-1)) mod T][(hp - (k1-1)) mod H][(wp - 8(nwc-1) - c) mod W])
+// Copy c of the forward operand, element (tp, hp, wp), is
+//   bf16(src[(tp - (k3-1)) mod T][(hp - (k1-1)) mod H][(wp - 8(nwc-1) - c) mod W]),
+// stored as Xc[c][wp / 8][hp][tp][wp % 8]: the k3 frames of a 16-byte w-segment are
+// adjacent, so one TMA box row of the tile halo is k3 * 16 bytes.
 __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
   const JobDev& J = sh.jobs[blockIdx.y];
   const float* src = from_L ? J.L : J.X;
-  const long long nunits = (long long)g.ncopy * J.xTp * J.xHp * (J.xWp / 8);
+  const int nwcol = J.xWp / 8;
+  const long long nunits = (long long)g.ncopy * nwcol * J.xHp * J.xTp;
   const int pw = 8 * (g.nwc - 1);
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < nunits;
        u += (long long)gridDim.x * blockDim.x) {
-    const int wu = (int)(u % (J.xWp / 8));
-    long long r = u / (J.xWp / 8);
+    const int tp = (int)(u % J.xTp);
+    long long r = u / J.xTp;
     const int hp = (int)(r % J.xHp);
     r /= J.xHp;
-    const int tp = (int)(r % J.xTp);
-    const int c = (int)(r / J.xTp);
+    const int wu = (int)(r % nwcol);
+    const int c = (int)(r / nwcol);
     const long long rowb = ((long long)wrapi(tp - (g.k3 - 1), J.T) * J.H + wrapi(hp - (g.k1 - 1), J.H)) * J.W;
     const int w0 = wu * 8 - pw - c;
     __align__(16) __nv_bfloat16 v[8];
@@ -591,7 +612,7 @@ __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(src[rowb + wrapi(w0 + e, J.W)]);
     }
-    *reinterpret_cast<uint4*>(J.Xc + (((long long)c * J.xTp + tp) * J.xHp + hp) * J.xWp + wu * 8) =
+    *reinterpret_cast<uint4*>(J.Xc + ((((long long)c * nwcol + wu) * J.xHp + hp) * J.xTp + tp) * 8) =
         *reinterpret_cast<const uint4*>(v);
   }
 }
@@ -758,9 +779,11 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap hm[2];
   {
-    cuuint64_t dims[4] = {(cuuint64_t)Wp, (cuuint64_t)Tp, (cuuint64_t)Hp, (cuuint64_t)g.ncopy};
-    cuuint64_t str[3] = {(cuuint64_t)Hp * Wp * 2, (cuuint64_t)Wp * 2, (cuuint64_t)Tp * Hp * Wp * 2};
-    cuuint32_t box[4] = {8, (cuuint32_t)g.k3, (cuuint32_t)g.Hh, (cuuint32_t)g.ncopy}, es[4] = {1, 1, 1, 1};
+    // [c][wc][hp][tp*8]: dim0 = (tp, w%8) flattened, dim1 = hp, dim2 = wc, dim3 = c
+    const int nwcol = Wp / 8;
+    cuuint64_t dims[4] = {(cuuint64_t)Tp * 8, (cuuint64_t)Hp, (cuuint64_t)nwcol, (cuuint64_t)g.ncopy};
+    cuuint64_t str[3] = {(cuuint64_t)Tp * 16, (cuuint64_t)Hp * Tp * 16, (cuuint64_t)nwcol * Hp * Tp * 16};
+    cuuint32_t box[4] = {(cuuint32_t)(8 * g.k3), (cuuint32_t)g.Hh, 1, (cuuint32_t)g.ncopy}, es[4] = {1, 1, 1, 1};
     if (enc(&hm[0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->Xc, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
@@ -769,7 +792,7 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   {
     cuuint64_t dims[4] = {(cuuint64_t)g.kc, (cuuint64_t)d->W, (cuuint64_t)d->H, (cuuint64_t)d->T};
     cuuint64_t str[3] = {(cuuint64_t)g.kc * 2, (cuuint64_t)d->W * g.kc * 2, (cuuint64_t)d->H * d->W * g.kc * 2};
-    cuuint32_t box[4] = {64, TW, TH, 1}, es[4] = {1, 1, 1, 1};
+    cuuint32_t box[4] = {64, TW, (cuuint32_t)(TH / g.cs), 1}, es[4] = {1, 1, 1, 1};
     if (enc(&hm[1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->U, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
@@ -807,16 +830,35 @@ cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, 
   return cudaGetLastError();
 }
 
-static int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
+// Per-device launch facts, set up once outside any stream capture: the SM count, the
+// shared-memory opt-in of both tcgen05 kernels and the resident-cluster count of the
+// adjoint for each (shared memory, cluster size).
+namespace {
+constexpr int MAX_DEV = 64;
+struct DevFacts {
+  bool ready = false;
+  int sms = 1;
+  std::vector<std::pair<long long, int>> clusters;   // key smem*16+cs -> max active clusters
+};
+DevFacts g_dev[MAX_DEV];
+std::mutex g_dev_mu;
+
+DevFacts& dev_facts() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= MAX_DEV) dev = 0;
+  DevFacts& f = g_dev[dev];
+  if (!f.ready) {
+    int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+    f.sms = n > 0 ? n : 1;
+    cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    f.ready = true;
   }
-  return n;
+  return f;
 }
+}  // namespace
 
 cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st) {
   FwdArgs a;
@@ -825,24 +867,62 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
   for (int i = 0; i < 64; ++i) { a.tab.boff[i] = v.boff[i]; a.tab.kstr[i] = v.kstr[i]; }
   a.mode = mode;
   const size_t smem = fwd_smem(v.g);
-  cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int per = std::max(1, std::min(num_sms() / v.g.nct, (sh.total_tiles + 0)));
+  int sms;
+  {
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    sms = dev_facts().sms;
+  }
+  const int per = std::max(1, std::min(sms / v.g.nct, sh.total_tiles));
   fwd_tc_kernel<<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st) {
+cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st) {
   build_B2_kernel<<<dim3(sh.njobs, v.g.ntt * v.g.nch_a), 256, 0, st>>>(sh, v.g);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st) {
   AdjArgs a;
   a.sh = sh;
   a.g = v.g;
   const size_t smem = adj_smem(v.g);
-  cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int per = std::max(1, std::min(num_sms() / v.g.ntt, sh.total_tiles));
-  adj_tc_kernel<<<per * v.g.ntt, TC_THREADS, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.numAttrs = 0;
+  int per;
+  {
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevFacts& f = dev_facts();
+    per = std::max(1, std::min(f.sms / v.g.ntt, sh.total_tiles));
+    if (v.g.cs > 1) {
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = v.g.cs;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      // only as many clusters as can be resident at once (the tile ranges are static)
+      const long long key = (long long)smem * 16 + v.g.cs;
+      int maxc = 0;
+      for (auto& kv : f.clusters)
+        if (kv.first == key) maxc = kv.second;
+      if (!maxc) {
+        cfg.gridDim = dim3(per * v.g.ntt);
+        if (cudaOccupancyMaxActiveClusters(&maxc, adj_tc_kernel, &cfg) != cudaSuccess || maxc < 1) {
+          cudaGetLastError();
+          maxc = 1;
+        }
+        f.clusters.emplace_back(key, maxc);
+      }
+      per = std::max(1, std::min(per, maxc * v.g.cs / v.g.ntt));
+    }
+  }
+  cfg.gridDim = dim3(per * v.g.ntt);
+  return cudaLaunchKernelEx(&cfg, adj_tc_kernel, a);
 }
 
 cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st) {

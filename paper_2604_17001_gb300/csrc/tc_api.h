@@ -23,6 +23,8 @@ struct TcGeom {
   int kcp;          // channels rounded up to 64
   int nch_a;        // 64-wide SW128 chunks of the adjoint A image
   int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*k3
+  int cs;           // adjoint cluster size: CTAs of one voxel-tile range that share U
+                    // tiles by TMA multicast (ntt if ntt is 2 or 4, else 1)
   int pitch, HBp;   // shared-memory row pitch of the halo buffers (an odd multiple of 8,
                     // >= Wb, so 4 rows x 8 voxels hit 32 banks) and k3*Hb*pitch
 };
@@ -44,6 +46,8 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
 int tc_nrp(int k);
 cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st);
 cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st);
+// B = V D image per job (bf16, SW128), then the adjoint GEMM + col2im into halo partials.
+cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st);
 cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st);
 cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st);
 
