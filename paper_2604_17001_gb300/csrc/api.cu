@@ -400,9 +400,15 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js) {
 }
 
 void run_fwd(icnnm_ctx* c, const Shared& sh, int prec, int mode, const TcVData* tcv) {
-  PassScope ps(c, 0, 1);
+  // the once-per-solve FP32 passes (theta0, objective) count as "other"
+  PassScope ps(c, mode == 0 || mode == 4 ? 3 : 0, 1);
   if (prec == ICNNM_FP32 || mode == 0 || mode == 4) CK(launch_fwd_fp32(sh, mode, c->stream));
   else CK(tc_launch_fwd(sh, *tcv, mode, c->stream));
+}
+
+// Row groups of the column partials written by the update pass (0 = one per tile).
+int fwd_slots(const Shared& sh, int prec, const TcVData* tcv) {
+  return prec == ICNNM_BF16 ? tc_fwd_slots(sh, *tcv) : 0;
 }
 
 #define OTHER(n, expr)            \
@@ -419,12 +425,12 @@ void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
   Shared sh = upload_list(c, js);
   OTHER(1, launch_init_L(sh, c->stream));
   run_fwd(c, sh, ICNNM_FP32, 0, tcv);
-  OTHER(1, launch_reduce_cols(sh, 0, c->stream));
+  OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
   OTHER(1, launch_theta0(sh, js[0]->p.theta0, c->stream));
   OTHER(1, launch_scale_X(sh, c->stream));
   if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
   run_fwd(c, sh, prec, 2, tcv);
-  OTHER(1, launch_reduce_cols(sh, 0, c->stream));
+  OTHER(1, launch_reduce_cols(sh, 0, fwd_slots(sh, prec, tcv), c->stream));
 }
 
 // One ADMM iteration for every job of the list. `check` (per list) adds the residual.
@@ -448,12 +454,12 @@ void engine_step(icnnm_ctx* c, const Shared& sh, int prec, const TcVData* tcv, b
   }
   if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
   run_fwd(c, sh, prec, 1, tcv);
-  OTHER(1, launch_reduce_cols(sh, 1, c->stream));
+  OTHER(1, launch_reduce_cols(sh, 1, fwd_slots(sh, prec, tcv), c->stream));
 }
 
 void engine_objective(icnnm_ctx* c, const Shared& sh) {
   run_fwd(c, sh, ICNNM_FP32, 4, nullptr);
-  OTHER(1, launch_reduce_cols(sh, 0, c->stream));
+  OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
   OTHER(1, launch_finish(sh, 2, c->stream));
 }
 

@@ -54,7 +54,8 @@ struct JobDev {
   __nv_bfloat16* Xc;    // BF16 path: wrap-padded, w-shifted copies of the operand
   void* U;              // m x kc shifted multiplier, row-major [voxel][channel]:
                         //   FP32 (FP32 path) or BF16 (BF16 path)
-  float* part;          // column partial sums of ||.||^2: [ntiles][PROW][kc]
+  float* part;          // column partial sums of ||.||^2: [rows][PROW][kc], one row per
+                        //   tile (FP32 passes) or per forward CTA slot (BF16 pass)
   float* rpart;         // per-tile residual partials: [ntiles][nrp]
   float* lpart;         // per-tile ||L'||^2 partials: [ntiles]
   double* colseg;       // first-stage column sums: [NSEG][kc]
@@ -62,8 +63,10 @@ struct JobDev {
   float* D;             // kc, 1 - s
   float* G;             // FP32 path: G^T = (V D) U^T, [k][m]; BF16 path: col2im partials
   __nv_bfloat16* B2img; // BF16 path: A-operand images of the adjoint pass (V D)
-  const void* tmapX;    // BF16 path: TMA map (CUtensorMap, device memory) of Xc
-  const void* tmapU;    // BF16 path: TMA map of U
+  const void* tmapX;    // BF16 path: TMA map (CUtensorMap, device memory) of Xc, 8 copies
+  const void* tmapX2;   // BF16 path: the same with k2 - 8 copies (kernels wider than 8)
+  const void* tmapU;    // BF16 path: TMA map of U, adjoint box (16/cs rows of a tile)
+  const void* tmapUf;   // BF16 path: TMA map of U, forward box (a whole tile)
   const int* glist;     // BF16 path: col2im gather lists (see k_tc.cu)
   int xTp, xHp, xWp;    // BF16 path: dims of each copy in Xc
 };
@@ -121,7 +124,9 @@ __device__ __forceinline__ float l_update(const JobDev& J, int k, long long v, f
 // ---------------------------------------------------------------------------------
 // k_common.cu
 cudaError_t launch_init_L(const Shared& sh, cudaStream_t st);
-cudaError_t launch_reduce_cols(const Shared& sh, int advance, cudaStream_t st);
+// slots = 0: the partials have one row group per tile; slots > 0: per forward CTA slot,
+// min(slots, ntiles) row groups per job.
+cudaError_t launch_reduce_cols(const Shared& sh, int advance, int slots, cudaStream_t st);
 cudaError_t launch_theta0(const Shared& sh, double theta0_user, cudaStream_t st);
 cudaError_t launch_scale_X(const Shared& sh, cudaStream_t st);
 cudaError_t launch_scalars(const Shared& sh, cudaStream_t st);

@@ -40,17 +40,18 @@ __global__ void init_L_kernel(Shared sh) {
   if (J.X) J.X[v] = x;
 }
 
-// First reduction stage: colseg[seg][c] = sum over the partial rows (PROW per tile) of
+// First reduction stage: colseg[seg][c] = sum over the partial rows (PROW per tile or
+// per forward CTA slot) of
 // segment seg of part[row][c], in FP64; warp w adds rows lo+w, lo+w+8, ... in increasing
 // order and the 8 warp sums are combined in warp order. Block = (job, 32 channels, segment).
 // With `advance`, one block per job moves theta to theta_next and counts the
 // iteration (every kernel of the iteration that reads theta has run by then).
-__global__ void reduce_cols_kernel(Shared sh, int advance) {
+__global__ void reduce_cols_kernel(Shared sh, int advance, int slots) {
   const JobDev& J = sh.jobs[blockIdx.x];
   const int c = blockIdx.y * 32 + (threadIdx.x & 31);
   const int warp = threadIdx.x >> 5;
   const int seg = blockIdx.z;
-  const int nrows = J.ntiles * PROW;
+  const int nrows = (slots > 0 ? min(slots, J.ntiles) : J.ntiles) * PROW;
   const int lo = (int)((long long)nrows * seg / NSEG);
   const int hi = (int)((long long)nrows * (seg + 1) / NSEG);
   double acc = 0.0;
@@ -207,9 +208,9 @@ cudaError_t launch_init_L(const Shared& sh, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_cols(const Shared& sh, int advance, cudaStream_t st) {
+cudaError_t launch_reduce_cols(const Shared& sh, int advance, int slots, cudaStream_t st) {
   dim3 grid(sh.njobs, (sh.kc + 31) / 32, NSEG);
-  reduce_cols_kernel<<<grid, 256, 0, st>>>(sh, advance);
+  reduce_cols_kernel<<<grid, 256, 0, st>>>(sh, advance, slots);
   return cudaGetLastError();
 }
 

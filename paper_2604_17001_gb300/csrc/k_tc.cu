@@ -52,11 +52,14 @@ constexpr int EPI_WARPS = 16;        // 4 per TMEM lane quarter, each owning 32 
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int LMAX = 16;             // (tile, offset) pairs per coordinate in the gather
 constexpr int ADJ_STAGES = 4;
+constexpr int FWD_USTAGES = 2;      // U tile stages of the forward pass (fewer if short of space)
+constexpr int USTAGE = 2 * 16384;    // one U tile: 128 voxels x 128 channels bf16 (two boxes)
 constexpr int CHUNK = 16384;         // one SW128 K-chunk: 128 rows x 128 bytes
 constexpr uint32_t TMEM_COLS = 256;
 constexpr int SMEM_LIMIT = 227 * 1024;
 
 int rup(int x, int a) { return (x + a - 1) / a * a; }
+size_t fwd_smem_n(const TcGeom& g, int nus);
 
 TcGeom make_geom(int k1, int k2, int k3) {
   TcGeom g{};
@@ -70,7 +73,7 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.nwc = (k2 + 7) / 8;
   g.Hh = TH + k1 - 1;
   g.region_bytes = g.Hh * k3 * 16;
-  g.stage_bytes = rup(g.nwc * g.ncopy * g.region_bytes + 8 * 16, 1024);
+  g.stage_bytes = rup(k2 * g.region_bytes + 8 * 16, 1024);   // k2 copies + 8 zero rows
   g.nct = (g.k + 127) / 128;
   g.ntt = (g.k + 127) / 128;
   g.kcp = rup(g.kc, 64);
@@ -82,10 +85,15 @@ TcGeom make_geom(int k1, int k2, int k3) {
   if ((g.pitch / 8) % 2 == 0) g.pitch += 8;
   g.HBp = k3 * g.Hb * g.pitch;
   g.cs = (g.ntt == 2 || g.ntt == 4) ? g.ntt : 1;
+  g.nus = FWD_USTAGES;
+  while (g.nus > 1 && fwd_smem_n(g, g.nus) > SMEM_LIMIT) --g.nus;
   return g;
 }
 
-size_t fwd_smem(const TcGeom& g) { return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + 256; }
+size_t fwd_smem_n(const TcGeom& g, int nus) {
+  return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + (size_t)nus * USTAGE + EPI_WARPS * 32 * 4 + 256;
+}
+size_t fwd_smem(const TcGeom& g) { return fwd_smem_n(g, g.nus); }
 size_t adj_smem(const TcGeom& g) {
   return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 2 * (size_t)g.HBp * 4 + 128 * 4 + 256;
 }
@@ -122,6 +130,42 @@ __device__ __forceinline__ void set_fail(const Shared& sh) {
   if (sh.njobs > 0) atomicExch(&sh.jobs[0].sc->status, 1);
 }
 
+// Sum a[j] (j = 0..31) over the 32 lanes of the warp in a fixed order and store the sum
+// for j = lane at dst[lane] (if `ok`): a transpose-reduce in five halving steps, after
+// which lane l holds the total of value l.
+__device__ __forceinline__ void warp_colsum_store(float (&a)[32], int lane, float* dst, bool ok) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float snd = (lane & 16) ? a[k] : a[k + 16];
+    const float kp = (lane & 16) ? a[k + 16] : a[k];
+    a[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float snd = (lane & 8) ? a[k] : a[k + 8];
+    const float kp = (lane & 8) ? a[k + 8] : a[k];
+    a[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float snd = (lane & 4) ? a[k] : a[k + 4];
+    const float kp = (lane & 4) ? a[k + 4] : a[k];
+    a[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 4);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float snd = (lane & 2) ? a[k] : a[k + 2];
+    const float kp = (lane & 2) ? a[k + 2] : a[k];
+    a[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 2);
+  }
+  {
+    const float snd = (lane & 1) ? a[0] : a[1];
+    const float kp = (lane & 1) ? a[1] : a[0];
+    a[0] = kp + __shfl_xor_sync(0xffffffffu, snd, 1);
+  }
+  if (ok) dst[lane] = a[0];
+}
+
 // ---------------------------------------------------------------------------------
 // Forward pass
 // ---------------------------------------------------------------------------------
@@ -130,19 +174,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   uint8_t* sm = align1k(smraw);
   const TcGeom& g = a.g;
   const Shared& sh = a.sh;
-  uint8_t* sA = sm;
-  uint8_t* sH = sm + (size_t)g.nch_f * CHUNK;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + 2 * (size_t)g.stage_bytes);
-  uint64_t* full = bars;        // [2]
-  uint64_t* empty = bars + 2;   // [2]
-  uint64_t* tfull = bars + 4;   // [2]
-  uint64_t* tempty = bars + 6;  // [2]
-  uint64_t* abar = bars + 8;
-  uint64_t* dbar = bars + 9;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 10);
+  uint8_t* sA = sm;                                              // V^T image of this channel tile
+  uint8_t* sH = sA + (size_t)g.nch_f * CHUNK;                    // [2] halo stages
+  uint8_t* sU = sH + 2 * (size_t)g.stage_bytes;                  // [g.nus] U tiles
+  float* sD = reinterpret_cast<float*>(sU + (size_t)g.nus * USTAGE);   // [EPI_WARPS][32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sD + EPI_WARPS * 32);
+  uint64_t* full = bars;                   // [2] halo landed
+  uint64_t* empty = bars + 2;              // [2] halo consumed by the MMAs
+  uint64_t* tfull = bars + 4;              // [2] accumulator ready
+  uint64_t* tempty = bars + 6;             // [2] accumulator read out
+  uint64_t* ufull = bars + 8;              // [g.nus] U tile landed
+  uint64_t* uempty = bars + 8 + g.nus;   // [g.nus] U stage free again
+  uint64_t* abar = bars + 8 + 2 * g.nus;
+  uint64_t* dbar = abar + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(dbar + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ct = blockIdx.x % g.nct;
   const int slot = blockIdx.x / g.nct, nslot = gridDim.x / g.nct;
+  const int mode = a.mode;
+  const bool rdU = (mode == 1 || mode == 3);   // U is read (TMA) in these modes
+  const bool wrU = (mode == 1 || mode == 2);   // U' is written (TMA store) in these modes
+  const int nbox = (ct * 128 + 64 < sh.kc) ? 2 : 1;   // 64-channel boxes of U inside kc
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -151,8 +204,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       ptx::mbar_init(&tfull[i], 1);
       ptx::mbar_init(&tempty[i], EPI_WARPS);
     }
+    for (int i = 0; i < g.nus; ++i) {
+      ptx::mbar_init(&ufull[i], 1);
+      ptx::mbar_init(&uempty[i], 1);
+    }
     ptx::mbar_init(abar, 1);
     ptx::mbar_init(dbar, 1);
+    *abort = 0;
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
@@ -161,7 +219,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   }
   // zero rows after the copies of each stage (read by the padded taps, times zero)
   for (int i = threadIdx.x; i < 2 * 32; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(sH + (i / 32) * g.stage_bytes + g.nwc * g.ncopy * g.region_bytes)[i % 32] = 0u;
+    reinterpret_cast<uint32_t*>(sH + (i / 32) * g.stage_bytes + g.k2 * g.region_bytes)[i % 32] = 0u;
   ptx::fence_proxy_async_smem();
   ptx::tc_fence_before();
   __syncthreads();
@@ -174,28 +232,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       ptx::mbar_arrive_expect_tx(abar, (uint32_t)g.nch_f * CHUNK);
       const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.VtImg) + (size_t)ct * g.nch_f * CHUNK;
       for (int c = 0; c < g.nch_f; ++c) ptx::bulk_g2s(sA + (size_t)c * CHUNK, src + (size_t)c * CHUNK, CHUNK, abar);
-      const uint32_t bytes = (uint32_t)(g.nwc * g.ncopy * g.region_bytes);
+      const uint32_t hbytes = (uint32_t)(g.k2 * g.region_bytes);
       int it = 0;
       for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
         const int s = it & 1;
         const uint32_t ph = (it >> 1) & 1;
-        if (!ptx::mbar_wait(&empty[s], ph ^ 1)) { failed = true; break; }
+        if (!ptx::mbar_wait_abortable(&empty[s], ph ^ 1, abort)) { failed = true; break; }
         const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
         const JobDev& J = sh.jobs[jb];
         const int tile = tg - sh.job_tile0[jb];
         const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
-        ptx::mbar_arrive_expect_tx(&full[s], bytes);
+        ptx::mbar_arrive_expect_tx(&full[s], hbytes);
+        // w-chunk q holds the copies of taps sw = 8q .. min(8q + 7, k2 - 1); the last
+        // chunk of a kernel wider than 8 uses the map whose box has only k2 - 8 copies
         for (int q = 0; q < g.nwc; ++q)
-          ptx::tma_load_4d(sH + (size_t)s * g.stage_bytes + (size_t)q * g.ncopy * g.region_bytes, J.tmapX,
-                           t * 8, th * TH, tw + (g.nwc - 1) - q, 0, &full[s]);
+          ptx::tma_load_4d(sH + (size_t)s * g.stage_bytes + (size_t)q * g.ncopy * g.region_bytes,
+                           (q > 0) ? J.tmapX2 : J.tmapX, t * 8, th * TH, tw + (g.nwc - 1) - q, 0, &full[s]);
+        if (rdU) {
+          const int us = it % g.nus;
+          const uint32_t uph = (it / g.nus) & 1;
+          if (!ptx::mbar_wait_abortable(&uempty[us], uph ^ 1, abort)) { failed = true; ++it; break; }
+          ptx::mbar_arrive_expect_tx(&ufull[us], (uint32_t)nbox * CHUNK);
+          for (int bx = 0; bx < nbox; ++bx)
+            ptx::tma_load_4d(sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, J.tmapUf, ct * 128 + bx * 64, tw * TW,
+                             th * TH, t, &ufull[us]);
+        }
       }
       // every issued load has landed before the CTA can exit
       for (int i = (it > 2 ? it - 2 : 0); i < it; ++i)
         if (!ptx::mbar_wait(&full[i & 1], (i >> 1) & 1)) failed = true;
+      if (rdU)
+        for (int i = (it > g.nus ? it - g.nus : 0); i < it; ++i)
+          if (!ptx::mbar_wait(&ufull[i % g.nus], (i / g.nus) & 1)) failed = true;
+      if (failed) *abort = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      if (!ptx::mbar_wait(abar, 0)) failed = true;
+      if (!ptx::mbar_wait_abortable(abar, 0, abort)) failed = true;
       // A = halo (voxels x taps, MN-major, overlapping core matrices), B = V^T image
       // (channels x taps, K-major SW128): D[voxel][channel] in TMEM.
       const uint32_t idesc = ptx::idesc_bf16(128, 128, 1, 0);
@@ -205,8 +278,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       for (int tg = slot; !failed && tg < sh.total_tiles; tg += nslot, ++it) {
         const int s = it & 1, b = it & 1;
         const uint32_t ph = (it >> 1) & 1;
-        if (!ptx::mbar_wait(&full[s], ph)) { failed = true; break; }
-        if (!ptx::mbar_wait(&tempty[b], ph ^ 1)) { failed = true; break; }
+        if (!ptx::mbar_wait_abortable(&full[s], ph, abort)) { failed = true; break; }
+        if (!ptx::mbar_wait_abortable(&tempty[b], ph ^ 1, abort)) { failed = true; break; }
         ptx::tc_fence_after();
         const uint32_t d = tbase + (uint32_t)b * 128;
         const uint32_t hs = hB + (uint32_t)s * g.stage_bytes;
@@ -220,53 +293,64 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       }
       ptx::mma_commit(dbar);
       if (!ptx::mbar_wait(dbar, 0)) failed = true;
+      if (failed) *abort = 1;
     }
   } else {
     // Epilogue: 16 warps. Warp w reads TMEM lanes 32q..32q+31 (q = w % 4), i.e. voxels
     // 32q + lane of the tile, and columns 32g..32g+31 (g = (w - 2) / 4), i.e. 32 channels.
-    // A TMEM load gives one voxel 32 consecutive channels, so U is read and written with
-    // 16-byte vector accesses; the U and D loads of a tile are issued before waiting for
-    // its accumulator.
+    // U of the tile sits in a shared-memory stage (two SW128 boxes of 64 channels, row =
+    // voxel), loaded by TMA ahead of time; U' is written back into the stage and stored
+    // by TMA. Column sums of U'^2 stay in registers (per voxel lane, per channel) across
+    // all tiles of a job that this CTA processes, and are reduced over the warp once per
+    // job into one partial row per (CTA, voxel quarter).
+    // A failed wait marks the thread failed; it still passes every named barrier (the
+    // other warps may be waiting there) but does no more waiting.
     const int q = warp & 3;
     const int cg = (warp - 2) >> 2;
+    const int ew = warp - 2;
     const int vox = q * 32 + lane;
-    const int mode = a.mode;
-    const bool rd = (mode == 1 || mode == 3);
-    const int c0 = ct * 128 + cg * 32;                    // first channel of this warp
-    const int nchk = max(0, min(2, (sh.kc - c0) / 16));   // chunks of 16 channels inside U
+    const int c0 = ct * 128 + cg * 32;                          // first channel of this warp
+    const int nun = max(0, min(4, (sh.kc - c0) / 8));           // 8-channel units inside kc
+    const uint32_t usw = (uint32_t)(lane & 7);                  // SW128 row phase (vox % 8)
+    float* sDw = sD + ew * 32;
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    int cur = -1, row0 = 0;
     int it = 0;
     for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
-      const int b = it & 1;
-      const uint32_t ph = (it >> 1) & 1;
       const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
       const JobDev& J = sh.jobs[jb];
       const int tile = tg - sh.job_tile0[jb];
+      if (jb != cur) {
+        if (cur >= 0 && wrU) {
+          // flush the previous job's column sums
+          const JobDev& P = sh.jobs[cur];
+          warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        }
+        cur = jb;
+        row0 = tile;
+        if (rdU) {
+          const float* src = mode == 1 ? J.D : J.s;
+          const float sc = mode == 1 ? 1.f : (float)(1.0 / J.sc->theta);
+          sDw[lane] = (c0 + lane < sh.kc) ? src[c0 + lane] * sc : 0.f;
+          __syncwarp();
+        }
+      }
       const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
       const int h = th * TH + (vox >> 3), w = tw * TW + (vox & 7);
       const bool valid = h < J.H && w < J.W;
-      __nv_bfloat16* Urow = reinterpret_cast<__nv_bfloat16*>(J.U) +
-                            (valid ? (((size_t)t * J.H + h) * J.W + w) * sh.kc : 0);
-      uint4 uv[4];
-      float dv[32];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) uv[i] = make_uint4(0, 0, 0, 0);
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-        if (rd && valid && i < nchk) {
-          uv[2 * i] = *reinterpret_cast<const uint4*>(Urow + c0 + 16 * i);
-          uv[2 * i + 1] = *reinterpret_cast<const uint4*>(Urow + c0 + 16 * i + 8);
-        }
-      if (mode == 1 || mode == 3) {
-        const float* src = mode == 1 ? J.D : J.s;
-        const float sc = mode == 1 ? 1.f : (float)(1.0 / J.sc->theta);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (c0 + 4 * i < sh.kc) d4 = *reinterpret_cast<const float4*>(src + c0 + 4 * i);
-          dv[4 * i] = d4.x * sc; dv[4 * i + 1] = d4.y * sc; dv[4 * i + 2] = d4.z * sc; dv[4 * i + 3] = d4.w * sc;
-        }
-      }
-      if (!ptx::mbar_wait(&tfull[b], ph)) { failed = true; break; }
+      const int b = it & 1;
+      const uint32_t ph = (it >> 1) & 1;
+      const int us = it % g.nus;
+      const uint32_t uph = (it / g.nus) & 1;
+      uint8_t* urow = sU + (size_t)us * USTAGE + (size_t)(cg >> 1) * CHUNK + (size_t)vox * 128;
+      const uint32_t u0 = (uint32_t)(cg & 1) * 4;
+      if (!failed)
+        failed = !ptx::mbar_wait_abortable(rdU ? &ufull[us] : &uempty[us], rdU ? uph : (uph ^ 1), abort);
+      if (!failed) failed = !ptx::mbar_wait_abortable(&tfull[b], ph, abort);
       ptx::tc_fence_after();
       float e[32];
       ptx::tmem_ld32(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cg * 32, e);
@@ -274,66 +358,80 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&tempty[b]);     // the accumulator is in registers
-      const __nv_bfloat16* ub = reinterpret_cast<const __nv_bfloat16*>(uv);
       if (mode == 3) {
         float rsum = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float r = fmaf(__bfloat162float(ub[j]), dv[j], e[j]);
-          rsum = (valid && j < 16 * nchk) ? fmaf(r, r, rsum) : rsum;
+        for (int u = 0; u < 4; ++u) {
+          if (u < nun) {
+            const uint4 x = *reinterpret_cast<const uint4*>(urow + (((u0 + u) ^ usw) << 4));
+            const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
+            const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
+            const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+            const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float uf = __uint_as_float((j & 1) ? (xw[j >> 1] & 0xffff0000u) : (xw[j >> 1] << 16));
+              const float r = fmaf(uf, dv[j], e[8 * u + j]);
+              rsum = fmaf(r, r, rsum);
+            }
+          }
         }
+        if (!valid) rsum = 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
         if (lane == 0) J.rpart[(size_t)tile * sh.nrp + ct * 16 + cg * 4 + q] = rsum;
-        continue;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u < nun) {
+            uint4* p = reinterpret_cast<uint4*>(urow + (((u0 + u) ^ usw) << 4));
+            float dv[8];
+            uint32_t xw[4] = {0u, 0u, 0u, 0u};
+            if (mode == 1) {
+              const uint4 x = *p;
+              xw[0] = x.x; xw[1] = x.y; xw[2] = x.z; xw[3] = x.w;
+              const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
+              const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
+              dv[0] = d0.x; dv[1] = d0.y; dv[2] = d0.z; dv[3] = d0.w;
+              dv[4] = d1.x; dv[5] = d1.y; dv[6] = d1.z; dv[7] = d1.w;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) dv[j] = 0.f;
+            }
+            uint32_t ow[4];
+#pragma unroll
+            for (int j2 = 0; j2 < 4; ++j2) {
+              const float ulo = __uint_as_float(xw[j2] << 16), uhi = __uint_as_float(xw[j2] & 0xffff0000u);
+              const float nlo = fmaf(ulo, dv[2 * j2], -e[8 * u + 2 * j2]);
+              const float nhi = fmaf(uhi, dv[2 * j2 + 1], -e[8 * u + 2 * j2 + 1]);
+              const __nv_bfloat162 pr = __floats2bfloat162_rn(nlo, nhi);
+              ow[j2] = *reinterpret_cast<const uint32_t*>(&pr);
+              const float rlo = __uint_as_float(ow[j2] << 16), rhi = __uint_as_float(ow[j2] & 0xffff0000u);
+              acc[8 * u + 2 * j2] = valid ? fmaf(rlo, rlo, acc[8 * u + 2 * j2]) : acc[8 * u + 2 * j2];
+              acc[8 * u + 2 * j2 + 1] = valid ? fmaf(rhi, rhi, acc[8 * u + 2 * j2 + 1]) : acc[8 * u + 2 * j2 + 1];
+            }
+            *p = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+          }
+        }
+        ptx::fence_proxy_async_smem();    // U' in shared memory -> the TMA store
       }
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        if (i >= nchk) break;
-        __align__(16) __nv_bfloat16 o[16];
-        float sq[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int jj = 16 * i + j;
-          const float un = mode == 1 ? fmaf(__bfloat162float(ub[jj]), dv[jj], -e[jj]) : -e[jj];
-          o[j] = __float2bfloat16(un);
-          const float uf = __bfloat162float(o[j]);
-          sq[j] = valid ? uf * uf : 0.f;
+      ptx::named_bar_sync(1, 32 * EPI_WARPS);
+      if (ew == 0 && lane == 0) {
+        if (wrU) {
+          for (int bx = 0; bx < nbox; ++bx)
+            ptx::tma_store_4d(J.tmapUf, sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, ct * 128 + bx * 64, tw * TW,
+                              th * TH, t);
+          ptx::bulk_commit_group();
+          ptx::bulk_wait_group_read0();   // the stage may be refilled once the store has read it
         }
-        if (valid) {
-          *reinterpret_cast<uint4*>(Urow + c0 + 16 * i) = *reinterpret_cast<const uint4*>(o);
-          *reinterpret_cast<uint4*>(Urow + c0 + 16 * i + 8) = *reinterpret_cast<const uint4*>(o + 8);
-        }
-        // column sums over the warp's 32 voxels: transpose-reduce 16 values across the 32
-        // lanes (fixed order); lane l ends with channel ((l >> 1) & 15) of this chunk
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float snd = (lane & 16) ? sq[k] : sq[k + 8];
-          const float kp = (lane & 16) ? sq[k + 8] : sq[k];
-          sq[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 16);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float snd = (lane & 8) ? sq[k] : sq[k + 4];
-          const float kp = (lane & 8) ? sq[k + 4] : sq[k];
-          sq[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const float snd = (lane & 4) ? sq[k] : sq[k + 2];
-          const float kp = (lane & 4) ? sq[k + 2] : sq[k];
-          sq[k] = kp + __shfl_xor_sync(0xffffffffu, snd, 4);
-        }
-        {
-          const float snd = (lane & 2) ? sq[0] : sq[1];
-          const float kp = (lane & 2) ? sq[1] : sq[0];
-          sq[0] = kp + __shfl_xor_sync(0xffffffffu, snd, 2);
-        }
-        sq[0] += __shfl_xor_sync(0xffffffffu, sq[0], 1);
-        if ((lane & 1) == 0)
-          J.part[((size_t)tile * PROW + q) * sh.kc + c0 + 16 * i + ((lane >> 1) & 15)] = sq[0];
+        ptx::mbar_arrive(&uempty[us]);
       }
     }
+    if (cur >= 0 && wrU) {
+      const JobDev& P = sh.jobs[cur];
+      warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+    }
+    if (ew == 0 && lane == 0 && wrU) ptx::bulk_wait_group0();   // U' stores complete
   }
   if (failed) set_fail(sh);
   ptx::tc_fence_before();
@@ -758,7 +856,7 @@ size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g) {
   add((size_t)g.ncopy * Tp * Hp * Wp * 2);             // Xc
   add((size_t)ntiles * g.ntt * g.HB * 4);              // col2im partials
   add((size_t)g.ntt * g.nch_a * CHUNK);                // V D images
-  add(2 * sizeof(CUtensorMap));                        // TMA maps
+  add(4 * sizeof(CUtensorMap));                        // TMA maps
   add((size_t)(H + W) * (1 + LMAX) * 4);               // gather lists
   return b;
 }
@@ -772,28 +870,34 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   d->Xc = (__nv_bfloat16*)take((size_t)g.ncopy * Tp * Hp * Wp * 2);
   d->G = (float*)take((size_t)d->ntiles * g.ntt * g.HB * 4);
   d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * CHUNK);
-  CUtensorMap* tm = (CUtensorMap*)take(2 * sizeof(CUtensorMap));
+  CUtensorMap* tm = (CUtensorMap*)take(4 * sizeof(CUtensorMap));
   int* gl = (int*)take((size_t)(d->H + d->W) * (1 + LMAX) * 4);
   if (off > total) return cudaErrorInvalidValue;
   EncodeTiledFn enc = encoder();
   if (!enc) return cudaErrorNotSupported;
-  CUtensorMap hm[2];
-  {
-    // [c][wc][hp][tp*8]: dim0 = (tp, w%8) flattened, dim1 = hp, dim2 = wc, dim3 = c
+  CUtensorMap hm[4];
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  // Xc as [c][wc][hp][tp*8]: dim0 = (tp, w%8) flattened, dim1 = hp, dim2 = wc, dim3 = c.
+  // Map 0 loads all ncopy copies of a w-chunk; map 1 only the first k2 - 8 (the last
+  // w-chunk of a kernel wider than 8).
+  for (int mi = 0; mi < 2; ++mi) {
     const int nwcol = Wp / 8;
+    const int nc = mi == 0 ? g.ncopy : std::max(1, g.k2 - 8 * (g.nwc - 1));
     cuuint64_t dims[4] = {(cuuint64_t)Tp * 8, (cuuint64_t)Hp, (cuuint64_t)nwcol, (cuuint64_t)g.ncopy};
     cuuint64_t str[3] = {(cuuint64_t)Tp * 16, (cuuint64_t)Hp * Tp * 16, (cuuint64_t)nwcol * Hp * Tp * 16};
-    cuuint32_t box[4] = {(cuuint32_t)(8 * g.k3), (cuuint32_t)g.Hh, 1, (cuuint32_t)g.ncopy}, es[4] = {1, 1, 1, 1};
-    if (enc(&hm[0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->Xc, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    cuuint32_t box[4] = {(cuuint32_t)(8 * g.k3), (cuuint32_t)g.Hh, 1, (cuuint32_t)nc};
+    if (enc(&hm[mi], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->Xc, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  {
+  // U as [t][h][w][kc]: map 2 = adjoint box (64 channels x 8 w x 16/cs h), map 3 =
+  // forward box (64 channels x 8 w x 16 h), both SW128 (row = voxel, 128 bytes).
+  for (int mi = 2; mi < 4; ++mi) {
     cuuint64_t dims[4] = {(cuuint64_t)g.kc, (cuuint64_t)d->W, (cuuint64_t)d->H, (cuuint64_t)d->T};
     cuuint64_t str[3] = {(cuuint64_t)g.kc * 2, (cuuint64_t)d->W * g.kc * 2, (cuuint64_t)d->H * d->W * g.kc * 2};
-    cuuint32_t box[4] = {64, TW, (cuuint32_t)(TH / g.cs), 1}, es[4] = {1, 1, 1, 1};
-    if (enc(&hm[1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->U, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    cuuint32_t box[4] = {64, TW, (cuuint32_t)(mi == 2 ? TH / g.cs : TH), 1};
+    if (enc(&hm[mi], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->U, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
       return cudaErrorInvalidValue;
@@ -801,7 +905,9 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   cudaError_t e = cudaMemcpy(tm, hm, sizeof hm, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   d->tmapX = &tm[0];
-  d->tmapU = &tm[1];
+  d->tmapX2 = &tm[1];
+  d->tmapU = &tm[2];
+  d->tmapUf = &tm[3];
   // gather lists: for each h, the (tile row th, halo row bh) with th*TH - (k1-1) + bh = h (mod H)
   std::vector<int> hl((size_t)(d->H + d->W) * (1 + LMAX), 0);
   int* hcnt = hl.data();
@@ -867,14 +973,18 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
   for (int i = 0; i < 64; ++i) { a.tab.boff[i] = v.boff[i]; a.tab.kstr[i] = v.kstr[i]; }
   a.mode = mode;
   const size_t smem = fwd_smem(v.g);
+  const int per = tc_fwd_slots(sh, v);
+  fwd_tc_kernel<<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+int tc_fwd_slots(const Shared& sh, const TcVData& v) {
   int sms;
   {
     std::lock_guard<std::mutex> lk(g_dev_mu);
     sms = dev_facts().sms;
   }
-  const int per = std::max(1, std::min(sms / v.g.nct, sh.total_tiles));
-  fwd_tc_kernel<<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
-  return cudaGetLastError();
+  return std::max(1, std::min(sms / v.g.nct, sh.total_tiles));
 }
 
 cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st) {

@@ -8,7 +8,7 @@ namespace icnnm {
 // Geometry of the tensor-core passes, fixed by the kernel dims.
 struct TcGeom {
   int k1, k2, k3, k, kc;
-  // forward pass E^T = V^T P(X)^T (M = 128 channels, N = 128 voxels, K = taps)
+  // forward pass E = P(X) V (M = 128 voxels, N = 128 channels, K = taps)
   int R, R8;        // taps per w-run (k1*k3) and the run rounded up to 8 rows
   int ngrp, nmma;   // K-groups of 8 taps, MMAs of K = 16
   int kpad;         // nmma * 16
@@ -16,15 +16,16 @@ struct TcGeom {
   int ncopy, nwc;   // w-shifted copies of the operand (min(k2, 8)) and 8-wide w-chunks
   int Hh;           // halo height TH + k1 - 1
   int region_bytes; // one copy's halo: Hh * k3 rows of 16 bytes
-  int stage_bytes;  // one halo stage (all copies and w-chunks + 8 zero rows), 1024-aligned
+  int stage_bytes;  // one halo stage (the k2 copies used + 8 zero rows), 1024-aligned
   int nct;          // channel tiles of 128
-  // adjoint pass G^T = (V D) U^T (M = 128 taps, N = 128 voxels, K = channels)
+  // adjoint pass G = U (D V^T) (M = 128 voxels, N = 128 taps, K = channels)
   int ntt;          // tap tiles of 128
   int kcp;          // channels rounded up to 64
   int nch_a;        // 64-wide SW128 chunks of the adjoint A image
   int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*k3
   int cs;           // adjoint cluster size: CTAs of one voxel-tile range that share U
                     // tiles by TMA multicast (ntt if ntt is 2 or 4, else 1)
+  int nus;          // forward U tile stages in shared memory (1 or 2)
   int pitch, HBp;   // shared-memory row pitch of the halo buffers (an odd multiple of 8,
                     // >= Wb, so 4 rows x 8 voxels hit 32 banks) and k3*Hb*pitch
 };
@@ -46,6 +47,9 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
 int tc_nrp(int k);
 cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st);
 cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st);
+// CTA slots per channel tile of the forward launch: the update modes write one
+// column-partial row group per (slot, job), min(slots, ntiles) groups per job.
+int tc_fwd_slots(const Shared& sh, const TcVData& v);
 // B = V D image per job (bf16, SW128), then the adjoint GEMM + col2im into halo partials.
 cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st);
 cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st);
