@@ -75,7 +75,10 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.region_bytes = g.Hh * k3 * 16;
   g.stage_bytes = rup(k2 * g.region_bytes + 8 * 16, 1024);   // k2 copies + 8 zero rows
   g.nct = (g.k + 127) / 128;
-  g.ntt = (g.k + 127) / 128;
+  // adjoint tap columns: whole tap rows per 32-column group for the kernel widths with a
+  // compile-time col2im (3, 5, 7, 9), taps in order otherwise
+  g.rpg = (k2 == 3 || k2 == 5 || k2 == 7 || k2 == 9) ? 32 / k2 : 0;
+  g.ntt = g.rpg ? ((k1 * k3 + g.rpg - 1) / g.rpg + 3) / 4 : (g.k + 127) / 128;
   g.kcp = rup(g.kc, 64);
   g.nch_a = g.kcp / 64;
   g.Hb = TH + k1 - 1;
@@ -84,7 +87,6 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.pitch = rup(g.Wb, 8);
   if ((g.pitch / 8) % 2 == 0) g.pitch += 8;
   g.HBp = k3 * g.Hb * g.pitch;
-  g.cs = (g.ntt == 2 || g.ntt == 4) ? g.ntt : 1;
   g.nus = FWD_USTAGES;
   while (g.nus > 1 && fwd_smem_n(g, g.nus) > SMEM_LIMIT) --g.nus;
   return g;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
           if (!ptx::mbar_wait_abortable(&uempty[us], uph ^ 1, abort)) { failed = true; ++it; break; }
           ptx::mbar_arrive_expect_tx(&ufull[us], (uint32_t)nbox * CHUNK);
           for (int bx = 0; bx < nbox; ++bx)
-            ptx::tma_load_4d(sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, J.tmapUf, ct * 128 + bx * 64, tw * TW,
+            ptx::tma_load_4d(sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, J.tmapU, ct * 128 + bx * 64, tw * TW,
                              th * TH, t, &ufull[us]);
         }
       }
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       if (ew == 0 && lane == 0) {
         if (wrU) {
           for (int bx = 0; bx < nbox; ++bx)
-            ptx::tma_store_4d(J.tmapUf, sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, ct * 128 + bx * 64, tw * TW,
+            ptx::tma_store_4d(J.tmapU, sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, ct * 128 + bx * 64, tw * TW,
                               th * TH, t);
           ptx::bulk_commit_group();
           ptx::bulk_wait_group_read0();   // the stage may be refilled once the store has read it
@@ -445,6 +447,70 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 // ---------------------------------------------------------------------------------
 // Adjoint pass
 // ---------------------------------------------------------------------------------
+// Tap columns of the adjoint: column j of tap tile tt belongs to 32-column group
+// G = 4 tt + j / 32, which holds rpg = floor(32 / k2) whole tap rows (st, sh) of k2 taps
+// each (row TR = G rpg + r, r = (j % 32) / k2, sw = (j % 32) % k2, TR = st k1 + sh);
+// the remaining 32 - rpg k2 columns of a group and the rows past k1 k3 are padding.
+// Returns the tap s = TR k2 + sw of a column, or -1 for padding.
+// Kernel widths without a compile-time col2im (rpg = 0) keep the taps in order: column
+// j of tap tile tt is tap 128 tt + j.
+__host__ __device__ __forceinline__ int adj_tap_of_col(const TcGeom& g, int tt, int j) {
+  if (g.rpg == 0) {
+    const int s = tt * 128 + j;
+    return s < g.k ? s : -1;
+  }
+  const int G = tt * 4 + j / 32, r = (j % 32) / g.k2, sw = (j % 32) % g.k2;
+  const int TR = G * g.rpg + r;
+  if (r >= g.rpg || TR >= g.k1 * g.k3) return -1;
+  return TR * g.k2 + sw;
+}
+
+// Halo-buffer offset of tap row TR = (st, sh) for a voxel in tile row 0: the contribution
+// of voxel (h, w) and tap (st, sh, sw) lands at h*pitch + rowoff(TR) + (w + k2 - 1 - sw).
+__device__ __forceinline__ int adj_rowoff(const TcGeom& g, int TR) {
+  const int st = TR / g.k1, shh = TR % g.k1;
+  return ((g.k3 - 1 - st) * g.Hb + (g.k1 - 1 - shh)) * g.pitch;
+}
+
+// col2im of one warp's 32 accumulator columns (K2 = k2 known at compile time): for each
+// of its whole tap rows, the 8 lanes of a tile row (w = lane % 8) first sum the values
+// that land on the same halo column o = w + k2 - 1 - sw with warp shuffles (lane w keeps
+// the outputs o = w + 8j), then add those sums into the halo buffer: 1 + (k2 - 1) / 8
+// shared-memory reductions per lane and tap row instead of k2. The sum over the 8 lanes
+// runs in a fixed order; the reductions of different warps into one address do not.
+template <int K2>
+__device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, float* hb, int hoff,
+                                                const TcGeom& g, int G) {
+  constexpr int RPG = 32 / K2;
+  constexpr int NJ = (K2 + 14) / 8;      // halo columns 0 .. K2 + 6 over 8 lanes
+  const int w = lane & 7;
+#pragma unroll
+  for (int r = 0; r < RPG; ++r) {
+    const int TR = G * RPG + r;
+    if (TR >= g.k1 * g.k3) break;          // warp-uniform: padding rows
+    const int base = hoff + adj_rowoff(g, TR);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      float T = 0.f;
+#pragma unroll
+      for (int d = -7; d <= 7; ++d) {
+        const int idx = d + K2 - 1 - 8 * j;  // tap sw whose value lane w + d sends to o = w + 8j
+        if (idx < 0 || idx >= K2) continue;
+        const float x = (d == 0) ? e[r * K2 + idx] : __shfl_sync(0xffffffffu, e[r * K2 + idx], (lane + d) & 31);
+        if (w + d >= 0 && w + d <= 7) T += x;
+      }
+      const int o = w + 8 * j;
+      if (o <= K2 + 6) atomicAdd(&hb[base + o], T);
+    }
+  }
+}
+
+// Adjoint pass G = U (D V^T) with col2im: per voxel tile and tap tile, the MMA leaves
+// G[voxel][tap column] in TMEM; the epilogue adds it into a shared-memory halo buffer
+// (Hb x pitch per frame of the k3-frame halo) and flushes the buffer to the tile's halo
+// partial, which the gather pass sums. K2 = 0 selects the per-element reduction path
+// for kernel widths without a compile-time specialisation.
+template <int K2>
 __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_constant__ AdjArgs a) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1k(smraw);
@@ -453,32 +519,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   uint8_t* sA = sm;
   uint8_t* sU = sm + (size_t)g.nch_a * CHUNK;
   float* buf = reinterpret_cast<float*>(sU + (size_t)ADJ_STAGES * CHUNK);   // [2][HBp]
-  int* toff = reinterpret_cast<int*>(buf + 2 * (size_t)g.HBp);
+  int* toff = reinterpret_cast<int*>(buf + 2 * (size_t)g.HBp);              // [128] (K2 = 0)
   uint64_t* bars = reinterpret_cast<uint64_t*>(toff + 128);
-  uint64_t* full = bars;                   // [4]
-  uint64_t* empty = bars + 4;              // [4]
-  uint64_t* tfull = bars + 8;              // [2]
-  uint64_t* tempty = bars + 10;            // [2]
-  uint64_t* abar = bars + 12;
-  uint64_t* dbar = bars + 13;
-  uint64_t* redbar = bars + 14;           // [2] all epilogue warps have added a tile
-  uint64_t* zbar = bars + 16;             // [2] a halo buffer has been flushed and cleared
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 18);
+  uint64_t* full = bars;                           // [ADJ_STAGES]
+  uint64_t* empty = bars + ADJ_STAGES;             // [ADJ_STAGES]
+  uint64_t* tfull = bars + 2 * ADJ_STAGES;         // [2]
+  uint64_t* tempty = tfull + 2;                    // [2]
+  uint64_t* abar = tfull + 4;
+  uint64_t* dbar = tfull + 5;
+  uint64_t* redbar = tfull + 6;                    // [2] all epilogue warps have added a tile
+  uint64_t* zbar = tfull + 8;                      // [2] a halo buffer has been flushed and cleared
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfull + 10);
+  static_assert((2 * ADJ_STAGES + 10) * 8 + 4 <= 256, "adjoint barriers exceed their space");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tt = blockIdx.x % g.ntt;
   const int slot = blockIdx.x / g.ntt, nslot = gridDim.x / g.ntt;
-  // cluster of g.cs CTAs (consecutive tap tiles, same voxel tiles): each loads 1/cs of
-  // every U chunk (16/cs rows of the tile) and multicasts it to all members
-  const int cs = g.cs;
-  const int crank = tt % cs;
-  const uint16_t cmask = (uint16_t)((1u << cs) - 1u);
   const int lo = (int)((long long)sh.total_tiles * slot / nslot);
   const int hi = (int)((long long)sh.total_tiles * (slot + 1) / nslot);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < ADJ_STAGES; ++i) {
       ptx::mbar_init(&full[i], 1);
-      ptx::mbar_init(&empty[i], cs);       // released by the MMAs of every member
+      ptx::mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&tfull[i], 1);
@@ -495,12 +557,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     ptx::tmem_relinquish();
   }
   for (int i = threadIdx.x; i < 2 * g.HBp; i += blockDim.x) buf[i] = 0.f;
-  // halo offset of each tap of this tap tile (-1 for padding taps): the contribution
-  // G[v][s] lands at buf[vbase(v) + toff[s]], vbase(v) = h_v * pitch + w_v
-  if (threadIdx.x < 128) {
-    const int s = tt * 128 + threadIdx.x;
+  // K2 = 0: halo offset of each tap column (-1 for padding); G[v][j] lands at
+  // buf[h_v * pitch + w_v + toff[j]]
+  if (K2 == 0 && threadIdx.x < 128) {
+    const int s = adj_tap_of_col(g, tt, threadIdx.x);
     int o = -1;
-    if (s < sh.k) {
+    if (s >= 0) {
       const int sw = s % g.k2, shh = (s / g.k2) % g.k1, st = s / (g.k1 * g.k2);
       o = ((g.k3 - 1 - st) * g.Hb + (g.k1 - 1 - shh)) * g.pitch + (g.k2 - 1 - sw);
     }
@@ -508,7 +570,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if (cs > 1) ptx::cluster_sync();          // every member's barriers exist before use
   ptx::tc_fence_after();
   const uint32_t tbase = *tslot;
   bool failed = false;
@@ -526,13 +587,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
           const uint32_t ph = (cnt / ADJ_STAGES) & 1;
           if (!ptx::mbar_wait(&empty[s], ph ^ 1)) { failed = true; break; }
           ptx::mbar_arrive_expect_tx(&full[s], CHUNK);
-          if (cs == 1) {
-            ptx::tma_load_4d(sU + (size_t)s * CHUNK, J.tmapU, c * 64, tw * TW, th * TH, t, &full[s]);
-          } else {
-            const int rows = TH / cs;
-            ptx::tma_load_4d_mc(sU + (size_t)s * CHUNK + (size_t)crank * rows * TW * 128, J.tmapU, c * 64, tw * TW,
-                                th * TH + crank * rows, t, &full[s], cmask);
-          }
+          ptx::tma_load_4d(sU + (size_t)s * CHUNK, J.tmapU, c * 64, tw * TW, th * TH, t, &full[s]);
         }
       }
       for (int i = (cnt > ADJ_STAGES ? cnt - ADJ_STAGES : 0); i < cnt; ++i)
@@ -540,8 +595,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // A = U tile (voxels x channels), B = V D image (taps x channels), both K-major
-      // SW128: D[voxel][tap] in TMEM.
+      // A = U tile (voxels x channels), B = V D image (tap columns x channels), both
+      // K-major SW128: G[voxel][tap column] in TMEM.
       const uint32_t idesc = ptx::idesc_bf16(128, 128, 0, 0);
       const uint32_t aB = ptx::smem_u32(sA), uB = ptx::smem_u32(sU);
       int cur = -1, cnt = 0, i = 0;
@@ -578,8 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
             const uint64_t bd = ptx::sdesc(aB + (uint32_t)c * CHUNK + kk * 32, 16, 1024, 2);
             ptx::mma_bf16(d, ad, bd, idesc, (c | kk) ? 1u : 0u);
           }
-          if (cs == 1) ptx::mma_commit(&empty[s]);
-          else ptx::mma_commit_mc(&empty[s], cmask);
+          ptx::mma_commit(&empty[s]);
         }
         if (failed) break;
         ptx::mma_commit(&tfull[b]);
@@ -589,16 +643,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     }
   } else {
     // Epilogue: 16 warps. Warp w reads TMEM lanes 32q..32q+31 (q = w % 4), i.e. voxels
-    // 32q + lane (rows 4q..4q+3 of the tile), and columns 32g..32g+31 (g = (w - 2) / 4),
-    // i.e. 32 taps. Tile i is added into halo buffer i % 2 with shared-memory reductions
-    // (lanes of one tap hit 32 distinct addresses and banks; different taps or warps may
-    // hit the same address). While tile i is added, the warps flush tile i-1's buffer
-    // (write the partial, clear), so the two phases of consecutive tiles overlap.
+    // 32q + lane (rows 4q..4q+3 of the tile, w = lane % 8), and columns 32g..32g+31
+    // (g = (w - 2) / 4), i.e. one group of whole tap rows. Tile i is added into halo
+    // buffer i % 2; while tile i is added, the warps flush tile i-1's buffer (write the
+    // partial, clear), so the two phases of consecutive tiles overlap.
     const int q = warp & 3;
     const int cg = (warp - 2) >> 2;
     const int ew = warp - 2;
     const int vox = q * 32 + lane;
-    const int vbase = (vox >> 3) * g.pitch + (vox & 7);
+    const int hoff = (vox >> 3) * g.pitch;
     int i = 0;
     int prev_tile = -1;
     float* prev_out = nullptr;
@@ -618,10 +671,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&tempty[b]);
+        if constexpr (K2 > 0) {
+          adj_col2im_rows<K2>(v, lane, hb, hoff, g, tt * 4 + cg);
+        } else {
+          const int vbase = hoff + (vox & 7);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          const int o = toff[cg * 32 + e];
-          if (o >= 0) atomicAdd(&hb[vbase + o], v[e]);
+          for (int e = 0; e < 32; ++e) {
+            const int o = toff[cg * 32 + e];
+            if (o >= 0) atomicAdd(&hb[vbase + o], v[e]);
+          }
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&redbar[i & 1]);
@@ -651,7 +709,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   if (failed) set_fail(sh);
   ptx::tc_fence_before();
   __syncthreads();
-  if (cs > 1) ptx::cluster_sync();          // no member exits while others may still write it
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tbase, TMEM_COLS);
@@ -669,12 +726,12 @@ __global__ void build_B2_kernel(Shared sh, TcGeom g) {
   uint8_t* img = reinterpret_cast<uint8_t*>(J.B2img) + ((size_t)tt * g.nch_a + c) * CHUNK;
   for (int u = threadIdx.x; u < 128 * 8; u += blockDim.x) {
     const int r = u >> 3, j = u & 7;
-    const int s = tt * 128 + r;
+    const int s = adj_tap_of_col(g, tt, r);
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int ch = c * 64 + j * 8 + e;
-      const float x = (s < sh.k && ch < sh.k) ? sh.Vf[(size_t)s * sh.kc + ch] * J.D[ch] : 0.f;
+      const float x = (s >= 0 && ch < sh.k) ? sh.Vf[(size_t)s * sh.kc + ch] * J.D[ch] : 0.f;
       v[e] = __float2bfloat16(x);
     }
     *reinterpret_cast<uint4*>(img + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) * 16)) =
@@ -856,7 +913,7 @@ size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g) {
   add((size_t)g.ncopy * Tp * Hp * Wp * 2);             // Xc
   add((size_t)ntiles * g.ntt * g.HB * 4);              // col2im partials
   add((size_t)g.ntt * g.nch_a * CHUNK);                // V D images
-  add(4 * sizeof(CUtensorMap));                        // TMA maps
+  add(3 * sizeof(CUtensorMap));                        // TMA maps
   add((size_t)(H + W) * (1 + LMAX) * 4);               // gather lists
   return b;
 }
@@ -870,12 +927,12 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   d->Xc = (__nv_bfloat16*)take((size_t)g.ncopy * Tp * Hp * Wp * 2);
   d->G = (float*)take((size_t)d->ntiles * g.ntt * g.HB * 4);
   d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * CHUNK);
-  CUtensorMap* tm = (CUtensorMap*)take(4 * sizeof(CUtensorMap));
+  CUtensorMap* tm = (CUtensorMap*)take(3 * sizeof(CUtensorMap));
   int* gl = (int*)take((size_t)(d->H + d->W) * (1 + LMAX) * 4);
   if (off > total) return cudaErrorInvalidValue;
   EncodeTiledFn enc = encoder();
   if (!enc) return cudaErrorNotSupported;
-  CUtensorMap hm[4];
+  CUtensorMap hm[3];
   const cuuint32_t es[4] = {1, 1, 1, 1};
   // Xc as [c][wc][hp][tp*8]: dim0 = (tp, w%8) flattened, dim1 = hp, dim2 = wc, dim3 = c.
   // Map 0 loads all ncopy copies of a w-chunk; map 1 only the first k2 - 8 (the last
@@ -891,13 +948,13 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
         CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  // U as [t][h][w][kc]: map 2 = adjoint box (64 channels x 8 w x 16/cs h), map 3 =
-  // forward box (64 channels x 8 w x 16 h), both SW128 (row = voxel, 128 bytes).
-  for (int mi = 2; mi < 4; ++mi) {
+  // U as [t][h][w][kc]: map 2, box = one tile of 64 channels (64 x 8 w x 16 h), SW128
+  // (row = voxel, 128 bytes); used by both tensor-core passes.
+  {
     cuuint64_t dims[4] = {(cuuint64_t)g.kc, (cuuint64_t)d->W, (cuuint64_t)d->H, (cuuint64_t)d->T};
     cuuint64_t str[3] = {(cuuint64_t)g.kc * 2, (cuuint64_t)d->W * g.kc * 2, (cuuint64_t)d->H * d->W * g.kc * 2};
-    cuuint32_t box[4] = {64, TW, (cuuint32_t)(mi == 2 ? TH / g.cs : TH), 1};
-    if (enc(&hm[mi], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->U, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    cuuint32_t box[4] = {64, TW, TH, 1};
+    if (enc(&hm[2], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->U, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
       return cudaErrorInvalidValue;
@@ -907,7 +964,6 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   d->tmapX = &tm[0];
   d->tmapX2 = &tm[1];
   d->tmapU = &tm[2];
-  d->tmapUf = &tm[3];
   // gather lists: for each h, the (tile row th, halo row bh) with th*TH - (k1-1) + bh = h (mod H)
   std::vector<int> hl((size_t)(d->H + d->W) * (1 + LMAX), 0);
   int* hcnt = hl.data();
@@ -936,20 +992,32 @@ cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, 
   return cudaGetLastError();
 }
 
-// Per-device launch facts, set up once outside any stream capture: the SM count, the
-// shared-memory opt-in of both tcgen05 kernels and the resident-cluster count of the
-// adjoint for each (shared memory, cluster size).
+// Per-device launch facts, set up once outside any stream capture: the SM count and the
+// shared-memory opt-in of the tcgen05 kernels.
 namespace {
 constexpr int MAX_DEV = 64;
 struct DevFacts {
   bool ready = false;
   int sms = 1;
-  std::vector<std::pair<long long, int>> clusters;   // key smem*16+cs -> max active clusters
 };
 DevFacts g_dev[MAX_DEV];
 std::mutex g_dev_mu;
 
-DevFacts& dev_facts() {
+typedef void (*AdjKernel)(AdjArgs);
+// compile-time kernel widths of the adjoint col2im (others take the per-element path)
+AdjKernel adj_kernel_for(const TcGeom& g) {
+  if (g.rpg == 0) return adj_tc_kernel<0>;
+  switch (g.k2) {
+    case 3: return adj_tc_kernel<3>;
+    case 5: return adj_tc_kernel<5>;
+    case 7: return adj_tc_kernel<7>;
+    case 9: return adj_tc_kernel<9>;
+    default: return adj_tc_kernel<0>;
+  }
+}
+
+int dev_sms() {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= MAX_DEV) dev = 0;
@@ -959,10 +1027,11 @@ DevFacts& dev_facts() {
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     f.sms = n > 0 ? n : 1;
     cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    for (AdjKernel kf : {adj_tc_kernel<0>, adj_tc_kernel<3>, adj_tc_kernel<5>, adj_tc_kernel<7>, adj_tc_kernel<9>})
+      cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     f.ready = true;
   }
-  return f;
+  return f.sms;
 }
 }  // namespace
 
@@ -979,12 +1048,7 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
 }
 
 int tc_fwd_slots(const Shared& sh, const TcVData& v) {
-  int sms;
-  {
-    std::lock_guard<std::mutex> lk(g_dev_mu);
-    sms = dev_facts().sms;
-  }
-  return std::max(1, std::min(sms / v.g.nct, sh.total_tiles));
+  return std::max(1, std::min(dev_sms() / v.g.nct, sh.total_tiles));
 }
 
 cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st) {
@@ -996,43 +1060,9 @@ cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st) {
   AdjArgs a;
   a.sh = sh;
   a.g = v.g;
-  const size_t smem = adj_smem(v.g);
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(TC_THREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.numAttrs = 0;
-  int per;
-  {
-    std::lock_guard<std::mutex> lk(g_dev_mu);
-    DevFacts& f = dev_facts();
-    per = std::max(1, std::min(f.sms / v.g.ntt, sh.total_tiles));
-    if (v.g.cs > 1) {
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = v.g.cs;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      // only as many clusters as can be resident at once (the tile ranges are static)
-      const long long key = (long long)smem * 16 + v.g.cs;
-      int maxc = 0;
-      for (auto& kv : f.clusters)
-        if (kv.first == key) maxc = kv.second;
-      if (!maxc) {
-        cfg.gridDim = dim3(per * v.g.ntt);
-        if (cudaOccupancyMaxActiveClusters(&maxc, adj_tc_kernel, &cfg) != cudaSuccess || maxc < 1) {
-          cudaGetLastError();
-          maxc = 1;
-        }
-        f.clusters.emplace_back(key, maxc);
-      }
-      per = std::max(1, std::min(per, maxc * v.g.cs / v.g.ntt));
-    }
-  }
-  cfg.gridDim = dim3(per * v.g.ntt);
-  return cudaLaunchKernelEx(&cfg, adj_tc_kernel, a);
+  const int per = std::max(1, std::min(dev_sms() / v.g.ntt, sh.total_tiles));
+  adj_kernel_for(v.g)<<<per * v.g.ntt, TC_THREADS, adj_smem(v.g), st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st) {

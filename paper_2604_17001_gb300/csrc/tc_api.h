@@ -19,12 +19,11 @@ struct TcGeom {
   int stage_bytes;  // one halo stage (the k2 copies used + 8 zero rows), 1024-aligned
   int nct;          // channel tiles of 128
   // adjoint pass G = U (D V^T) (M = 128 voxels, N = 128 taps, K = channels)
-  int ntt;          // tap tiles of 128
+  int ntt;          // tap tiles of 128 columns (4 groups of rpg tap rows)
   int kcp;          // channels rounded up to 64
   int nch_a;        // 64-wide SW128 chunks of the adjoint A image
   int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*k3
-  int cs;           // adjoint cluster size: CTAs of one voxel-tile range that share U
-                    // tiles by TMA multicast (ntt if ntt is 2 or 4, else 1)
+  int rpg;          // adjoint: whole tap rows (k2 taps) per 32-column group (0: taps in order)
   int nus;          // forward U tile stages in shared memory (1 or 2)
   int pitch, HBp;   // shared-memory row pitch of the halo buffers (an odd multiple of 8,
                     // >= Wb, so 4 rows x 8 voxels hit 32 banks) and k3*Hb*pitch
