@@ -93,7 +93,8 @@ TcGeom make_geom(int k1, int k2, int k3) {
 }
 
 size_t fwd_smem_n(const TcGeom& g, int nus) {
-  return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + (size_t)nus * USTAGE + EPI_WARPS * 32 * 4 + 256;
+  return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + (size_t)nus * USTAGE + EPI_WARPS * 32 * 4 +
+         64 * 16 + 256;
 }
 size_t fwd_smem(const TcGeom& g) { return fwd_smem_n(g, g.nus); }
 size_t adj_smem(const TcGeom& g) {
@@ -180,7 +181,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   uint8_t* sH = sA + (size_t)g.nch_f * CHUNK;                    // [2] halo stages
   uint8_t* sU = sH + 2 * (size_t)g.stage_bytes;                  // [g.nus] U tiles
   float* sD = reinterpret_cast<float*>(sU + (size_t)g.nus * USTAGE);   // [EPI_WARPS][32]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sD + EPI_WARPS * 32);
+  ulonglong2* sDesc = reinterpret_cast<ulonglong2*>(sD + EPI_WARPS * 32);  // [64] MMA descriptors
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sDesc + 64);
   uint64_t* full = bars;                   // [2] halo landed
   uint64_t* empty = bars + 2;              // [2] halo consumed by the MMAs
   uint64_t* tfull = bars + 4;              // [2] accumulator ready
@@ -269,13 +271,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       if (failed) *abort = 1;
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      if (!ptx::mbar_wait_abortable(abar, 0, abort)) failed = true;
-      // A = halo (voxels x taps, MN-major, overlapping core matrices), B = V^T image
-      // (channels x taps, K-major SW128): D[voxel][channel] in TMEM.
-      const uint32_t idesc = ptx::idesc_bf16(128, 128, 1, 0);
+    // A = halo (voxels x taps, MN-major, overlapping core matrices), B = V^T image
+    // (channels x taps, K-major SW128): D[voxel][channel] in TMEM. The descriptors of the
+    // nmma MMAs of a tile (halo stage 0) are built once here, so that the issuing thread
+    // only loads, offsets and issues: its dependent scalar chain sets the MMA rate.
+    {
       const uint32_t aB = ptx::smem_u32(sA), hB = ptx::smem_u32(sH);
       const uint32_t nstride = (uint32_t)g.k3 * 16;
+      for (int i = lane; i < g.nmma; i += 32) {
+        ulonglong2 dd;
+        dd.x = ptx::sdesc(hB + a.tab.boff[i], a.tab.kstr[i], nstride, 0);
+        dd.y = ptx::sdesc(aB + (uint32_t)(i >> 2) * CHUNK + (uint32_t)(i & 3) * 32, 16, 1024, 2);
+        sDesc[i] = dd;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      if (!ptx::mbar_wait_abortable(abar, 0, abort)) failed = true;
+      const uint32_t idesc = ptx::idesc_bf16(128, 128, 1, 0);
       int it = 0;
       for (int tg = slot; !failed && tg < sh.total_tiles; tg += nslot, ++it) {
         const int s = it & 1, b = it & 1;
@@ -284,11 +297,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         if (!ptx::mbar_wait_abortable(&tempty[b], ph ^ 1, abort)) { failed = true; break; }
         ptx::tc_fence_after();
         const uint32_t d = tbase + (uint32_t)b * 128;
-        const uint32_t hs = hB + (uint32_t)s * g.stage_bytes;
+        const uint64_t sadd = (uint64_t)(((uint32_t)s * (uint32_t)g.stage_bytes) >> 4);   // start-address field
+#pragma unroll 4
         for (int i = 0; i < g.nmma; ++i) {
-          const uint64_t ad = ptx::sdesc(hs + a.tab.boff[i], a.tab.kstr[i], nstride, 0);
-          const uint64_t bd = ptx::sdesc(aB + (uint32_t)(i >> 2) * CHUNK + (uint32_t)(i & 3) * 32, 16, 1024, 2);
-          ptx::mma_bf16(d, ad, bd, idesc, i > 0 ? 1u : 0u);
+          const ulonglong2 dd = sDesc[i];
+          ptx::mma_bf16(d, dd.x + sadd, dd.y, idesc, i > 0 ? 1u : 0u);
         }
         ptx::mma_commit(&empty[s]);
         ptx::mma_commit(&tfull[b]);
@@ -598,7 +611,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
       // A = U tile (voxels x channels), B = V D image (tap columns x channels), both
       // K-major SW128: G[voxel][tap column] in TMEM.
       const uint32_t idesc = ptx::idesc_bf16(128, 128, 0, 0);
-      const uint32_t aB = ptx::smem_u32(sA), uB = ptx::smem_u32(sU);
+      // descriptors of U stage 0 and image chunk 0; others differ only in the start address
+      const uint64_t ubase = ptx::sdesc(ptx::smem_u32(sU), 16, 1024, 2);
+      const uint64_t bbase = ptx::sdesc(ptx::smem_u32(sA), 16, 1024, 2);
       int cur = -1, cnt = 0, i = 0;
       uint32_t aph = 0, dph = 0;
       for (int tg = lo; tg < hi && !failed; ++tg, ++i) {
@@ -627,12 +642,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
           const uint32_t ph = (cnt / ADJ_STAGES) & 1;
           if (!ptx::mbar_wait(&full[s], ph)) { failed = true; break; }
           ptx::tc_fence_after();
+          const uint64_t ad0 = ubase + (uint64_t)(s * (CHUNK >> 4));
+          const uint64_t bd0 = bbase + (uint64_t)(c * (CHUNK >> 4));
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = ptx::sdesc(uB + (uint32_t)s * CHUNK + kk * 32, 16, 1024, 2);
-            const uint64_t bd = ptx::sdesc(aB + (uint32_t)c * CHUNK + kk * 32, 16, 1024, 2);
-            ptx::mma_bf16(d, ad, bd, idesc, (c | kk) ? 1u : 0u);
-          }
+          for (int kk = 0; kk < 4; ++kk) ptx::mma_bf16(d, ad0 + 2 * kk, bd0 + 2 * kk, idesc, (c | kk) ? 1u : 0u);
           ptx::mma_commit(&empty[s]);
         }
         if (failed) break;
