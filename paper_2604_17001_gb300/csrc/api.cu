@@ -347,6 +347,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   CK(cudaMemsetAsync(d.U, 0, (size_t)m * kc * (j.p.prec == ICNNM_FP32 ? 4 : 2), c->stream));
   CK(cudaMemsetAsync(d.part, 0, (size_t)d.ntiles * PROW * kc * 4, c->stream));
   CK(cudaMemsetAsync(d.rpart, 0, (size_t)d.ntiles * nrp * 4, c->stream));
+  if (j.p.prec == ICNNM_BF16) CK(cudaMemsetAsync(d.G, 0, (size_t)m * 4, c->stream));
   // inputs
   const float* srcM = j.srcM ? j.srcM : j.hM.data();
   const uint8_t* srcK = j.srcmask ? j.srcmask : j.hmask.data();

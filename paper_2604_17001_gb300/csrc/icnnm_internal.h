@@ -61,12 +61,12 @@ struct JobDev {
   double* colseg;       // first-stage column sums: [NSEG][kc]
   float* s;             // kc, shrink factors of this iteration
   float* D;             // kc, 1 - s
-  float* G;             // FP32 path: G^T = (V D) U^T, [k][m]; BF16 path: col2im partials
+  float* G;             // FP32 path: G^T = (V D) U^T, [k][m]; BF16 path: col2im sums Delta [m],
+                        //   zero between passes (the gather clears what it reads)
   __nv_bfloat16* B2img; // BF16 path: A-operand images of the adjoint pass (V D)
   const void* tmapX;    // BF16 path: TMA map (CUtensorMap, device memory) of Xc, 8 copies
   const void* tmapX2;   // BF16 path: the same with k2 - 8 copies (kernels wider than 8)
   const void* tmapU;    // BF16 path: TMA map of U (box: one tile x 64 channels)
-  const int* glist;     // BF16 path: col2im gather lists (see k_tc.cu)
   int xTp, xHp, xWp;    // BF16 path: dims of each copy in Xc
 };
 

@@ -96,10 +96,23 @@ __device__ __forceinline__ double colsq_of(const JobDev& J, int kc, int c) {
 // shifted form): s_c = max(0, 1 - 1/||U_c||) (the column-wise l2,1 shrinkage with
 // threshold 1/theta applied to -U/theta), D_c = 1 - s_c; theta' = min(rho theta, theta_max).
 __global__ void scalars_kernel(Shared sh) {
+  // block = (job, 32 channels); warp w sums segments w, w + 8, ... (fixed order), then
+  // the 8 warp sums are added in warp order
   const JobDev& J = sh.jobs[blockIdx.x];
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y * 32 + lane;
+  double q = 0.0;
   if (c < sh.kc) {
-    const double n = sqrt(colsq_of(J, sh.kc, c));
+#pragma unroll
+    for (int i = 0; i < NSEG / 8; ++i) q += J.colseg[(long long)(warp + 8 * i) * sh.kc + c];
+  }
+  __shared__ double red[8][32];
+  red[warp][lane] = q;
+  __syncthreads();
+  if (warp == 0 && c < sh.kc) {
+    double n2 = 0.0;
+    for (int w = 0; w < 8; ++w) n2 += red[w][lane];
+    const double n = sqrt(n2);
     const double sc = (c < sh.k && n > 1.0) ? 1.0 - 1.0 / n : 0.0;
     J.s[c] = (float)sc;
     J.D[c] = (c < sh.k) ? (float)(1.0 - sc) : 0.f;
@@ -215,7 +228,7 @@ cudaError_t launch_reduce_cols(const Shared& sh, int advance, int slots, cudaStr
 }
 
 cudaError_t launch_scalars(const Shared& sh, cudaStream_t st) {
-  scalars_kernel<<<dim3(sh.njobs, (sh.kc + 127) / 128), 128, 0, st>>>(sh);
+  scalars_kernel<<<dim3(sh.njobs, (sh.kc + 31) / 32), 256, 0, st>>>(sh);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,6 @@ namespace {
 
 constexpr int EPI_WARPS = 16;        // 4 per TMEM lane quarter, each owning 32 columns
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
-constexpr int LMAX = 16;             // (tile, offset) pairs per coordinate in the gather
 constexpr int ADJ_STAGES = 4;
 constexpr int FWD_USTAGES = 2;      // U tile stages of the forward pass (fewer if short of space)
 constexpr int USTAGE = 2 * 16384;    // one U tile: 128 voxels x 128 channels bf16 (two boxes)
@@ -83,7 +82,29 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.nch_a = g.kcp / 64;
   g.Hb = TH + k1 - 1;
   g.Wb = TW + k2 - 1;
-  g.HB = g.Hb * g.Wb * k3;
+  // frames (st) each tap tile's taps reach: its col2im partial keeps only those nsl
+  // frames of the halo, starting at frame slo[tt]
+  g.nsl = 1;
+  for (int tt = 0; tt < g.ntt && tt < 16; ++tt) {
+    int lo = 1 << 30, hi = -1;
+    for (int j = 0; j < 128; ++j) {
+      int sp = -1;
+      if (g.rpg == 0) {
+        sp = tt * 128 + j < g.k ? tt * 128 + j : -1;
+      } else {
+        const int G = tt * 4 + j / 32, r = (j % 32) / k2, sw = (j % 32) % k2, TR = G * g.rpg + r;
+        sp = (r < g.rpg && TR < k1 * k3) ? TR * k2 + sw : -1;
+      }
+      if (sp < 0) continue;
+      const int st = sp / (k1 * k2);
+      lo = std::min(lo, st);
+      hi = std::max(hi, st);
+    }
+    if (hi < 0) lo = hi = 0;
+    g.slo[tt] = lo;
+    g.nsl = std::max(g.nsl, hi - lo + 1);
+  }
+  g.HB = g.Hb * g.Wb * g.nsl;
   g.pitch = rup(g.Wb, 8);
   if ((g.pitch / 8) % 2 == 0) g.pitch += 8;
   g.HBp = k3 * g.Hb * g.pitch;
@@ -666,8 +687,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     const int vox = q * 32 + lane;
     const int hoff = (vox >> 3) * g.pitch;
     int i = 0;
-    int prev_tile = -1;
-    float* prev_out = nullptr;
+    int prev_jb = 0, prev_t = 0, prev_h0 = 0, prev_w0 = 0;   // tile flushed next: job, frame, halo origin
     for (int tg = lo; tg <= hi; ++tg, ++i) {
       const bool have = tg < hi;
       float* hb = buf + (size_t)(i & 1) * g.HBp;
@@ -702,11 +722,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         const int pb = (i - 1) & 1;
         if (!ptx::mbar_wait(&redbar[pb], ((i - 1) >> 1) & 1)) { failed = true; break; }
         float* src = buf + (size_t)pb * g.HBp;
+        // halo entry (frame st, row bh, column bw) belongs to voxel ((t - st) mod T,
+        // (th*TH - (k1-1) + bh) mod H, (tw*TW - (k2-1) + bw) mod W); only the nsl frames
+        // this tap tile reaches (from slo) can be nonzero
         for (int p = ew * 32 + lane; p < g.HB; p += 32 * EPI_WARPS) {
-          const int row = p / g.Wb, col = p - row * g.Wb;   // row = bt * Hb + bh
-          const int si = row * g.pitch + col;
-          prev_out[p] = src[si];
+          const int row = p / g.Wb, col = p - row * g.Wb;   // row = j * Hb + bh
+          const int j = row / g.Hb, bh = row - j * g.Hb;
+          const int st = g.slo[tt] + j;
+          if (st >= g.k3) continue;
+          const int si = ((g.k3 - 1 - st) * g.Hb + bh) * g.pitch + col;
+          const float v = src[si];
           src[si] = 0.f;
+          const JobDev& P = sh.jobs[prev_jb];
+          int tq = prev_t - st, hq = prev_h0 + bh, wq = prev_w0 + col;
+          tq += tq < 0 ? P.T : 0;
+          hq = hq < 0 ? hq + P.H : (hq >= P.H ? hq - P.H : hq);
+          wq = wq < 0 ? wq + P.W : (wq >= P.W ? wq - P.W : wq);
+          atomicAdd(P.G + ((size_t)tq * P.H + hq) * P.W + wq, v);
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&zbar[pb]);
@@ -714,8 +746,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
       if (have) {
         const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
         const JobDev& J = sh.jobs[jb];
-        prev_tile = tg - sh.job_tile0[jb];
-        prev_out = J.G + ((size_t)prev_tile * g.ntt + tt) * g.HB;
+        const int tile = tg - sh.job_tile0[jb];
+        prev_jb = jb;
+        prev_t = tile / (J.ntw * J.nth);
+        prev_h0 = ((tile / J.ntw) % J.nth) * TH - (g.k1 - 1);
+        prev_w0 = (tile % J.ntw) * TW - (g.k2 - 1);
       }
     }
   }
@@ -755,39 +790,46 @@ __global__ void build_B2_kernel(Shared sh, TcGeom g) {
 // Copy c of the forward operand, element (tp, hp, wp), is
 //   bf16(src[(tp - (k3-1)) mod T][(hp - (k1-1)) mod H][(wp - 8(nwc-1) - c) mod W]),
 // stored as Xc[c][wp / 8][hp][tp][wp % 8]: the k3 frames of a 16-byte w-segment are
-// adjacent, so one TMA box row of the tile halo is k3 * 16 bytes.
+// adjacent, so one TMA box row of the tile halo is k3 * 16 bytes. A thread reads the
+// NC + 7 source values of one (w-segment, hp, tp) once and writes all NC copies.
+template <int NC>
 __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
   const JobDev& J = sh.jobs[blockIdx.y];
   const float* src = from_L ? J.L : J.X;
   const int nwcol = J.xWp / 8;
-  const long long nunits = (long long)g.ncopy * nwcol * J.xHp * J.xTp;
+  const long long nunits = (long long)nwcol * J.xHp * J.xTp;
   const int pw = 8 * (g.nwc - 1);
+  const size_t plane = (size_t)nwcol * J.xHp * J.xTp * 8;   // one copy
   for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < nunits;
        u += (long long)gridDim.x * blockDim.x) {
     const int tp = (int)(u % J.xTp);
     long long r = u / J.xTp;
     const int hp = (int)(r % J.xHp);
-    r /= J.xHp;
-    const int wu = (int)(r % nwcol);
-    const int c = (int)(r / nwcol);
+    const int wu = (int)(r / J.xHp);
     const long long rowb = ((long long)wrapi(tp - (g.k3 - 1), J.T) * J.H + wrapi(hp - (g.k1 - 1), J.H)) * J.W;
-    const int w0 = wu * 8 - pw - c;
-    __align__(16) __nv_bfloat16 v[8];
-    if (w0 >= 0 && w0 + 7 < J.W) {
+    const int w0 = wu * 8 - pw - (NC - 1);                     // first source column of the window
+    float win[NC + 7];
+    if (w0 >= 0 && w0 + NC + 6 < J.W) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(src[rowb + w0 + e]);
+      for (int i = 0; i < NC + 7; ++i) win[i] = src[rowb + w0 + i];
     } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(src[rowb + wrapi(w0 + e, J.W)]);
+      for (int i = 0; i < NC + 7; ++i) win[i] = src[rowb + wrapi(w0 + i, J.W)];
     }
-    *reinterpret_cast<uint4*>(J.Xc + ((((long long)c * nwcol + wu) * J.xHp + hp) * J.xTp + tp) * 8) =
-        *reinterpret_cast<const uint4*>(v);
+    __nv_bfloat16* dst = J.Xc + (((size_t)wu * J.xHp + hp) * J.xTp + tp) * 8;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(win[NC - 1 - c + e]);
+      *reinterpret_cast<uint4*>(dst + (size_t)c * plane) = *reinterpret_cast<const uint4*>(v);
+    }
   }
 }
 
-// L-update from the col2im partials: Delta_j = sum of the halo partials of every tile
-// whose halo covers voxel j (taps tiles innermost), in a fixed order; then the same
-// projection as the FP32 path.
+// L-update from the col2im sums: Delta_j (added into J.G by the adjoint pass, over all
+// tap tiles and tiles whose halo covers voxel j) is read and cleared for the next pass,
+// then the same projection as the FP32 path.
 __global__ void gather_tc_kernel(Shared sh, TcGeom g) {
   const int tile_g = blockIdx.x;
   const int jb = job_of_tile(sh.job_tile0, sh.njobs, tile_g);
@@ -798,28 +840,9 @@ __global__ void gather_tc_kernel(Shared sh, TcGeom g) {
   __shared__ float red[TILE_VOX];
   float l2 = 0.f;
   if (h < J.H && w < J.W) {
-    const int* hcnt = J.glist;
-    const int* hent = hcnt + J.H;
-    const int* wcnt = hent + (size_t)J.H * LMAX;
-    const int* went = wcnt + J.W;
-    const int nh = hcnt[h], nw = wcnt[w];
-    float d = 0.f;
-    for (int st = 0; st < g.k3; ++st) {
-      const int tf = wrapi(t + st, J.T);
-      const int bt = g.k3 - 1 - st;
-      for (int ih = 0; ih < nh; ++ih) {
-        const int eh = hent[h * LMAX + ih];
-        const int th = eh >> 8, bh = eh & 255;
-        for (int iw = 0; iw < nw; ++iw) {
-          const int ew = went[w * LMAX + iw];
-          const int tw = ew >> 8, bw = ew & 255;
-          const size_t tl = ((size_t)tf * J.nth + th) * J.ntw + tw;
-          const size_t off = ((size_t)bt * g.Hb + bh) * g.Wb + bw;
-          for (int k = 0; k < g.ntt; ++k) d += J.G[(tl * g.ntt + k) * g.HB + off];
-        }
-      }
-    }
     const long long v = ((long long)t * J.H + h) * J.W + w;
+    const float d = J.G[v];
+    J.G[v] = 0.f;
     const float Ln = l_update(J, sh.k, v, d);
     l2 = Ln * Ln;
   }
@@ -859,6 +882,7 @@ bool tc_supported(int k1, int k2, int k3, std::string* why) {
   auto no = [&](const char* m) { if (why) *why = m; return false; };
   if (g.k > 512) return no("k > 512");
   if (k2 > 16) return no("k2 > 16");
+  if (g.ntt > 16) return no("more than 16 adjoint tap tiles");
   if (g.nmma > 64) return no("padded forward K > 1024");
   if (g.Hh > 256 || k3 > 256) return no("halo box too tall");
   if (fwd_smem(g) > SMEM_LIMIT) return no("forward shared memory exceeds 227 KiB");
@@ -924,10 +948,9 @@ size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g) {
   size_t b = 0;
   auto add = [&](size_t n) { b += (n + 255) / 256 * 256; };
   add((size_t)g.ncopy * Tp * Hp * Wp * 2);             // Xc
-  add((size_t)ntiles * g.ntt * g.HB * 4);              // col2im partials
+  add((size_t)H * W * T * 4);                          // col2im sums (Delta)
   add((size_t)g.ntt * g.nch_a * CHUNK);                // V D images
   add(3 * sizeof(CUtensorMap));                        // TMA maps
-  add((size_t)(H + W) * (1 + LMAX) * 4);               // gather lists
   return b;
 }
 
@@ -938,10 +961,9 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   xc_dims(g, d->H, d->W, d->T, Tp, Hp, Wp);
   d->xTp = Tp; d->xHp = Hp; d->xWp = Wp;
   d->Xc = (__nv_bfloat16*)take((size_t)g.ncopy * Tp * Hp * Wp * 2);
-  d->G = (float*)take((size_t)d->ntiles * g.ntt * g.HB * 4);
+  d->G = (float*)take((size_t)d->m * 4);
   d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * CHUNK);
   CUtensorMap* tm = (CUtensorMap*)take(3 * sizeof(CUtensorMap));
-  int* gl = (int*)take((size_t)(d->H + d->W) * (1 + LMAX) * 4);
   if (off > total) return cudaErrorInvalidValue;
   EncodeTiledFn enc = encoder();
   if (!enc) return cudaErrorNotSupported;
@@ -977,31 +999,21 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   d->tmapX = &tm[0];
   d->tmapX2 = &tm[1];
   d->tmapU = &tm[2];
-  // gather lists: for each h, the (tile row th, halo row bh) with th*TH - (k1-1) + bh = h (mod H)
-  std::vector<int> hl((size_t)(d->H + d->W) * (1 + LMAX), 0);
-  int* hcnt = hl.data();
-  int* hent = hcnt + d->H;
-  int* wcnt = hent + (size_t)d->H * LMAX;
-  int* went = wcnt + d->W;
-  for (int th = 0; th < d->nth; ++th)
-    for (int bh = 0; bh < g.Hb; ++bh) {
-      const int h = ((th * TH - (g.k1 - 1) + bh) % d->H + d->H) % d->H;
-      if (hcnt[h] >= LMAX) return cudaErrorNotSupported;
-      hent[h * LMAX + hcnt[h]++] = (th << 8) | bh;
-    }
-  for (int tw = 0; tw < d->ntw; ++tw)
-    for (int bw = 0; bw < g.Wb; ++bw) {
-      const int w = ((tw * TW - (g.k2 - 1) + bw) % d->W + d->W) % d->W;
-      if (wcnt[w] >= LMAX) return cudaErrorNotSupported;
-      went[w * LMAX + wcnt[w]++] = (tw << 8) | bw;
-    }
-  e = cudaMemcpy(gl, hl.data(), hl.size() * 4, cudaMemcpyHostToDevice);
-  d->glist = gl;
-  return e;
+  return cudaSuccess;
 }
 
 cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st) {
-  prepare_X_kernel<<<dim3(1024, sh.njobs), 256, 0, st>>>(sh, v.g, from_L);
+  const dim3 grid(608, sh.njobs);
+  switch (v.g.ncopy) {
+    case 1: prepare_X_kernel<1><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+    case 2: prepare_X_kernel<2><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+    case 3: prepare_X_kernel<3><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+    case 4: prepare_X_kernel<4><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+    case 5: prepare_X_kernel<5><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+    case 6: prepare_X_kernel<6><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+    case 7: prepare_X_kernel<7><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+    default: prepare_X_kernel<8><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+  }
   return cudaGetLastError();
 }
 

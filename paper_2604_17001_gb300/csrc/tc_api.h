@@ -22,7 +22,9 @@ struct TcGeom {
   int ntt;          // tap tiles of 128 columns (4 groups of rpg tap rows)
   int kcp;          // channels rounded up to 64
   int nch_a;        // 64-wide SW128 chunks of the adjoint A image
-  int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*k3
+  int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*nsl
+  int nsl;          // frames of the halo one tap tile reaches (its partial keeps only those)
+  int slo[16];      // first frame (st) reached by each tap tile
   int rpg;          // adjoint: whole tap rows (k2 taps) per 32-column group (0: taps in order)
   int nus;          // forward U tile stages in shared memory (1 or 2)
   int pitch, HBp;   // shared-memory row pitch of the halo buffers (an odd multiple of 8,
