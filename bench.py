@@ -12,6 +12,7 @@ reported under "learn_V". `value` is BF16 solves/s with the inputs resident in H
 region); "fp32_plain" is the plain FP32 path, one solve at a time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload completion|batch|serving   (the other workload families)
 """
 from __future__ import annotations
 
@@ -48,6 +49,9 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learn", action="store_true")
+    ap.add_argument("--workload", default="prediction", choices=["prediction", "completion", "batch", "serving"],
+                    help="prediction (the default line); the others print their own line")
+    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     return ap.parse_args()
 
 
@@ -351,11 +355,199 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(out))
 
 
+# -- the other workload families (one JSON line each; not the default bench line) --------
+def _learn_V_gpu(ctx, refs, kdims, dev):
+    import torch
+    refs_d = [torch.from_numpy(r).to(dev) for r in refs]
+    V, _ = ctx.icnnm_learn_V(refs_d, kdims)
+    return V
+
+
+def _timed(stream, fn, n):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_completion(args, local):
+    """32x32x8, kernel 5x5x3, 50% uniform observations, 100 iterations: BF16 and FP32
+    solves/s with the stored FP64 oracle run's V, and both errors against that run."""
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    g = np.load(os.path.join(ROOT, "tests", "golden", "completion_32x32x8_k5x5x3.npz"))
+    w = synth.workload(1, n_ref=0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = icnnm.Context(local, stream=stream.cuda_stream)
+    Md, Kd = torch.from_numpy(w["M"]).to(dev), torch.from_numpy(w["mask"]).to(dev)
+    Vd = torch.from_numpy(np.ascontiguousarray(g["V"])).to(dev)
+    Ld = torch.zeros_like(Md)
+    it = int(g["iters"])
+    out = {}
+    for prec in ("bf16", "fp32"):
+        f = lambda: ctx.icnnm_solve(Md, Kd, Vd, w["kdims"], L_out=Ld, max_iters=it, prec=prec)
+        for _ in range(args.warmup):
+            f()
+        sec = _timed(stream, f, args.steps)
+        L = Ld.cpu().numpy().astype(np.float64)
+        out[prec] = {"solves_per_s": args.steps / sec, "ms_per_solve": 1e3 * sec / args.steps,
+                     "rel_err_vs_oracle": float(np.linalg.norm(L - g["L"]) / np.linalg.norm(g["L"]))}
+    ctx.close()
+    print(json.dumps({"metric": METRIC, "workload": "completion_32x32x8_k5x5x3", "value": out["bf16"]["solves_per_s"],
+                      "unit": "solves/s", "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "steps": args.steps, "warmup": args.warmup, "iters": it, "bf16": out["bf16"],
+                      "fp32_plain": out["fp32"], "note": "fits in L2; launch- and latency-bound"}))
+
+
+def run_batch(args, local):
+    """64 uneven tensors (H, W in 32..192 step 16, T in 8..48), kernel 7x7x3, mixed masks,
+    100 iterations: one batched BF16 solve per step (all jobs stepped together) against
+    plain FP32 one job at a time."""
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    kd = synth.WORKLOADS[4]["kdims"]
+    it = synth.WORKLOADS[4]["iters"]
+    jobs = synth.batch_jobs(synth.WORKLOADS[4]["n_jobs"], cfg=4)
+    refs = [synth.video(64, 64, 16, synth.seed_for(4, j)) for j in range(1, synth.WORKLOADS[4]["n_ref"] + 1)]
+    stream = torch.cuda.current_stream(dev)
+    ctx = icnnm.Context(local, stream=stream.cuda_stream)
+    V = _learn_V_gpu(ctx, refs, kd, dev)
+    Ms = [torch.from_numpy(j["M"]).to(dev) for j in jobs]
+    Ks = [torch.from_numpy(j["mask"]).to(dev) for j in jobs]
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(dev)
+    Ls = [torch.zeros_like(m) for m in Ms]
+    vox = sum(int(np.prod(j["dims"])) for j in jobs)
+    f = lambda: ctx.icnnm_solve_batch(Ms, Ks, Vd, kd, L_outs=Ls, max_iters=it, prec="bf16")
+    for _ in range(args.warmup):
+        f()
+    ctx.lib.icnnm_profile_enable(ctx.h, 0)
+    sec = _timed(stream, f, args.steps)
+    import ctypes as C
+    nl = C.c_int64()
+    ctx.lib.icnnm_profile_read(ctx.h, -1, None, C.byref(nl))
+    obs_ok = all(bool(np.array_equal(L.cpu().numpy()[j["mask"].astype(bool)], j["M"][j["mask"].astype(bool)]))
+                 for L, j in zip(Ls, jobs))
+    # plain FP32, one job at a time (one pass over the 64 jobs)
+    g = lambda: [ctx.icnnm_solve(m, k, Vd, kd, L_out=l, max_iters=it, prec="fp32") for m, k, l in zip(Ms, Ks, Ls)]
+    g()
+    fsec = _timed(stream, g, 1)
+    ctx.close()
+    n = len(jobs)
+    print(json.dumps({"metric": METRIC, "workload": "batch64_uneven_k7x7x3", "value": n * args.steps / sec,
+                      "unit": "solves/s", "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "steps": args.steps, "warmup": args.warmup, "iters": it, "jobs": n, "voxels": vox,
+                      "ms_per_batch": 1e3 * sec / args.steps,
+                      "voxel_iters_per_s": vox * it * args.steps / sec, "gpu_launches_per_batch": int(nl.value) // args.steps,
+                      "observed_entries_exact": obs_ok,
+                      "fp32_plain": {"value": n / fsec, "unit": "solves/s", "ms_per_pass": 1e3 * fsec,
+                                     "mode": "one job at a time"}}))
+
+
+def run_serving(args, local):
+    """A Poisson stream of requests (H, W in 32..256 step 16, T in 8..64, kernel 7x7x3,
+    mixed masks), each run to a relative residual of 1e-3 (checked every 10 iterations,
+    at most 1000). Plain FP32 solves every request one at a time (its service times give
+    its capacity and, through a first-come-first-served queue on the same arrival times,
+    its latencies); served BF16 admits the same stream into the continuous-batching
+    server at 0.9x the FP32 capacity, and once more with every request arriving at once
+    (throughput)."""
+    import threading
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    kd = synth.WORKLOADS[5]["kdims"]
+    n = args.requests
+    jobs = synth.batch_jobs(n, cfg=5, hw_range=(32, 256), t_range=(8, 64))
+    refs = [synth.video(64, 64, 16, synth.seed_for(5, j)) for j in range(1, synth.WORKLOADS[5]["n_ref"] + 1)]
+    kw = dict(max_iters=1000, tol=1e-3, check_every=10)
+    ctx = icnnm.Context(local)
+    V = _learn_V_gpu(ctx, refs, kd, dev)
+    # plain FP32 service times (host buffers, blocking, one at a time)
+    ctx.icnnm_solve(jobs[0]["M"], jobs[0]["mask"], V, kd, prec="fp32", **kw)
+    svc, iters32 = [], []
+    for j in jobs:
+        t0 = time.perf_counter()
+        _, st = ctx.icnnm_solve(j["M"], j["mask"], V, kd, prec="fp32", **kw)
+        svc.append(time.perf_counter() - t0)
+        iters32.append(st["iters"])
+    cap32 = n / sum(svc)
+    rate = 0.9 * cap32
+    rng = np.random.default_rng(synth.seed_for(5, 77))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    # FP32 one at a time on the same arrivals (FCFS)
+    done, lat32 = 0.0, []
+    for a, sv in zip(arrivals, svc):
+        start = max(a, done)
+        done = start + sv
+        lat32.append(done - a)
+
+    def serve(arr):
+        lat = [None] * n
+        its = [None] * n
+        ids = [None] * n
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, a in enumerate(arr):
+                dt = a - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                ids[i] = (ctx.icnnm_submit(jobs[i]["M"], jobs[i]["mask"], V, kd, prec="bf16", **kw),
+                          time.perf_counter())
+        th = threading.Thread(target=submitter)
+        th.start()
+        outs = [np.zeros_like(j["M"]) for j in jobs]
+        left = set(range(n))
+        while left:
+            for i in sorted(left):
+                if ids[i] is None:
+                    continue
+                r, st = ctx.icnnm_wait(ids[i][0], L_out=outs[i], timeout_ms=0)
+                if r == icnnm.OK:
+                    lat[i] = time.perf_counter() - ids[i][1]
+                    its[i] = st["iters"]
+                    left.discard(i)
+            time.sleep(0.0005)
+        th.join()
+        return lat, time.perf_counter() - t0, its
+
+    lat_p, span_p, its_p = serve(arrivals)
+    lat_s, span_s, its_s = serve(np.zeros(n))
+    ctx.close()
+    pct = lambda x, q: float(np.percentile(np.asarray(x) * 1e3, q))
+    print(json.dumps({
+        "metric": METRIC, "workload": f"serving_poisson{n}_k7x7x3", "value": n / span_s, "unit": "solves/s",
+        "higher_is_better": True, "dtype": "bf16", "data": "synthetic", "requests": n,
+        "stop": "relative residual <= 1e-3, checked every 10 iterations, at most 1000",
+        "served_bf16": {"saturated": {"solves_per_s": n / span_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99)},
+                        "poisson": {"rate_per_s": rate, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                                    "solves_per_s": n / span_p},
+                        "mean_iters": float(np.mean(its_s))},
+        "plain_fp32": {"solves_per_s": cap32, "poisson_p50_ms": pct(lat32, 50), "poisson_p99_ms": pct(lat32, 99),
+                       "mean_iters": float(np.mean(iters32)), "mode": "one at a time, FCFS on the same arrivals"}}))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "completion":
+        run_completion(args, local)
+    elif args.workload == "batch":
+        run_batch(args, local)
+    elif args.workload == "serving":
+        run_serving(args, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
