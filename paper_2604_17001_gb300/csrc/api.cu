@@ -84,6 +84,10 @@ struct Job {
   bool src_dev = false;
   void* block = nullptr;        // one device allocation for all of the job's state
   size_t bytes = 0;
+  int run_prec = 0;             // arithmetic of the next iterations (BF16 jobs may finish in FP32)
+  void* block2 = nullptr;       // FP32 finish: widened U and the FP32 adjoint workspace
+  size_t bytes2 = 0;
+  double last_resid = INFINITY; // residual at the previous check (BF16 stall detection)
   JobDev dev{};
   Phase phase = QUEUED;
   icnnm_status st = ICNNM_OK;
@@ -311,6 +315,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   const int k = vd->k, kc = vd->kc;
   const int nrp = std::max(fwd_fp32_nrp(k), tc_nrp(k));
   j.bytes = job_bytes(j.H, j.W, j.T, k, kc, j.p.prec, nrp, &vd->tc.g);
+  j.run_prec = j.p.prec;
   if (c->used + j.bytes > c->budget) fail(ICNNM_ENOMEM, "job state exceeds the HBM budget");
   CK(cudaMalloc(&j.block, j.bytes));
   c->used += j.bytes;
@@ -361,6 +366,44 @@ void free_job(icnnm_ctx* c, Job& j) {
     c->used -= j.bytes;
     j.block = nullptr;
   }
+  if (j.block2) {
+    cudaFree(j.block2);
+    c->used -= j.bytes2;
+    j.block2 = nullptr;
+  }
+}
+
+// Mixed-precision finish of a BF16 job with a residual tolerance. U is stored in BF16, so
+// the BF16 residual ||Z - A_k(L)V|| carries U's rounding (about 1e-3 relative) and stalls
+// near that level; a tolerance at or below it cannot be certified in BF16. When the BF16
+// residual is within 4x the tolerance or has stopped falling (less than 10% between
+// checks), the job continues on the FP32 path: U is widened exactly to FP32 (the state
+// the next iteration reads: U, L, X, theta and the column sums are unchanged) and the
+// remaining iterations and residual checks run in FP32. Returns false (the job stays in
+// BF16) when the extra state does not fit the budget.
+bool bf16_should_finish_fp32(const Job& j) {
+  return j.run_prec == ICNNM_BF16 && j.p.tol > 0 && (j.resid <= 4 * j.p.tol || j.resid > 0.9 * j.last_resid);
+}
+
+bool switch_to_fp32(icnnm_ctx* c, Job& j) {
+  const size_t m = (size_t)j.m, kc = (size_t)j.vd->kc, k = (size_t)j.vd->k;
+  const size_t ub = (m * kc * 4 + 255) / 256 * 256;
+  const size_t need = ub + k * m * 4;
+  if (c->used + need > c->budget) return false;
+  void* b = nullptr;
+  if (cudaMalloc(&b, need) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->used += need;
+  j.block2 = b;
+  j.bytes2 = need;
+  float* U32 = static_cast<float*>(b);
+  CK(launch_widen_bf16(static_cast<const __nv_bfloat16*>(j.dev.U), U32, (long long)(m * kc), c->stream));
+  j.dev.U = U32;
+  j.dev.G = reinterpret_cast<float*>(static_cast<char*>(b) + ub);
+  j.run_prec = ICNNM_FP32;
+  return true;
 }
 
 struct List {
@@ -390,7 +433,7 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js) {
   const VData* vd = js[0]->vd;
   Shared sh{};
   sh.k1 = vd->k1; sh.k2 = vd->k2; sh.k3 = vd->k3; sh.k = vd->k; sh.kc = vd->kc;
-  sh.nrp = js[0]->p.prec == ICNNM_FP32 ? fwd_fp32_nrp(vd->k) : tc_nrp(vd->k);
+  sh.nrp = js[0]->run_prec == ICNNM_FP32 ? fwd_fp32_nrp(vd->k) : tc_nrp(vd->k);
   sh.Vf = vd->dVf;
   sh.VtImg = vd->tc_ready ? vd->tc.VtImg : nullptr;
   sh.njobs = n;
@@ -421,7 +464,7 @@ int fwd_slots(const Shared& sh, int prec, const TcVData* tcv) {
 // Initial state: L = P_Omega M, theta0, U0 = -theta0 A_k(L)V and its column norms.
 // theta0's column norms always come from the FP32 forward pass.
 void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
-  const int prec = js[0]->p.prec;
+  const int prec = js[0]->run_prec;
   const TcVData* tcv = &js[0]->vd->tc;
   Shared sh = upload_list(c, js);
   OTHER(1, launch_init_L(sh, c->stream));
@@ -477,7 +520,7 @@ double resid_of(const JobScal& s, int k) {
 
 // Run a fixed set of jobs to completion (blocking solves).
 void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
-  const int prec = js[0]->p.prec;
+  int prec = js[0]->p.prec;
   const TcVData* tcv = &js[0]->vd->tc;
   const int k = js[0]->vd->k;
   cudaEvent_t e0, e1;
@@ -487,6 +530,8 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   engine_init(c, js);
   std::vector<Job*> live = js;
   Shared sh = upload_list(c, live);
+  std::vector<Job*> live32;      // BF16 jobs finishing in FP32 (see switch_to_fp32)
+  Shared sh32{};
   int it = 0;
   const icnnm_params& p = js[0]->p;
   // Runs of plain (non-check) iterations are replayed from a CUDA graph of GRAPH_ITERS
@@ -503,7 +548,7 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
     return n;
   };
   while (!live.empty()) {
-    if (graphs && !c->prof && it >= 1 && plain_run(it + 1) >= GRAPH_ITERS) {
+    if (graphs && !c->prof && it >= 1 && live32.empty() && plain_run(it + 1) >= GRAPH_ITERS) {
       if (!gexec) {
         long long before[5];
         for (int i = 0; i < 5; ++i) before[i] = c->pass_n[i];
@@ -535,22 +580,40 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
     const bool last = it >= p.max_iters;
     const bool check = is_check(it);
     engine_step(c, sh, prec, tcv, check);
+    if (!live32.empty()) engine_step(c, sh32, ICNNM_FP32, nullptr, check);
     if (check) {
-      std::vector<Job*> keep;
-      for (Job* j : live) {
-        JobScal s = read_scal(*j, c->stream);
-        j->resid = resid_of(s, k);
-        j->iters = it;
-        const bool conv = p.tol > 0 && j->resid <= p.tol && it % p.check_every == 0;
-        if (conv || last) j->converged = conv;
-        else keep.push_back(j);
-      }
-      if (keep.size() != live.size()) {
-        live = keep;
-        if (!live.empty()) {
-          sh = upload_list(c, live);
-          if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+      std::vector<Job*> keep, keep32;
+      bool moved = false;
+      for (int grp = 0; grp < 2; ++grp)
+        for (Job* j : grp == 0 ? live : live32) {
+          JobScal s = read_scal(*j, c->stream);
+          j->resid = resid_of(s, k);
+          j->iters = it;
+          const bool conv = p.tol > 0 && j->resid <= p.tol && it % p.check_every == 0;
+          if (conv || last) {
+            j->converged = conv;
+          } else if (grp == 0 && bf16_should_finish_fp32(*j) && switch_to_fp32(c, *j)) {
+            keep32.push_back(j);
+            moved = true;
+          } else {
+            (grp == 0 ? keep : keep32).push_back(j);
+          }
+          j->last_resid = j->resid;
         }
+      if (keep.size() != live.size() || moved) {
+        live = keep;
+        if (!live.empty()) sh = upload_list(c, live);
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+      }
+      if (keep32.size() != live32.size() || moved) {
+        live32 = keep32;
+        if (!live32.empty()) sh32 = upload_list(c, live32);
+      }
+      if (live.empty() && !live32.empty()) {   // only FP32 finishers left: they become the main list
+        live.swap(live32);
+        std::swap(sh, sh32);
+        prec = ICNNM_FP32;
+        tcv = nullptr;
       }
     }
   }
@@ -672,16 +735,20 @@ void server_loop(icnnm_ctx* c) {
       for (auto& j : c->active)
         if (j->phase == RUNNING) run.push_back(j.get());
       if (!run.empty()) {
-        const int prec = run[0]->p.prec;
-        const TcVData* tcv = &run[0]->vd->tc;
-        std::vector<Job*> plain;
-        for (Job* j : run) {
-          const int it = j->iters + 1;
-          const bool check = it >= j->p.max_iters || (j->p.tol > 0 && it % j->p.check_every == 0) || j->cancel;
-          (check ? chk : plain).push_back(j);
+        // the jobs step in groups of one arithmetic (BF16 jobs that finish in FP32 move)
+        for (int prec : {(int)ICNNM_BF16, (int)ICNNM_FP32}) {
+          std::vector<Job*> plain, chk1;
+          for (Job* j : run) {
+            if (j->run_prec != prec) continue;
+            const int it = j->iters + 1;
+            const bool check = it >= j->p.max_iters || (j->p.tol > 0 && it % j->p.check_every == 0) || j->cancel;
+            (check ? chk1 : plain).push_back(j);
+          }
+          const TcVData* tcv = prec == ICNNM_BF16 ? &run[0]->vd->tc : nullptr;
+          if (!plain.empty()) engine_step(c, upload_list(c, plain), prec, tcv, false);
+          if (!chk1.empty()) engine_step(c, upload_list(c, chk1), prec, tcv, true);
+          chk.insert(chk.end(), chk1.begin(), chk1.end());
         }
-        if (!plain.empty()) engine_step(c, upload_list(c, plain), prec, tcv, false);
-        if (!chk.empty()) engine_step(c, upload_list(c, chk), prec, tcv, true);
         for (Job* j : run) j->iters += 1;
         std::vector<Job*> fin;
         for (Job* j : chk) {
@@ -691,7 +758,10 @@ void server_loop(icnnm_ctx* c) {
           if (conv || j->iters >= j->p.max_iters || j->cancel) {
             j->converged = conv;
             fin.push_back(j);
+          } else if (bf16_should_finish_fp32(*j)) {
+            switch_to_fp32(c, *j);
           }
+          j->last_resid = j->resid;
         }
         if (!fin.empty()) {
           engine_objective(c, upload_list(c, fin));

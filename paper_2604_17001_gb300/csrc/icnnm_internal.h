@@ -128,6 +128,8 @@ cudaError_t launch_init_L(const Shared& sh, cudaStream_t st);
 cudaError_t launch_reduce_cols(const Shared& sh, int advance, int slots, cudaStream_t st);
 cudaError_t launch_theta0(const Shared& sh, double theta0_user, cudaStream_t st);
 cudaError_t launch_scale_X(const Shared& sh, cudaStream_t st);
+// dst[i] = float(src[i]) (BF16 to FP32 state, for the FP32 finish of a BF16 job)
+cudaError_t launch_widen_bf16(const __nv_bfloat16* src, float* dst, long long n, cudaStream_t st);
 cudaError_t launch_scalars(const Shared& sh, cudaStream_t st);
 cudaError_t launch_gather_fp32(const Shared& sh, cudaStream_t st);
 // what: 1 = residual (||L||^2 and residual^2 from the partials), 2 = objective

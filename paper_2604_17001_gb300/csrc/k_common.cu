@@ -204,6 +204,12 @@ __global__ void finish_kernel(Shared sh, int what) {
   }
 }
 
+// U widened from BF16 to FP32 (exact), for the FP32 finish of a BF16 job.
+__global__ void widen_bf16_kernel(const __nv_bfloat16* src, float* dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = __bfloat162float(src[i]);
+}
+
 __global__ void check_observed_kernel(const float* M, const uint8_t* mask, long long n, int* out) {
   int cnt = 0, bad = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -218,6 +224,11 @@ __global__ void check_observed_kernel(const float* M, const uint8_t* mask, long 
 
 cudaError_t launch_init_L(const Shared& sh, cudaStream_t st) {
   init_L_kernel<<<sh.total_tiles, TILE_VOX, 0, st>>>(sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_bf16(const __nv_bfloat16* src, float* dst, long long n, cudaStream_t st) {
+  widen_bf16_kernel<<<1216, 256, 0, st>>>(src, dst, n);
   return cudaGetLastError();
 }
 

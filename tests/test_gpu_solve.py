@@ -223,3 +223,26 @@ def test_serving_bf16_mix_equals_alone_and_oracle(ctx):
         assert rel(L, Ls) <= SAME_BF16
         Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=its)
         assert rel(L, Lo) <= TOL["bf16"]
+
+
+@pytest.mark.parametrize("serve", [False, True])
+def test_bf16_tolerance_finishes_in_fp32(ctx, serve):
+    # U is stored in BF16, so the BF16 residual stalls near 1e-3; with tol = 1e-3 a BF16
+    # job finishes its last iterations in FP32 and stops on an exact residual, like the
+    # oracle under the same rule.
+    kd = (5, 5, 3)
+    M, mask, V, _ = case((32, 24, 8), kd, frac=0.5, seed=31)
+    kw = dict(max_iters=1000, tol=1e-3, check_every=10)
+    Lo, so = O.icnnm_solve(M, mask, V, kd, **kw)
+    if serve:
+        jid = ctx.icnnm_submit(M, mask, V, kd, prec="bf16", **kw)
+        L = np.zeros_like(M)
+        r, st = ctx.icnnm_wait(jid, L_out=L, timeout_ms=120000)
+        assert r == icnnm.OK
+    else:
+        L, st = ctx.icnnm_solve(M, mask, V, kd, prec="bf16", **kw)
+    assert st["iters"] < 1000 and st["residual"] <= 1e-3
+    assert abs(st["iters"] - so["iters"]) <= 30
+    msk = mask.astype(bool)
+    assert np.array_equal(L[msk], M[msk])
+    assert rel(L, Lo) <= TOL["bf16"]
