@@ -63,7 +63,10 @@ size_t fwd_smem_n(const TcGeom& g, int nus);
 TcGeom make_geom(int k1, int k2, int k3) {
   TcGeom g{};
   g.k1 = k1; g.k2 = k2; g.k3 = k3; g.k = k1 * k2 * k3; g.kc = rup(g.k, 16);
-  g.R = k1 * k3; g.R8 = rup(g.R, 8);
+  // each w-run of taps is padded to a multiple of 16 (two 8-row K-groups): every MMA then
+  // stays inside one run, its K stride is one group and the issuer advances descriptors
+  // by register adds
+  g.R = k1 * k3; g.R8 = rup(g.R, 16);
   g.ngrp = k2 * (g.R8 / 8);
   g.nmma = (g.ngrp + 1) / 2;
   g.kpad = g.nmma * 16;
@@ -72,7 +75,7 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.nwc = (k2 + 7) / 8;
   g.Hh = TH + k1 - 1;
   g.region_bytes = g.Hh * k3 * 16;
-  g.stage_bytes = rup(k2 * g.region_bytes + 8 * 16, 1024);   // k2 copies + 8 zero rows
+  g.stage_bytes = rup(k2 * g.region_bytes + 16 * 16, 1024);  // k2 copies + 16 zero rows
   g.nct = (g.k + 127) / 128;
   // adjoint tap columns: whole tap rows per 32-column group for the kernel widths with a
   // compile-time col2im (3, 5, 7, 9), taps in order otherwise
@@ -132,6 +135,8 @@ uint32_t group_off(const TcGeom& g, int grp) {
 struct FwdTab {
   uint32_t boff[64];
   uint32_t kstr[64];
+  int reg;       // 1: boff[i] = (i / hp) * region_bytes + (i % hp) * 256 and kstr[i] = 128 for all i
+  int hp;        // MMAs per w-run (half the 8-tap groups of a run)
 };
 
 struct FwdArgs {
@@ -243,8 +248,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     ptx::tmem_relinquish();
   }
   // zero rows after the copies of each stage (read by the padded taps, times zero)
-  for (int i = threadIdx.x; i < 2 * 32; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(sH + (i / 32) * g.stage_bytes + g.k2 * g.region_bytes)[i % 32] = 0u;
+  for (int i = threadIdx.x; i < 2 * 64; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(sH + (i / 64) * g.stage_bytes + g.k2 * g.region_bytes)[i % 64] = 0u;
   ptx::fence_proxy_async_smem();
   ptx::tc_fence_before();
   __syncthreads();
@@ -319,10 +324,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         ptx::tc_fence_after();
         const uint32_t d = tbase + (uint32_t)b * 128;
         const uint64_t sadd = (uint64_t)(((uint32_t)s * (uint32_t)g.stage_bytes) >> 4);   // start-address field
+        if (a.tab.reg) {
+          // regular tap layout: both descriptors advance by register adds (no table
+          // loads, so the issue rate is the tensor core's): A by 256 bytes inside a
+          // w-run and to the next copy's region at its end, B by 32 bytes inside a
+          // 64-tap chunk and to the next chunk at its end
+          uint64_t ad = sDesc[0].x + sadd, bd = sDesc[0].y;
+          const uint64_t a_run = (uint64_t)((g.region_bytes - (a.tab.hp - 1) * 256) >> 4);
+          int jj = 0, bq = 0;
+          for (int i = 0; i < g.nmma; ++i) {
+            ptx::mma_bf16(d, ad, bd, idesc, i > 0 ? 1u : 0u);
+            if (++jj == a.tab.hp) { jj = 0; ad += a_run; } else { ad += 16; }
+            if (++bq == 4) { bq = 0; bd += (CHUNK >> 4) - 6; } else { bd += 2; }
+          }
+        } else {
 #pragma unroll 4
-        for (int i = 0; i < g.nmma; ++i) {
-          const ulonglong2 dd = sDesc[i];
-          ptx::mma_bf16(d, dd.x + sadd, dd.y, idesc, i > 0 ? 1u : 0u);
+          for (int i = 0; i < g.nmma; ++i) {
+            const ulonglong2 dd = sDesc[i];
+            ptx::mma_bf16(d, dd.x + sadd, dd.y, idesc, i > 0 ? 1u : 0u);
+          }
         }
         ptx::mma_commit(&empty[s]);
         ptx::mma_commit(&tfull[b]);
@@ -837,7 +857,7 @@ __global__ void gather_tc_kernel(Shared sh, TcGeom g) {
   const int tile = tile_g - sh.job_tile0[jb];
   const int tw0 = tile % J.ntw, th0 = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
   const int h = th0 * TH + threadIdx.x / TW, w = tw0 * TW + threadIdx.x % TW;
-  __shared__ float red[TILE_VOX];
+  __shared__ float red[TILE_VOX / 32];
   float l2 = 0.f;
   if (h < J.H && w < J.W) {
     const long long v = ((long long)t * J.H + h) * J.W + w;
@@ -846,13 +866,12 @@ __global__ void gather_tc_kernel(Shared sh, TcGeom g) {
     const float Ln = l_update(J, sh.k, v, d);
     l2 = Ln * Ln;
   }
-  red[threadIdx.x] = l2;
+  // ||L'||^2 partial of the tile: warp sums (fixed butterfly order), then the four warps
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float s = 0.f;
-    for (int i = 0; i < TILE_VOX; ++i) s += red[i];
-    J.lpart[tile] = s;
-  }
+  if (threadIdx.x == 0) J.lpart[tile] = (red[0] + red[1]) + (red[2] + red[3]);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1065,6 +1084,11 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
   a.sh = sh;
   a.g = v.g;
   for (int i = 0; i < 64; ++i) { a.tab.boff[i] = v.boff[i]; a.tab.kstr[i] = v.kstr[i]; }
+  a.tab.hp = v.g.R8 / 16;
+  a.tab.reg = (v.g.R8 / 8) % 2 == 0 && (v.g.region_bytes % 16) == 0;
+  for (int i = 0; a.tab.reg && i < v.g.nmma; ++i)
+    if (v.kstr[i] != 128u || v.boff[i] != (uint32_t)((i / a.tab.hp) * v.g.region_bytes + (i % a.tab.hp) * 256))
+      a.tab.reg = 0;
   a.mode = mode;
   const size_t smem = fwd_smem(v.g);
   const int per = tc_fwd_slots(sh, v);

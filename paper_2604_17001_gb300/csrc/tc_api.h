@@ -9,14 +9,14 @@ namespace icnnm {
 struct TcGeom {
   int k1, k2, k3, k, kc;
   // forward pass E = P(X) V (M = 128 voxels, N = 128 channels, K = taps)
-  int R, R8;        // taps per w-run (k1*k3) and the run rounded up to 8 rows
+  int R, R8;        // taps per w-run (k1*k3) and the run padded to a multiple of 16 rows
   int ngrp, nmma;   // K-groups of 8 taps, MMAs of K = 16
   int kpad;         // nmma * 16
   int nch_f;        // 64-wide SW128 chunks of the forward A image
   int ncopy, nwc;   // w-shifted copies of the operand (min(k2, 8)) and 8-wide w-chunks
   int Hh;           // halo height TH + k1 - 1
   int region_bytes; // one copy's halo: Hh * k3 rows of 16 bytes
-  int stage_bytes;  // one halo stage (the k2 copies used + 8 zero rows), 1024-aligned
+  int stage_bytes;  // one halo stage (the k2 copies used + 16 zero rows), 1024-aligned
   int nct;          // channel tiles of 128
   // adjoint pass G = U (D V^T) (M = 128 voxels, N = 128 taps, K = channels)
   int ntt;          // tap tiles of 128 columns (4 groups of rpg tap rows)
