@@ -203,7 +203,7 @@ def run_ours(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         learn = {"seconds": e0.elapsed_time(e1) / 1e3, "refs": len(refs_d), "k": k,
-                 "gram": "autocorrelation lags, FP32 products / FP64 sums", "eig": "FP64 parallel cyclic Jacobi"}
+                 "gram": "autocorrelation lags, FP32 products / FP64 sums", "eig": "FP64 parallel cyclic Jacobi over all SMs (cooperative launch)"}
         if V is None:
             V = V_gpu
     Md = torch.from_numpy(w["M"]).to(dev)

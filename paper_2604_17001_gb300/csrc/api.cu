@@ -948,12 +948,18 @@ icnnm_status icnnm_learn_V(icnnm_ctx* c, const int64_t kdims[3], int32_t b, cons
     CK(cudaMalloc(&dV, sizeof(double) * k * k)); tmp.push_back(dV);
     CK(cudaMalloc(&dVout, sizeof(double) * k * k)); tmp.push_back(dVout);
     CK(cudaMalloc(&dev, sizeof(double) * k)); tmp.push_back(dev);
-    CK(cudaMalloc(&dinfo, sizeof(int))); tmp.push_back(dinfo);
+    CK(cudaMalloc(&dinfo, 2 * sizeof(int))); tmp.push_back(dinfo);
+    CK(cudaMemsetAsync(dinfo, 0, 2 * sizeof(int), c->stream));
+    void* dscr;
+    CK(cudaMalloc(&dscr, learn_eig_grid_scratch(c->device))); tmp.push_back(dscr);
     CK(learn_gram(b, dL, ddims, k1, k2, k3, dpart, nblk, dgram, c->stream));
-    CK(learn_eig(dgram, dV, k, dev, dVout, dinfo, c->stream));
+    CK(learn_eig_grid(dgram, dV, k, dev, dVout, dinfo, dscr, c->stream));
     CK(cudaMemcpyAsync(V_out, dVout, sizeof(double) * k * k, cudaMemcpyDefault, c->stream));
     if (eig_out) CK(cudaMemcpyAsync(eig_out, dev, sizeof(double) * k, cudaMemcpyDefault, c->stream));
+    int hinfo[2] = {0, 0};
+    CK(cudaMemcpyAsync(hinfo, dinfo, sizeof hinfo, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (hinfo[1]) fail(ICNNM_ETIMEOUT, "a bounded grid barrier of the eigensolver expired");
     for (void* p : tmp) cudaFree(p);
     return ICNNM_OK;
   } catch (StatusFail& f) {

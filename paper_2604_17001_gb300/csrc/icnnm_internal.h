@@ -150,6 +150,11 @@ size_t learn_smem_bytes(int k1, int k2, int k3);
 int learn_max_lags();
 cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo,
                       cudaStream_t st);
+// The same eigensolver spread over every SM (cooperative launch, grid barriers); dinfo[0]
+// = sweeps, dinfo[1] = 1 if a grid barrier timed out. scratch: learn_eig_grid_scratch bytes.
+size_t learn_eig_grid_scratch(int dev);
+cudaError_t learn_eig_grid(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo, void* scratch,
+                           cudaStream_t st);
 cudaError_t check_finite(const float* x, long long n, int* dbad, cudaStream_t st);
 cudaError_t learn_gram_streamed(int b, const float* const* dptrs, const int* ddims, int k1, int k2, int k3,
                                 double* dpart, int nblk, double* dlagsum, double* dgram, cudaStream_t st);

@@ -104,6 +104,32 @@ __global__ void gram_kernel(LearnArgs a, double* gram) {
 constexpr int EIG_THREADS = 1024;
 constexpr int EIG_MAXK = 1024;
 
+// Sort by decreasing eigenvalue (stable: ties by index), make the largest-|.| entry of each
+// eigenvector positive (ties: lowest index), write the vectors column by column. One block.
+__device__ void eig_sort_sign(const double* A, const double* V, int k, double* evals_out, double* Vout, double* ev,
+                              int* order) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ev[i] = A[(long long)i * k + i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    int rank = 0;
+    for (int j = 0; j < k; ++j) rank += (ev[j] > ev[i]) || (ev[j] == ev[i] && j < i);
+    order[rank] = i;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < k; o += blockDim.x) {
+    const int i = order[o];
+    int amax = 0;
+    double vmax = -1.0;
+    for (int srow = 0; srow < k; ++srow) {
+      const double a = fabs(V[(long long)srow * k + i]);
+      if (a > vmax) { vmax = a; amax = srow; }
+    }
+    const double sg = V[(long long)amax * k + i] < 0 ? -1.0 : 1.0;
+    for (int srow = 0; srow < k; ++srow) Vout[(long long)o * k + srow] = sg * V[(long long)srow * k + i];
+    evals_out[o] = ev[i];
+  }
+}
+
 __global__ void __launch_bounds__(EIG_THREADS)
 jacobi_kernel(double* A, double* V, int k, int max_sweeps, double tol, double* evals_out,
               double* Vout, int* info) {
@@ -189,28 +215,165 @@ jacobi_kernel(double* A, double* V, int k, int max_sweeps, double tol, double* e
       __syncthreads();
     }
   }
-  // Sort by decreasing eigenvalue (stable), canonical sign, write column-major output.
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ev[i] = A[(long long)i * k + i];
-  __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    int rank = 0;
-    for (int j = 0; j < k; ++j) rank += (ev[j] > ev[i]) || (ev[j] == ev[i] && j < i);
-    order[rank] = i;
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < k; o += blockDim.x) {
-    const int i = order[o];
-    int amax = 0;
-    double vmax = -1.0;
-    for (int srow = 0; srow < k; ++srow) {
-      const double a = fabs(V[(long long)srow * k + i]);
-      if (a > vmax) { vmax = a; amax = srow; }
-    }
-    const double sg = V[(long long)amax * k + i] < 0 ? -1.0 : 1.0;
-    for (int srow = 0; srow < k; ++srow) Vout[(long long)o * k + srow] = sg * V[(long long)srow * k + i];
-    evals_out[o] = ev[i];
-  }
+  eig_sort_sign(A, V, k, evals_out, Vout, ev, order);
   if (threadIdx.x == 0) info[0] = sweep;
+}
+
+
+// Rotation of pair slot i of round r of the round-robin ordering on n (even) indices:
+// p < q, and (c, s) zeroing A[p][q] (c = 1, s = 0 for a padding index or A[p][q] = 0).
+__device__ __forceinline__ void jacobi_pair(const double* A, int k, int n, int r, int i, int& p, int& q, double& c,
+                                            double& s) {
+  if (i == 0) { p = r; q = n - 1; }
+  else { p = (r + i) % (n - 1); q = (r - i + (n - 1)) % (n - 1); }
+  if (p > q) { const int t = p; p = q; q = t; }
+  c = 1.0;
+  s = 0.0;
+  if (q < k) {
+    const double apq = __ldcg(A + (long long)p * k + q);
+    if (apq != 0.0) {
+      const double app = __ldcg(A + (long long)p * k + p), aqq = __ldcg(A + (long long)q * k + q);
+      const double th = (aqq - app) / (2.0 * apq);
+      const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+      c = 1.0 / sqrt(t * t + 1.0);
+      s = t * c;
+    }
+  }
+}
+
+constexpr int JG_THREADS = 256;
+
+// Barrier over all blocks of a cooperative launch: bar[0] arrivals, bar[1] generation,
+// bar[2] error. A wait that exceeds ~2 s sets the error; every later barrier is then a
+// no-op, so the kernel ends promptly and the host reports the failure.
+__device__ __forceinline__ void grid_sync(unsigned* bar) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* verr = bar + 2;
+    if (!*verr) {
+      const unsigned g = *vgen;
+      __threadfence();
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        bar[0] = 0;
+        __threadfence();
+        atomicExch(bar + 1, g + 1);
+      } else {
+        unsigned long long t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        while (*vgen == g) {
+          if (*verr) break;
+          unsigned long long t1;
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+          if (t1 - t0 > 2000000000ull) { atomicExch(bar + 2, 1u); break; }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+// Block sum of v (fixed order) -> part[blockIdx.x]; after a grid barrier every block reads
+// the total as the in-order sum of part[0..gridDim.x).
+__device__ __forceinline__ void block_partial(double v, double* part, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < JG_THREADS / 32; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+__device__ __forceinline__ double grid_total(const double* part, double* red) {
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + b);
+    red[0] = t;
+  }
+  __syncthreads();
+  const double t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// The same cyclic Jacobi as jacobi_kernel, spread over every SM (A, V and the partial sums
+// are read from L2, as other SMs rewrite them between barriers): each round's rotations
+// are computed by every block (into its shared memory, from the matrix as the previous
+// round left it), the row updates and the column updates of the round are split over all
+// threads, with a grid barrier after each.
+__global__ void __launch_bounds__(JG_THREADS)
+jacobi_grid_kernel(double* A, double* V, int k, int max_sweeps, double tol, unsigned* bar, double* part,
+                   int* info) {
+  __shared__ double cs[EIG_MAXK / 2], sn[EIG_MAXK / 2];
+  __shared__ int pp[EIG_MAXK / 2], qq[EIG_MAXK / 2];
+  __shared__ double red[JG_THREADS / 32];
+  const int n = (k + 1) & ~1;
+  const int npair = n / 2;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  double fr = 0.0;
+  for (long long e = gt; e < (long long)k * k; e += nt) {
+    V[e] = (e / k == e % k) ? 1.0 : 0.0;
+    const double a0 = __ldcg(A + e);
+    fr += a0 * a0;
+  }
+  block_partial(fr, part, red);
+  grid_sync(bar);
+  const double normA = sqrt(grid_total(part, red));
+  double* offpart = part + gridDim.x;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    double off = 0.0;
+    for (long long e = gt; e < (long long)k * k; e += nt)
+      if (e / k != e % k) {
+        const double a0 = __ldcg(A + e);
+        off += a0 * a0;
+      }
+    block_partial(off, offpart, red);
+    grid_sync(bar);
+    if (sqrt(grid_total(offpart, red)) <= tol * normA) break;
+    for (int r = 0; r < n - 1; ++r) {
+      for (int i = threadIdx.x; i < npair; i += blockDim.x) jacobi_pair(A, k, n, r, i, pp[i], qq[i], cs[i], sn[i]);
+      __syncthreads();
+      for (long long e = gt; e < (long long)npair * k; e += nt) {
+        const int i = (int)(e / k), col = (int)(e % k);
+        const int p = pp[i], q = qq[i];
+        if (q >= k || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double ap = __ldcg(A + (long long)p * k + col), aq = __ldcg(A + (long long)q * k + col);
+        A[(long long)p * k + col] = c * ap - s * aq;
+        A[(long long)q * k + col] = s * ap + c * aq;
+      }
+      grid_sync(bar);
+      for (long long e = gt; e < (long long)npair * k; e += nt) {
+        const int i = (int)(e / k), row = (int)(e % k);
+        const int p = pp[i], q = qq[i];
+        if (q >= k || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double ap = __ldcg(A + (long long)row * k + p), aq = __ldcg(A + (long long)row * k + q);
+        A[(long long)row * k + p] = c * ap - s * aq;
+        A[(long long)row * k + q] = s * ap + c * aq;
+        const double vp = __ldcg(V + (long long)row * k + p), vq = __ldcg(V + (long long)row * k + q);
+        V[(long long)row * k + p] = c * vp - s * vq;
+        V[(long long)row * k + q] = s * vp + c * vq;
+      }
+      grid_sync(bar);
+    }
+  }
+  if (gt == 0) {
+    info[0] = sweep;
+    info[1] = (int)bar[2];
+  }
+}
+
+__global__ void __launch_bounds__(EIG_THREADS)
+eig_sort_kernel(const double* A, const double* V, int k, double* evals_out, double* Vout) {
+  __shared__ int order[EIG_MAXK];
+  __shared__ double ev[EIG_MAXK];
+  eig_sort_sign(A, V, k, evals_out, Vout, ev, order);
 }
 
 // lagsum[l] += sum_blk part[blk][l] (blocks in order): the running sum over tensors of
@@ -269,6 +432,39 @@ int learn_max_lags() { return AC_THREADS * AC_MAXLAG_PER_THREAD; }
 cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo,
                       cudaStream_t st) {
   jacobi_kernel<<<1, EIG_THREADS, 0, st>>>(dA, dV, k, 30, 1e-15, devals, dVout, dinfo);
+  return cudaGetLastError();
+}
+
+size_t learn_eig_grid_scratch(int dev) {
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return 64 + 2 * (size_t)sms * sizeof(double);
+}
+
+cudaError_t learn_eig_grid(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo, void* scratch,
+                           cudaStream_t st) {
+  int dev = 0, sms = 1, per = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_grid_kernel, JG_THREADS, 0);
+  if (e != cudaSuccess || !coop || per < 1) {
+    cudaGetLastError();
+    return learn_eig(dA, dV, k, devals, dVout, dinfo, st);       // one block
+  }
+  unsigned* bar = static_cast<unsigned*>(scratch);
+  double* part = reinterpret_cast<double*>(static_cast<char*>(scratch) + 64);
+  if ((e = cudaMemsetAsync(bar, 0, 64, st)) != cudaSuccess) return e;
+  int maxs = 30;
+  double tol = 1e-15;
+  void* args[] = {&dA, &dV, &k, &maxs, &tol, &bar, &part, &dinfo};
+  // one block per SM: every block is resident, as the grid barriers require
+  if (cudaLaunchCooperativeKernel((const void*)jacobi_grid_kernel, dim3(sms), dim3(JG_THREADS), args, 0, st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return learn_eig(dA, dV, k, devals, dVout, dinfo, st);       // not co-resident here: one block
+  }
+  eig_sort_kernel<<<1, EIG_THREADS, 0, st>>>(dA, dV, k, devals, dVout);
   return cudaGetLastError();
 }
 
