@@ -12,7 +12,7 @@ reported under "learn_V". `value` is BF16 solves/s with the inputs resident in H
 region); "fp32_plain" is the plain FP32 path, one solve at a time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --workload completion|batch|serving   (the other workload families)
+    python bench.py --workload completion|interpolation|batch|serving   (the other workload families)
 """
 from __future__ import annotations
 
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learn", action="store_true")
-    ap.add_argument("--workload", default="prediction", choices=["prediction", "completion", "batch", "serving"],
+    ap.add_argument("--workload", default="prediction", choices=["prediction", "completion", "interpolation", "batch", "serving"],
                     help="prediction (the default line); the others print their own line")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     return ap.parse_args()
@@ -406,6 +406,44 @@ def run_completion(args, local):
                       "fp32_plain": out["fp32"], "note": "fits in L2; launch- and latency-bound"}))
 
 
+def run_interpolation(args, local):
+    """256x256x64, kernel 7x7x5, every other frame dropped plus 20% of the rest, noise,
+    100 iterations: BF16 and FP32 solves/s with the stored FP64 oracle run's V, and both
+    errors on its 65536 sampled voxels."""
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    path = os.path.join(ROOT, "tests", "golden", "interpolation_256x256x64_k7x7x5.npz")
+    if not os.path.exists(path):
+        print(json.dumps({"workload": "interpolation_256x256x64_k7x7x5", "unavailable": "stored oracle run missing"}))
+        return
+    g = np.load(path)
+    w = synth.workload(3, n_ref=0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = icnnm.Context(local, stream=stream.cuda_stream)
+    Md, Kd = torch.from_numpy(w["M"]).to(dev), torch.from_numpy(w["mask"]).to(dev)
+    Vd = torch.from_numpy(np.ascontiguousarray(g["V"])).to(dev)
+    Ld = torch.zeros_like(Md)
+    it = int(g["iters"])
+    idx, ref = g["sample_idx"], g["L_sample"]
+    out = {}
+    for prec, steps in (("bf16", args.steps), ("fp32", max(1, args.fp32_steps))):
+        f = lambda: ctx.icnnm_solve(Md, Kd, Vd, w["kdims"], L_out=Ld, max_iters=it, prec=prec)
+        f()
+        sec = _timed(stream, f, steps)
+        got = Ld.reshape(-1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+        out[prec] = {"solves_per_s": steps / sec, "ms_per_solve": 1e3 * sec / steps,
+                     "rel_err_vs_oracle_sample": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    ctx.close()
+    m = int(np.prod(w["M"].shape))
+    print(json.dumps({"metric": METRIC, "workload": "interpolation_256x256x64_k7x7x5",
+                      "value": out["bf16"]["solves_per_s"], "unit": "solves/s", "higher_is_better": True,
+                      "dtype": "bf16", "data": "synthetic", "iters": it, "voxels": m,
+                      "voxel_iters_per_s": m * it * out["bf16"]["solves_per_s"], "bf16": out["bf16"],
+                      "fp32_plain": out["fp32"]}))
+
+
 def run_batch(args, local):
     """64 uneven tensors (H, W in 32..192 step 16, T in 8..48), kernel 7x7x3, mixed masks,
     100 iterations: one batched BF16 solve per step (all jobs stepped together) against
@@ -544,6 +582,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "completion":
         run_completion(args, local)
+    elif args.workload == "interpolation":
+        run_interpolation(args, local)
     elif args.workload == "batch":
         run_batch(args, local)
     elif args.workload == "serving":
