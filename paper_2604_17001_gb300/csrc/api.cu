@@ -338,6 +338,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   d.part = (float*)take((size_t)d.ntiles * PROW * kc * 4);
   d.rpart = (float*)take((size_t)d.ntiles * nrp * 4);
   d.lpart = (float*)take((size_t)d.ntiles * 4);
+  d.nlp = j.p.prec == ICNNM_FP32 ? d.ntiles : (int)((m + 1023) / 1024);
   d.colseg = (double*)take((size_t)NSEG * kc * 8);
   d.s = (float*)take(kc * 4);
   d.D = (float*)take(kc * 4);
@@ -402,6 +403,7 @@ bool switch_to_fp32(icnnm_ctx* c, Job& j) {
   CK(launch_widen_bf16(static_cast<const __nv_bfloat16*>(j.dev.U), U32, (long long)(m * kc), c->stream));
   j.dev.U = U32;
   j.dev.G = reinterpret_cast<float*>(static_cast<char*>(b) + ub);
+  j.dev.nlp = j.dev.ntiles;            // the FP32 gather writes one partial per tile
   j.run_prec = ICNNM_FP32;
   return true;
 }
@@ -440,6 +442,8 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js) {
   sh.jobs = c->dlist;
   sh.job_tile0 = c->dtile0;
   sh.total_tiles = t0[n];
+  sh.max_vblk = 1;
+  for (int i = 0; i < n; ++i) sh.max_vblk = std::max(sh.max_vblk, (int)((js[i]->m + 1023) / 1024));
   return sh;
 }
 

@@ -57,7 +57,9 @@ struct JobDev {
   float* part;          // column partial sums of ||.||^2: [rows][PROW][kc], one row per
                         //   tile (FP32 passes) or per forward CTA slot (BF16 pass)
   float* rpart;         // per-tile residual partials: [ntiles][nrp]
-  float* lpart;         // per-tile ||L'||^2 partials: [ntiles]
+  float* lpart;         // ||L'||^2 partials: nlp of them (per tile on the FP32 path, per
+                        //   1024-voxel block on the BF16 path); room for ntiles
+  int nlp;
   double* colseg;       // first-stage column sums: [NSEG][kc]
   float* s;             // kc, shrink factors of this iteration
   float* D;             // kc, 1 - s
@@ -81,6 +83,7 @@ struct Shared {
   const JobDev* jobs;    // device array of njobs
   const int* job_tile0;  // device, njobs + 1 prefix sums of ntiles
   int total_tiles;
+  int max_vblk;          // most 1024-voxel blocks of one job in the list
 };
 
 // Binary search: the job that owns global tile `t`.

@@ -190,7 +190,7 @@ __global__ void finish_kernel(Shared sh, int what) {
   if (what == 2) {
     for (int c = threadIdx.x; c < sh.k; c += blockDim.x) x += sqrt(colsq_of(J, sh.kc, c));
   } else {
-    for (int t = threadIdx.x; t < J.ntiles; t += blockDim.x) x += J.lpart[t];
+    for (int t = threadIdx.x; t < J.nlp; t += blockDim.x) x += J.lpart[t];
     for (int t = threadIdx.x; t < J.ntiles * sh.nrp; t += blockDim.x) y += J.rpart[t];
   }
   a[threadIdx.x] = x;

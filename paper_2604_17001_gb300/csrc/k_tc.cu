@@ -849,29 +849,55 @@ __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
 
 // L-update from the col2im sums: Delta_j (added into J.G by the adjoint pass, over all
 // tap tiles and tiles whose halo covers voxel j) is read and cleared for the next pass,
-// then the same projection as the FP32 path.
-__global__ void gather_tc_kernel(Shared sh, TcGeom g) {
-  const int tile_g = blockIdx.x;
-  const int jb = job_of_tile(sh.job_tile0, sh.njobs, tile_g);
-  const JobDev& J = sh.jobs[jb];
-  const int tile = tile_g - sh.job_tile0[jb];
-  const int tw0 = tile % J.ntw, th0 = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
-  const int h = th0 * TH + threadIdx.x / TW, w = tw0 * TW + threadIdx.x % TW;
-  __shared__ float red[TILE_VOX / 32];
+// then the same projection as the FP32 path. Flat over the voxels: block (b, job) takes
+// voxels 1024 b .. 1024 b + 1023 of the job, four per thread with 16-byte accesses; the
+// block's ||L'||^2 partial goes to lpart[b].
+__global__ void __launch_bounds__(256) gather_tc_kernel(Shared sh) {
+  const JobDev& J = sh.jobs[blockIdx.y];
+  const long long v0 = (long long)blockIdx.x * 1024 + 4 * threadIdx.x;
+  if ((long long)blockIdx.x * 1024 >= J.m) return;             // the whole block is past this job
+  const double th = J.sc->theta, thn = J.sc->theta_next;
+  const float xa = (float)(th + thn), xb = -(float)th;
+  const float inv = (float)(1.0 / (sh.k * th));
   float l2 = 0.f;
-  if (h < J.H && w < J.W) {
-    const long long v = ((long long)t * J.H + h) * J.W + w;
-    const float d = J.G[v];
-    J.G[v] = 0.f;
-    const float Ln = l_update(J, sh.k, v, d);
-    l2 = Ln * Ln;
+  if (v0 + 3 < J.m) {
+    const float4 d = *reinterpret_cast<const float4*>(J.G + v0);
+    *reinterpret_cast<float4*>(J.G + v0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 lo = *reinterpret_cast<const float4*>(J.L + v0);
+    const float4 mv = *reinterpret_cast<const float4*>(J.M + v0);
+    const uchar4 ob = *reinterpret_cast<const uchar4*>(J.mask + v0);
+    const float dd[4] = {d.x, d.y, d.z, d.w}, ll[4] = {lo.x, lo.y, lo.z, lo.w}, mm[4] = {mv.x, mv.y, mv.z, mv.w};
+    const bool oo[4] = {ob.x != 0, ob.y != 0, ob.z != 0, ob.w != 0};
+    float ln[4], xn[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (isinf(J.lam)) {
+        ln[e] = oo[e] ? mm[e] : fmaf(dd[e], inv, ll[e]);
+      } else {
+        const double lt = oo[e] ? J.lam : 0.0;
+        ln[e] = (float)(((double)dd[e] / sh.k + th * (double)ll[e] + lt * (oo[e] ? (double)mm[e] : 0.0)) / (lt + th));
+      }
+      xn[e] = fmaf(xa, ln[e], xb * ll[e]);
+      l2 = fmaf(ln[e], ln[e], l2);
+    }
+    *reinterpret_cast<float4*>(J.L + v0) = make_float4(ln[0], ln[1], ln[2], ln[3]);
+    *reinterpret_cast<float4*>(J.X + v0) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+  } else {
+    for (long long v = v0; v < J.m; ++v) {
+      const float d = J.G[v];
+      J.G[v] = 0.f;
+      const float Ln = l_update(J, sh.k, v, d);
+      l2 = fmaf(Ln, Ln, l2);
+    }
   }
-  // ||L'||^2 partial of the tile: warp sums (fixed butterfly order), then the four warps
+  // block partial in a fixed order: warp butterflies, then the 8 warps
+  __shared__ float red[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
   __syncthreads();
-  if (threadIdx.x == 0) J.lpart[tile] = (red[0] + red[1]) + (red[2] + red[3]);
+  if (threadIdx.x == 0)
+    J.lpart[blockIdx.x] = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1115,7 +1141,8 @@ cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st) {
 }
 
 cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st) {
-  gather_tc_kernel<<<sh.total_tiles, TILE_VOX, 0, st>>>(sh, v.g);
+  (void)v;
+  gather_tc_kernel<<<dim3(sh.max_vblk, sh.njobs), 256, 0, st>>>(sh);
   return cudaGetLastError();
 }
 
