@@ -246,3 +246,20 @@ def test_bf16_tolerance_finishes_in_fp32(ctx, serve):
     msk = mask.astype(bool)
     assert np.array_equal(L[msk], M[msk])
     assert rel(L, Lo) <= TOL["bf16"]
+
+
+def test_bf16_tolerance_batch_mixed_phases(ctx):
+    # Jobs of one batch reach the FP32 finish at different checks, so BF16 and FP32
+    # lists step side by side; each job still stops on an exact residual <= tol and agrees
+    # with the oracle under the same rule.
+    kd = (5, 5, 3)
+    kw = dict(max_iters=1000, tol=1e-3, check_every=10)
+    probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 24, 8), 0.5, 41), ((16, 40, 6), 0.3, 42),
+                                                         ((24, 24, 5), 0.7, 43)]]
+    V = probs[0][2]
+    outs, stats = ctx.icnnm_solve_batch([p[0] for p in probs], [p[1] for p in probs], V, kd, prec="bf16", **kw)
+    for (M, mask, _, _), L, st in zip(probs, outs, stats):
+        assert st["iters"] < 1000 and st["residual"] <= 1e-3
+        Lo, so = O.icnnm_solve(M, mask, V, kd, **kw)
+        assert abs(st["iters"] - so["iters"]) <= 30
+        assert rel(L, Lo) <= TOL["bf16"]
