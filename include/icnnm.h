@@ -152,6 +152,32 @@ icnnm_status icnnm_solve_batch(icnnm_ctx* ctx, int32_t n, const icnnm_shape* sha
                                float* const* L_out, icnnm_stats* stats);
 
 /*
+ * Relative convolution diagnostics of a tensor L0 with respect to V (Sec. III-A,
+ * Definition 2, Eqs. rkL0 and alphaK; the coherence of Eq. coherence):
+ *   sigma_i = ||L0 * kappa_i||_F = ||A_k(L0) v_i||_2   (relative convolution eigenvalues)
+ *   r_K     = |I|, I = {i : sigma_i > rank_tol * max(1, max_j sigma_j)}   (the paper counts
+ *             the nonzero sigma_i; rank_tol is the numerical reading of "nonzero")
+ *   alpha_K = ||A_k(L0) V D|| (operator norm), D_ii = 1/sigma_i on I, 0 elsewhere
+ *   mu_K    = mu_1(V_I), V_I the columns of V on I: (k / r_K) max_s sum_{i in I} V[i*k+s]^2
+ * Computed on the GPU through G = A_k(L0)^T A_k(L0) (circular autocorrelations, FP64
+ * products and sums): sigma_i^2 = v_i^T G v_i, and alpha_K^2 is the largest eigenvalue of
+ * D V^T G V D (FP64 Jacobi). Squaring limits the resolution: a sigma_i that is zero
+ * in exact arithmetic comes out near sqrt(k * 1e-16) * max sigma, so rank_tol should be
+ * at least 1e-6.
+ *   shape    : dims and kdims of L0
+ *   L0       : m floats (host or device)
+ *   V        : k*k doubles as above
+ *   rank_tol : in (0, 1)
+ *   sigma_out: k doubles in V's column order (host or device), or NULL
+ *   r_K, alpha_K, mu_K : host outputs, each may be NULL (alpha_K = mu_K = 0 when I is empty)
+ * EINVAL: bad shape, V not orthonormal to 1e-6, non-finite L0, rank_tol outside (0, 1).
+ * ETIMEOUT: a bounded grid barrier of the eigensolver expired.
+ */
+icnnm_status icnnm_spectral_diagnostics(icnnm_ctx* ctx, const icnnm_shape* shape, const float* L0,
+                                        const double* V, double rank_tol, double* sigma_out,
+                                        int32_t* r_K, double* alpha_K, double* mu_K);
+
+/*
  * Serving. icnnm_submit validates and copies the inputs, queues the job and returns
  * at once with its id. A serving thread admits queued jobs while their device state
  * fits the HBM budget, keeps admitted jobs resident, and steps all admitted jobs that

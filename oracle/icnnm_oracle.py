@@ -30,7 +30,8 @@ __all__ = [
     "conv_index", "conv_matrix", "conv_matrix_times", "adjoint", "adjoint_of_product",
     "P_Omega", "column_norms", "norm_21", "gram", "learn_V", "canonical_signs",
     "prox_21", "icnnm_init", "icnnm_iteration", "icnnm_solve", "cnnm_solve",
-    "relative_eigvals", "spectral_correlation", "relative_rank", "theta0_default",
+    "relative_eigvals", "spectral_correlation", "relative_rank", "active_coherence",
+    "theta0_default",
 ]
 
 CHUNK_ROWS = 8192
@@ -223,6 +224,21 @@ def spectral_correlation(L0, V, kdims, tol=1e-9) -> float:
     sup = s > tol * max(1.0, s.max())
     d = np.where(sup, 1.0 / np.where(sup, s, 1.0), 0.0)
     return float(np.linalg.norm(Q * d[None, :], 2))
+
+
+def active_coherence(L0, V, kdims, tol=1e-9) -> float:
+    """mu_K^I = mu_1(K_I), the first coherence (Eq. (coherence)) of the active submatrix
+    K_I, the columns of K on the column support I of A_k(L0)K (Sec. III-A). K_I has
+    orthonormal columns, so its skinny SVD has left factor K_I itself and
+    mu_1(K_I) = (k / r) max_s ||[K_I]_{s,:}||^2. Zero when I is empty."""
+    s = relative_eigvals(L0, V, kdims)
+    sup = s > tol * max(1.0, s.max())
+    r = int(sup.sum())
+    if r == 0:
+        return 0.0
+    U, sv, _ = np.linalg.svd(V[:, sup], full_matrices=False)
+    Ur = U[:, sv > 1e-12]
+    return float(V.shape[0] / Ur.shape[1] * np.max(np.sum(Ur * Ur, axis=1)))
 
 
 # ----------------------------------------------------------------------------------

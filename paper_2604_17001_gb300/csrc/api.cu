@@ -975,6 +975,93 @@ icnnm_status icnnm_learn_V(icnnm_ctx* c, const int64_t kdims[3], int32_t b, cons
   }
 }
 
+icnnm_status icnnm_spectral_diagnostics(icnnm_ctx* c, const icnnm_shape* shape, const float* L0, const double* V,
+                                        double rank_tol, double* sigma_out, int32_t* r_K, double* alpha_K,
+                                        double* mu_K) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  std::vector<void*> tmp;
+  try {
+    CK(cudaSetDevice(c->device));
+    int H, W, T, k1, k2, k3;
+    validate_shape(shape, H, W, T, k1, k2, k3);
+    if (!L0) fail(ICNNM_EINVAL, "L0 is NULL");
+    if (!(rank_tol > 0 && rank_tol < 1)) fail(ICNNM_EINVAL, "rank_tol must be in (0, 1)");
+    if ((long long)(2 * k1 - 1) * (2 * k2 - 1) * (2 * k3 - 1) > learn_max_lags())
+      fail(ICNNM_EUNSUPPORTED, "too many autocorrelation lags for this build");
+    if (learn_smem_bytes(k1, k2, k3) > 220 * 1024) fail(ICNNM_EUNSUPPORTED, "kernel too large");
+    VData* vd = get_vdata(c, V, k1, k2, k3, ICNNM_FP32);       // validates V (orthonormal, finite)
+    const int k = vd->k;
+    const long long m = (long long)H * W * T;
+    auto dalloc = [&](size_t bytes) {
+      void* p;
+      CK(cudaMalloc(&p, bytes));
+      tmp.push_back(p);
+      return p;
+    };
+    const float* dL = L0;
+    if (!is_device_ptr(L0)) {
+      float* p = (float*)dalloc(m * 4);
+      CK(cudaMemcpyAsync(p, L0, m * 4, cudaMemcpyHostToDevice, c->stream));
+      dL = p;
+    }
+    int* dbad = (int*)dalloc(4);
+    CK(cudaMemsetAsync(dbad, 0, 4, c->stream));
+    CK(check_finite(dL, m, dbad, c->stream));
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, dbad, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hbad) fail(ICNNM_EINVAL, "L0 has a non-finite entry");
+    const int dims[3] = {H, W, T};
+    const float** dLp = (const float**)dalloc(sizeof(float*));
+    int* ddims = (int*)dalloc(sizeof dims);
+    CK(cudaMemcpyAsync(dLp, &dL, sizeof(float*), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(ddims, dims, sizeof dims, cudaMemcpyHostToDevice, c->stream));
+    const size_t kk = (size_t)k * k;
+    const long long nlag = (long long)(2 * k1 - 1) * (2 * k2 - 1) * (2 * k3 - 1);
+    int sms = 1;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int nblk = 2 * sms;                // b = 1: spread the bricks over every SM
+    double* dpart = (double*)dalloc(sizeof(double) * nblk * nlag);
+    double* dG = (double*)dalloc(sizeof(double) * kk);
+    double* dV = (double*)dalloc(sizeof(double) * kk);
+    double* dT = (double*)dalloc(sizeof(double) * kk);
+    double* dP = (double*)dalloc(sizeof(double) * kk);
+    double* dS = (double*)dalloc(sizeof(double) * kk);
+    double* dR = (double*)dalloc(sizeof(double) * kk);
+    double* dRout = (double*)dalloc(sizeof(double) * kk);
+    double* dsig = (double*)dalloc(sizeof(double) * k);
+    double* dev = (double*)dalloc(sizeof(double) * k);
+    double* dout = (double*)dalloc(sizeof(double) * 2);
+    int* dinfo = (int*)dalloc(2 * sizeof(int));
+    void* dscr = dalloc(learn_eig_grid_scratch(c->device));
+    CK(cudaMemsetAsync(dinfo, 0, 2 * sizeof(int), c->stream));
+    CK(cudaMemcpyAsync(dV, vd->V64.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, c->stream));
+    CK(learn_gram(1, dLp, ddims, k1, k2, k3, dpart, nblk, dG, c->stream, true));
+    CK(diag_spectral(dG, dV, k, rank_tol, dT, dP, dsig, dS, dout, c->stream));
+    CK(learn_eig_grid(dS, dR, k, dev, dRout, dinfo, dscr, c->stream));
+    double hout[2] = {0, 0}, lmax = 0;
+    int hinfo[2] = {0, 0};
+    if (sigma_out) CK(cudaMemcpyAsync(sigma_out, dsig, sizeof(double) * k, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(hout, dout, sizeof hout, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&lmax, dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hinfo, dinfo, sizeof hinfo, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hinfo[1]) fail(ICNNM_ETIMEOUT, "a bounded grid barrier of the eigensolver expired");
+    if (r_K) *r_K = (int32_t)hout[0];
+    if (mu_K) *mu_K = hout[1];
+    if (alpha_K) *alpha_K = hout[0] > 0 ? sqrt(fmax(lmax, 0.0)) : 0.0;
+    for (void* p : tmp) cudaFree(p);
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    for (void* p : tmp) cudaFree(p);
+    return report(c, f);
+  } catch (CudaFail& f) {
+    for (void* p : tmp) cudaFree(p);
+    return report(c, f);
+  }
+}
+
 icnnm_status icnnm_solve_batch(icnnm_ctx* c, int32_t n, const icnnm_shape* shapes, const float* const* M,
                                const uint8_t* const* mask, const double* V, const icnnm_params* params,
                                float* const* L_out, icnnm_stats* stats) {

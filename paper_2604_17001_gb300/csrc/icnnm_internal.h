@@ -147,8 +147,15 @@ cudaError_t launch_adj_gemm_fp32(const Shared& sh, cudaStream_t st);
 int fwd_fp32_nrp(int k);
 
 // k_learn.cu
+// exact: FP64 products and sums (diagnostics); otherwise FP32 products summed over 64
+// voxels, then in FP64.
 cudaError_t learn_gram(int b, const float* const* dL, const int* ddims, int k1, int k2, int k3,
-                       double* dpart, int nblk, double* dgram, cudaStream_t st);
+                       double* dpart, int nblk, double* dgram, cudaStream_t st, bool exact = false);
+// P = V^T G V (dT: k*k scratch), sigma_i = sqrt(P_ii), the support I (sigma_i > tol *
+// max(1, max sigma)), S = D P D (D = 1/sigma on I, 0 elsewhere), dout[0] = r_K,
+// dout[1] = mu_1(V_I).
+cudaError_t diag_spectral(const double* dG, const double* dV, int k, double tol, double* dT, double* dP,
+                          double* dsigma, double* dS, double* dout, cudaStream_t st);
 size_t learn_smem_bytes(int k1, int k2, int k3);
 int learn_max_lags();
 cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo,

@@ -32,6 +32,9 @@ struct LearnArgs {
 };
 
 // Lag index l <-> (dt, dh, dw) with dt in [-(k3-1), k3-1] etc, l = ((dt+k3-1)*nl1 + dh+k1-1)*nl2 + dw+k2-1.
+// EXACT: products and sums in FP64 (the product of two floats is exact in FP64), for the
+// diagnostics, whose smallest eigenvalues need the extra range.
+template <bool EXACT>
 __global__ void __launch_bounds__(AC_THREADS) autocorr_kernel(LearnArgs a) {
   extern __shared__ float sL[];
   const int j = blockIdx.x;
@@ -62,6 +65,17 @@ __global__ void __launch_bounds__(AC_THREADS) autocorr_kernel(LearnArgs a) {
     __syncthreads();
     const int vw = min(BW, W - bw * BW), vh = min(BH, H - bh * BH), vt = min(BT, T - bt * BT);
     for (int q = 0; q < nmy; ++q) {
+      if (EXACT) {
+        double part = 0.0;
+        for (int z = 0; z < vt; ++z)
+          for (int y = 0; y < vh; ++y) {
+            const int base = ((z + a.k3 - 1) * eh + (y + a.k1 - 1)) * ew + (a.k2 - 1);
+            for (int x = 0; x < vw; ++x)
+              part = fma((double)sL[base + x], (double)sL[base + x + lagoff[q]], part);
+          }
+        acc[q] += part;
+        continue;
+      }
       float part = 0.f;
       int cnt = 0;
       for (int z = 0; z < vt; ++z)
@@ -398,6 +412,87 @@ __global__ void gram_from_lags_kernel(const double* lagsum, int k1, int k2, int 
   gram[idx] = lagsum[((ut - st + k3 - 1) * nl1 + (uh - shh + k1 - 1)) * nl2 + (uw - sw + k2 - 1)];
 }
 
+// Diagnostics (Sec. III-A, Definition 2). With G = A_k(L0)^T A_k(L0) and K = V:
+// P = K^T G K, sigma_i^2 = P_ii, and (A_k(L0) K D)^T (A_k(L0) K D) = D P D.
+// T[j][s] = sum_u G[s][u] V[j][u]   (V[j*k + u] = tap u of eigenvector j)
+__global__ void gv_kernel(const double* G, const double* V, int k, double* T) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)k * k) return;
+  const int j = (int)(idx / k), srow = (int)(idx % k);
+  double t = 0.0;
+  for (int u = 0; u < k; ++u) t = fma(G[(long long)srow * k + u], V[(long long)j * k + u], t);
+  T[idx] = t;
+}
+
+// P[i][j] = sum_s V[i][s] T[j][s]
+__global__ void vt_kernel(const double* V, const double* T, int k, double* P) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)k * k) return;
+  const int i = (int)(idx / k), j = (int)(idx % k);
+  double p = 0.0;
+  for (int srow = 0; srow < k; ++srow) p = fma(V[(long long)i * k + srow], T[(long long)j * k + srow], p);
+  P[idx] = p;
+}
+
+// One block: sigma_i = sqrt(max(P_ii, 0)); I = {i : sigma_i > tol * max(1, max sigma)};
+// S = D P D (zero outside I) for the eigensolver; out[0] = r_K, out[1] = mu_1(V_I) =
+// (k / r) max_s sum_{i in I} V[i][s]^2 (Eq. (coherence); V_I has orthonormal columns).
+__global__ void __launch_bounds__(EIG_THREADS)
+diag_support_kernel(const double* P, const double* V, int k, double tol, double* sigma, double* S, double* out) {
+  __shared__ double red[EIG_THREADS];
+  __shared__ double d[EIG_MAXK];
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double sg = sqrt(fmax(P[(long long)i * k + i], 0.0));
+    sigma[i] = sg;
+    d[i] = sg;
+    mx = fmax(mx, sg);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const double thr = tol * fmax(1.0, red[0]);
+  __syncthreads();
+  int cnt = 0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const bool on = d[i] > thr;
+    d[i] = on ? 1.0 / d[i] : 0.0;
+    cnt += on;
+  }
+  red[threadIdx.x] = (double)cnt;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    S[e] = d[i] * P[e] * d[j];
+  }
+  double rowmax = 0.0;
+  for (int srow = threadIdx.x; srow < k; srow += blockDim.x) {
+    double q = 0.0;
+    for (int i = 0; i < k; ++i)
+      if (d[i] != 0.0) q = fma(V[(long long)i * k + srow], V[(long long)i * k + srow], q);
+    rowmax = fmax(rowmax, q);
+  }
+  red[threadIdx.x] = rowmax;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = r;
+    out[1] = r > 0 ? (double)k / r * red[0] : 0.0;
+  }
+}
+
 __global__ void finite_check_kernel(const float* x, long long n, int* bad) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     if (!isfinite(x[i])) { atomicExch(bad, 1); return; }
@@ -407,7 +502,7 @@ __global__ void finite_check_kernel(const float* x, long long n, int* bad) {
 
 // Host launchers -------------------------------------------------------------------
 cudaError_t learn_gram(int b, const float* const* dL, const int* ddims, int k1, int k2, int k3,
-                       double* dpart, int nblk, double* dgram, cudaStream_t st) {
+                       double* dpart, int nblk, double* dgram, cudaStream_t st, bool exact) {
   LearnArgs a;
   a.b = b; a.L = dL; a.dims = ddims; a.k1 = k1; a.k2 = k2; a.k3 = k3;
   a.nl1 = 2 * k1 - 1; a.nl2 = 2 * k2 - 1; a.nl3 = 2 * k3 - 1;
@@ -415,8 +510,13 @@ cudaError_t learn_gram(int b, const float* const* dL, const int* ddims, int k1, 
   a.nblk = nblk; a.part = dpart;
   const int ew = BW + 2 * (k2 - 1), eh = BH + 2 * (k1 - 1), et = BT + 2 * (k3 - 1);
   const size_t smem = sizeof(float) * (size_t)ew * eh * et;
-  cudaFuncSetAttribute(autocorr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  autocorr_kernel<<<dim3(b, nblk), AC_THREADS, smem, st>>>(a);
+  if (exact) {
+    cudaFuncSetAttribute(autocorr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    autocorr_kernel<true><<<dim3(b, nblk), AC_THREADS, smem, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(autocorr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    autocorr_kernel<false><<<dim3(b, nblk), AC_THREADS, smem, st>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long kk = (long long)k1 * k2 * k3;
@@ -478,15 +578,24 @@ cudaError_t learn_gram_streamed(int b, const float* const* dptrs, const int* ddi
   a.nlag = a.nl1 * a.nl2 * a.nl3;
   a.nblk = nblk; a.part = dpart;
   const size_t smem = learn_smem_bytes(k1, k2, k3);
-  cudaFuncSetAttribute(autocorr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(autocorr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   for (int j = 0; j < b; ++j) {
     a.L = dptrs + j;
     a.dims = ddims + 3 * j;
-    autocorr_kernel<<<dim3(1, nblk), AC_THREADS, smem, st>>>(a);
+    autocorr_kernel<false><<<dim3(1, nblk), AC_THREADS, smem, st>>>(a);
     lag_accumulate_kernel<<<(a.nlag + 255) / 256, 256, 0, st>>>(dpart, nblk, a.nlag, dlagsum, j == 0);
   }
   const long long kk = (long long)k1 * k2 * k3;
   gram_from_lags_kernel<<<(unsigned)((kk * kk + 255) / 256), 256, 0, st>>>(dlagsum, k1, k2, k3, dgram);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_spectral(const double* dG, const double* dV, int k, double tol, double* dT, double* dP,
+                          double* dsigma, double* dS, double* dout, cudaStream_t st) {
+  const unsigned nb = (unsigned)(((long long)k * k + 255) / 256);
+  gv_kernel<<<nb, 256, 0, st>>>(dG, dV, k, dT);
+  vt_kernel<<<nb, 256, 0, st>>>(dV, dT, k, dP);
+  diag_support_kernel<<<1, EIG_THREADS, 0, st>>>(dP, dV, k, tol, dsigma, dS, dout);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
         "icnnm_cancel": ([P, U64], I32),
         "icnnm_profile_enable": ([P, I32], I32),
         "icnnm_profile_read": ([P, I32, C.POINTER(D), C.POINTER(I64)], I32),
+        "icnnm_spectral_diagnostics": ([P, C.POINTER(icnnm_shape), P, P, D, P, C.POINTER(I32), C.POINTER(D),
+                                        C.POINTER(D)], I32),
         "icnnm_learn_V_noalloc": ([C.POINTER(I64), I32, C.POINTER(icnnm_shape), C.POINTER(P), P, P, P], I32),
         "icnnm_noalloc_last_error": ([], C.c_char_p),
     }
@@ -201,6 +203,23 @@ class Context:
         if own:
             return V_out.T.copy(), eig_out
         return V_out, eig_out
+
+    def icnnm_spectral_diagnostics(self, L0, V, kdims, rank_tol=1e-6, dims=None):
+        """Relative convolution eigenvalues sigma (in V's column order), r_K, alpha_K and
+        mu_K of L0 ((T, H, W) / (H, W) float32 array or tensor) with respect to V (a
+        (k, k) array whose column i is eigenvector i). Returns a dict."""
+        shp = tuple(L0.shape)
+        if dims is None:
+            dims = (shp[1], shp[2], shp[0]) if len(shp) == 3 else (shp[0], shp[1])
+        s = make_shape(dims, kdims)
+        k = int(np.prod(kdims))
+        sigma = np.zeros(k, dtype=np.float64)
+        r = C.c_int32(0)
+        a, mu = C.c_double(0.0), C.c_double(0.0)
+        Vc = self._v_colmajor(V)
+        self._check(self.lib.icnnm_spectral_diagnostics(self.h, C.byref(s), _ptr(L0), _ptr(Vc), float(rank_tol),
+                                                        _ptr(sigma), C.byref(r), C.byref(a), C.byref(mu)))
+        return dict(sigma=sigma, r_K=int(r.value), alpha_K=float(a.value), mu_K=float(mu.value))
 
     # -- solves -----------------------------------------------------------------
     @staticmethod

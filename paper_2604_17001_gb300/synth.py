@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "video", "mask_uniform", "mask_last_frames", "mask_every_other_frame",
     "mask_drop_frames_plus_random", "mask_block_holes", "mask_mixed",
-    "workload", "WORKLOADS", "seed_for",
+    "workload", "WORKLOADS", "seed_for", "image_jobs",
 ]
 
 
@@ -165,6 +165,10 @@ WORKLOADS = {
             iters=100, mask="mixed", n_jobs=64),
     5: dict(name="serving_poisson2000_k7x7x3", dims=None, kdims=(7, 7, 3), n_ref=32,
             iters=None, mask="mixed", n_jobs=2000),
+    # image completion (Sec. V-A): 200x200 images, 13x13 kernel, V from 7 reference
+    # images, masks of 4x4 pixel blocks (adjacent pixels tend to be missing together)
+    6: dict(name="image_200x200_k13x13", dims=(200, 200, 1), kdims=(13, 13, 1), n_ref=7,
+            iters=500, mask="blocks4_50pct", n_images=24),
 }
 
 
@@ -175,6 +179,8 @@ def _mask_for(cfg: int, H, W, T):
         return mask_last_frames(H, W, T, 8 if T >= 16 else max(1, T // 4))
     if cfg == 3:
         return mask_drop_frames_plus_random(H, W, T, 0.2, seed_for(3, 500))
+    if cfg == 6:
+        return mask_block_holes(H, W, T, seed_for(6, 500), block=4, hole_frac=0.5)
     raise ValueError(cfg)
 
 
@@ -217,4 +223,18 @@ def batch_jobs(n_jobs: int, cfg: int = 4, hw_range=(32, 192), t_range=(8, 48)):
         mask, fam = mask_mixed(H, W, T, seed_for(cfg, 500) + 13 * j)
         M = np.where(mask.astype(bool), L0, 0).astype(np.float32)
         jobs.append(dict(L0=L0, M=M, mask=mask, dims=(H, W, T), family=fam))
+    return jobs
+
+
+def image_jobs(n_images: int, missing: float = 0.5, dims=(200, 200)):
+    """Targets of the image-completion family: n_images smooth images (T = 1) with
+    masks of 4x4 pixel blocks, about ``missing`` of them missing. Returns a list of
+    dict(L0, M, mask, dims)."""
+    H, W = dims
+    jobs = []
+    for j in range(n_images):
+        L0 = video(H, W, 1, seed_for(6, 100 + j))
+        mask = mask_block_holes(H, W, 1, seed_for(6, 500) + j, block=4, hole_frac=missing)
+        M = np.where(mask.astype(bool), L0, 0).astype(np.float32)
+        jobs.append(dict(L0=L0, M=M, mask=mask, dims=(H, W, 1)))
     return jobs

@@ -245,6 +245,9 @@ def test_bf16_tolerance_finishes_in_fp32(ctx, serve):
     assert abs(st["iters"] - so["iters"]) <= 30
     msk = mask.astype(bool)
     assert np.array_equal(L[msk], M[msk])
+    # the iterate is unique for a given iteration count; the stopping check may land one
+    # check apart on the two sides, so compare with the oracle run for the same count
+    Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=st["iters"])
     assert rel(L, Lo) <= TOL["bf16"]
 
 
@@ -260,6 +263,8 @@ def test_bf16_tolerance_batch_mixed_phases(ctx):
     outs, stats = ctx.icnnm_solve_batch([p[0] for p in probs], [p[1] for p in probs], V, kd, prec="bf16", **kw)
     for (M, mask, _, _), L, st in zip(probs, outs, stats):
         assert st["iters"] < 1000 and st["residual"] <= 1e-3
-        Lo, so = O.icnnm_solve(M, mask, V, kd, **kw)
+        _, so = O.icnnm_solve(M, mask, V, kd, **kw)
         assert abs(st["iters"] - so["iters"]) <= 30
+        assert np.array_equal(L[mask.astype(bool)], M[mask.astype(bool)])
+        Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=st["iters"])
         assert rel(L, Lo) <= TOL["bf16"]

@@ -362,3 +362,32 @@ def test_planted_multiplier_sign_is_caught(monkeypatch):
     monkeypatch.setattr(O, "icnnm_iteration", wrong)
     with pytest.raises(AssertionError):
         test_multiplier_update_dual_feasibility(np.inf)
+
+
+def test_active_coherence_bounds_and_special_cases():
+    # Eq. (coherence): 1 <= mu_1(B) <= p for a p x r matrix B; for K_I (k x r, orthonormal
+    # columns) the row norms sum to r and none exceeds 1, so 1 <= mu_K^I <= k / r.
+    L0 = synth.video(10, 8, 4, seed=23).astype(np.float64)
+    kd = (3, 3, 2)
+    k = 18
+    # full support and an orthogonal K: every row of K has unit norm, so mu = 1
+    Vr = np.linalg.qr(RNG.standard_normal((k, k)))[0]
+    assert O.relative_rank(L0, Vr, kd) == k
+    assert O.active_coherence(L0, Vr, kd) == pytest.approx(1.0, abs=1e-12)
+    # a rank-2 plane wave with its own eigenvectors: I = the two leading columns
+    hh, ww = np.meshgrid(np.arange(12), np.arange(12), indexing="ij")
+    P = (0.5 + 0.4 * np.cos(2 * np.pi * (hh + 2 * ww) / 12.0)).reshape(1, 12, 12)
+    kd2 = (4, 4, 1)
+    V, _ = O.learn_V([P], kd2)
+    s = O.relative_eigvals(P, V, kd2)
+    r = O.relative_rank(P, V, kd2)
+    assert r == 3 and np.all(s[3:] < 1e-9 * s[0])            # constant term + the cos pair
+    # K_I spans the row space of A_k(P), so K_I K_I^T is the projector pinv(A) A and the
+    # squared row norms of K_I are its diagonal
+    A = O.conv_matrix(P, kd2)
+    proj = np.linalg.pinv(A, rcond=1e-10) @ A
+    mu = O.active_coherence(P, V, kd2)
+    assert mu == pytest.approx(16 / 3 * np.max(np.diag(proj)), rel=1e-9)
+    assert 1 - 1e-12 <= mu <= 16 / 3 + 1e-12
+    # K = I (unit taps) keeps full support on a generic tensor, so mu = 1 again
+    assert O.active_coherence(L0, np.eye(k), kd) == pytest.approx(1.0, abs=1e-12)
