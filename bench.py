@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learn", action="store_true")
-    ap.add_argument("--workload", default="prediction", choices=["prediction", "completion", "interpolation", "batch", "serving"],
+    ap.add_argument("--workload", default="prediction", choices=["prediction", "completion", "interpolation", "batch", "serving", "image", "cnnm"],
                     help="prediction (the default line); the others print their own line")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     return ap.parse_args()
@@ -575,6 +575,116 @@ def run_serving(args, local):
                        "mean_iters": float(np.mean(iters32)), "mode": "one at a time, FCFS on the same arrivals"}}))
 
 
+def run_image(args, local):
+    """Image completion (Sec. V-A shape): 200x200 images, 13x13 kernel, 4x4-pixel blocks
+    missing at 50%, 500 iterations, V from 7 reference images. BF16 and FP32 solves/s of
+    one image with the stored FP64 oracle run's V (errors against that run), a batch of
+    24 images stepped together, and the spectral correlation alpha_K of the target under
+    the reference schemes of the paper's Table I (the target itself, one other image, 7
+    images, a random orthogonal K), computed on the GPU."""
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    g = np.load(os.path.join(ROOT, "tests", "golden", "image_200x200_k13x13.npz"))
+    w = synth.workload(6)
+    kd = w["kdims"]
+    it = int(g["iters"])
+    stream = torch.cuda.current_stream(dev)
+    ctx = icnnm.Context(local, stream=stream.cuda_stream)
+    Md, Kd = torch.from_numpy(w["M"]).to(dev), torch.from_numpy(w["mask"]).to(dev)
+    Vd = torch.from_numpy(np.ascontiguousarray(g["V"])).to(dev)
+    Ld = torch.zeros_like(Md)
+    out = {}
+    for prec, steps in (("bf16", max(args.steps, 10)), ("fp32", max(args.steps, 3))):
+        f = lambda: ctx.icnnm_solve(Md, Kd, Vd, kd, L_out=Ld, max_iters=it, prec=prec)
+        for _ in range(args.warmup):
+            f()
+        sec = _timed(stream, f, steps)
+        L = Ld.cpu().numpy().astype(np.float64)
+        out[prec] = {"solves_per_s": steps / sec, "ms_per_solve": 1e3 * sec / steps,
+                     "rel_err_vs_oracle": float(np.linalg.norm(L - g["L"]) / np.linalg.norm(g["L"])),
+                     "rel_err_vs_target": float(np.linalg.norm(L - w["L0"]) / np.linalg.norm(w["L0"]))}
+    jobs = synth.image_jobs(synth.WORKLOADS[6]["n_images"])
+    Ms = [torch.from_numpy(j["M"]).to(dev) for j in jobs]
+    Ks = [torch.from_numpy(j["mask"]).to(dev) for j in jobs]
+    Ls = [torch.zeros_like(m) for m in Ms]
+    fb = lambda: ctx.icnnm_solve_batch(Ms, Ks, Vd, kd, L_outs=Ls, max_iters=it, prec="bf16")
+    for _ in range(args.warmup):
+        fb()
+    secb = _timed(stream, fb, args.steps)
+    errs = [float(np.linalg.norm(l.cpu().numpy() - j["L0"]) / np.linalg.norm(j["L0"])) for l, j in zip(Ls, jobs)]
+    # Table I schemes (alpha_K of the target)
+    rng = np.random.default_rng(synth.seed_for(6, 900))
+    L0d = torch.from_numpy(w["L0"]).to(dev)
+    schemes = {"G.T. (the target)": _learn_V_gpu(ctx, [w["L0"]], kd, dev),
+               "one other image": _learn_V_gpu(ctx, w["refs"][:1], kd, dev),
+               "7 reference images": g["V"],
+               "random orthogonal": np.linalg.qr(rng.standard_normal((169, 169)))[0]}
+    table = {}
+    for name, V in schemes.items():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dg = ctx.icnnm_spectral_diagnostics(L0d, V, kd, rank_tol=1e-6)
+        torch.cuda.synchronize()
+        table[name] = {"alpha_K": dg["alpha_K"], "r_K": dg["r_K"], "mu_K": dg["mu_K"],
+                       "ms": 1e3 * (time.perf_counter() - t0)}
+    ctx.close()
+    print(json.dumps({"metric": METRIC, "workload": "image_200x200_k13x13", "value": out["bf16"]["solves_per_s"],
+                      "unit": "solves/s", "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "iters": it, "bf16": out["bf16"], "fp32_plain": out["fp32"],
+                      "batch24_bf16": {"images_per_s": len(jobs) * args.steps / secb,
+                                       "ms_per_batch": 1e3 * secb / args.steps,
+                                       "mean_rel_err_vs_target": float(np.mean(errs))},
+                      "alpha_K_schemes": table}))
+
+
+def run_cnnm(args, local):
+    """CNNM (SVD every iteration) against ICNNM on the same image-completion inputs
+    (200x200, 13x13 kernel, 500 iterations; the comparison of the paper's Kodak table), plus
+    the per-iteration time of CNNM at the video-prediction size (128x128x32, 9x9x5)."""
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    g = np.load(os.path.join(ROOT, "tests", "golden", "image_200x200_k13x13.npz"))
+    w = synth.workload(6, n_ref=0)
+    kd = w["kdims"]
+    it = int(g["iters"])
+    stream = torch.cuda.current_stream(dev)
+    ctx = icnnm.Context(local, stream=stream.cuda_stream)
+    Md, Kd = torch.from_numpy(w["M"]).to(dev), torch.from_numpy(w["mask"]).to(dev)
+    Vd = torch.from_numpy(np.ascontiguousarray(g["V"])).to(dev)
+    Ld = torch.zeros_like(Md)
+    res = {}
+    runs = (("icnnm_bf16", lambda: ctx.icnnm_solve(Md, Kd, Vd, kd, L_out=Ld, max_iters=it, prec="bf16"), 10),
+            ("icnnm_fp32", lambda: ctx.icnnm_solve(Md, Kd, Vd, kd, L_out=Ld, max_iters=it, prec="fp32"), 3),
+            ("cnnm_fp32", lambda: ctx.icnnm_cnnm_solve(Md, Kd, kd, L_out=Ld, max_iters=it), 1))
+    for name, f, steps in runs:
+        f()
+        sec = _timed(stream, f, steps)
+        L = Ld.cpu().numpy().astype(np.float64)
+        res[name] = {"solves_per_s": steps / sec, "ms_per_solve": 1e3 * sec / steps,
+                     "ms_per_iter": 1e3 * sec / steps / it,
+                     "rel_err_vs_target": float(np.linalg.norm(L - w["L0"]) / np.linalg.norm(w["L0"]))}
+    # CNNM per iteration at the video-prediction size (a few iterations)
+    wp = synth.workload(2, n_ref=0)
+    Mp, Kp = torch.from_numpy(wp["M"]).to(dev), torch.from_numpy(wp["mask"]).to(dev)
+    Lp = torch.zeros_like(Mp)
+    itp = 10
+    fp = lambda: ctx.icnnm_cnnm_solve(Mp, Kp, wp["kdims"], L_out=Lp, max_iters=itp)
+    fp()
+    secp = _timed(stream, fp, 1)
+    ctx.close()
+    c, b = res["cnnm_fp32"], res["icnnm_bf16"]
+    print(json.dumps({"metric": "CNNM vs ICNNM solve time on the same inputs", "workload": "image_200x200_k13x13",
+                      "value": c["ms_per_solve"] / b["ms_per_solve"], "unit": "x (CNNM time / ICNNM BF16 time)",
+                      "higher_is_better": True, "data": "synthetic", "iters": it, **res,
+                      "cnnm_over_icnnm_fp32": c["ms_per_solve"] / res["icnnm_fp32"]["ms_per_solve"],
+                      "cnnm_prediction_128x128x32_k9x9x5": {"iters": itp, "ms_per_iter": 1e3 * secp / itp},
+                      "paper_kodak_13x13_s": {"cnnm": 18.643, "icnnm": 11.189}}))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -588,6 +698,10 @@ def main():
         run_batch(args, local)
     elif args.workload == "serving":
         run_serving(args, local)
+    elif args.workload == "image":
+        run_image(args, local)
+    elif args.workload == "cnnm":
+        run_cnnm(args, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -152,6 +152,26 @@ icnnm_status icnnm_solve_batch(icnnm_ctx* ctx, int32_t n, const icnnm_shape* sha
                                float* const* L_out, icnnm_stats* stats);
 
 /*
+ * CNNM, the method ICNNM is compared with (Eq. cnnm; Sec. II-C; Tables II and IV):
+ *     min_L ||A_k(L)||_*  s.t. P_Omega(L) = P_Omega(M),
+ * by the same ADMM iteration with the Z-update done by singular-value thresholding of
+ * A_k(L) - Y/theta at 1/theta, i.e. an SVD of an m x k matrix every iteration. On the
+ * GPU the SVD goes through the k x k Gram of that matrix (FP64 sums of exact products)
+ * and the FP64 Jacobi eigensolver, warm-started from the previous iteration's singular
+ * vectors; everything else is plain FP32. theta0 <= 0 selects 1/||A_k(P_Omega M)||_2.
+ *   shape, M, mask, L_out : as for icnnm_solve (no V)
+ *   params : NULL for the defaults; lambda must be INFINITY, tol 0 (runs exactly
+ *            max_iters iterations) and prec ICNNM_FP32, else EUNSUPPORTED
+ *   stats  : iters, objective = ||A_k(L)||_* of the result, theta = final penalty,
+ *            seconds; residual is 0 (not computed). May be NULL.
+ * EINVAL as for icnnm_solve; ENOMEM if the state (two k x m FP32 arrays plus O(m + k^2))
+ * exceeds the budget; ETIMEOUT if a bounded grid barrier of the eigensolver expired.
+ */
+icnnm_status icnnm_cnnm_solve(icnnm_ctx* ctx, const icnnm_shape* shape, const float* M,
+                              const uint8_t* mask, const icnnm_params* params, float* L_out,
+                              icnnm_stats* stats);
+
+/*
  * Relative convolution diagnostics of a tensor L0 with respect to V (Sec. III-A,
  * Definition 2, Eqs. rkL0 and alphaK; the coherence of Eq. coherence):
  *   sigma_i = ||L0 * kappa_i||_F = ||A_k(L0) v_i||_2   (relative convolution eigenvalues)

@@ -1062,6 +1062,70 @@ icnnm_status icnnm_spectral_diagnostics(icnnm_ctx* c, const icnnm_shape* shape, 
   }
 }
 
+icnnm_status icnnm_cnnm_solve(icnnm_ctx* c, const icnnm_shape* shape, const float* M, const uint8_t* mask,
+                              const icnnm_params* params, float* L_out, icnnm_stats* stats) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  std::vector<void*> tmp;
+  try {
+    CK(cudaSetDevice(c->device));
+    int H, W, T, k1, k2, k3;
+    validate_shape(shape, H, W, T, k1, k2, k3);
+    const icnnm_params p = params ? *params : defaults();
+    validate_params(p);
+    if (!M || !mask || !L_out) fail(ICNNM_EINVAL, "M, mask and L_out must not be NULL");
+    if (!isinf(p.lambda)) fail(ICNNM_EUNSUPPORTED, "CNNM: only lambda = INFINITY (the exact projection)");
+    if (p.tol != 0) fail(ICNNM_EUNSUPPORTED, "CNNM: fixed iteration counts only (tol = 0)");
+    if (p.prec != ICNNM_FP32) fail(ICNNM_EUNSUPPORTED, "CNNM: FP32 only");
+    if (learn_smem_bytes(k1, k2, k3) > 220 * 1024 ||
+        (long long)(2 * k1 - 1) * (2 * k2 - 1) * (2 * k3 - 1) > learn_max_lags())
+      fail(ICNNM_EUNSUPPORTED, "kernel too large");
+    const long long m = (long long)H * W * T;
+    if (cnnm_state_bytes(H, W, T, k1, k2, k3) + c->used > c->budget)
+      fail(ICNNM_ENOMEM, "CNNM state exceeds the HBM budget");
+    auto dalloc = [&](size_t bytes) {
+      void* q;
+      CK(cudaMalloc(&q, bytes));
+      tmp.push_back(q);
+      return q;
+    };
+    float* dM = (float*)dalloc(m * 4);
+    uint8_t* dK = (uint8_t*)dalloc(m);
+    float* dL = (float*)dalloc(m * 4);
+    CK(cudaMemcpyAsync(dM, M, m * 4, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(dK, mask, m, cudaMemcpyDefault, c->stream));
+    int* d2 = (int*)dalloc(8);
+    CK(cudaMemsetAsync(d2, 0, 8, c->stream));
+    CK(check_observed(dM, dK, m, d2, c->stream));
+    int h2[2];
+    CK(cudaMemcpyAsync(h2, d2, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h2[1]) fail(ICNNM_EINVAL, "mask entries must be 0/1 and M must be finite on Omega");
+    if (h2[0] == 0) fail(ICNNM_EINVAL, "Omega is empty");
+    CnnmProblem P{H, W, T, k1, k2, k3, dM, dK, dL, p.max_iters, p.theta0, p.rho, p.theta_max, false};
+    CnnmResult r{};
+    CK(cnnm_run(P, c->stream, &r));
+    if (r.timed_out) fail(ICNNM_ETIMEOUT, "a bounded grid barrier of the eigensolver expired");
+    CK(cudaMemcpyAsync(L_out, dL, m * 4, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (stats) {
+      stats->iters = p.max_iters;
+      stats->residual = 0.0;
+      stats->objective = r.objective;
+      stats->theta = r.theta;
+      stats->seconds = r.seconds;
+    }
+    for (void* q : tmp) cudaFree(q);
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    for (void* q : tmp) cudaFree(q);
+    return report(c, f);
+  } catch (CudaFail& f) {
+    for (void* q : tmp) cudaFree(q);
+    return report(c, f);
+  }
+}
+
 icnnm_status icnnm_solve_batch(icnnm_ctx* c, int32_t n, const icnnm_shape* shapes, const float* const* M,
                                const uint8_t* const* mask, const double* V, const icnnm_params* params,
                                float* const* L_out, icnnm_stats* stats) {

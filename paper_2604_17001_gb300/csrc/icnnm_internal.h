@@ -165,7 +165,26 @@ cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVo
 size_t learn_eig_grid_scratch(int dev);
 cudaError_t learn_eig_grid(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo, void* scratch,
                            cudaStream_t st);
+// P = V^T G V (dT: k*k scratch); column j of V is V[j*k ...].
+cudaError_t diag_spectral_products(const double* dG, const double* dV, int k, double* dT, double* dP, cudaStream_t st);
 cudaError_t check_finite(const float* x, long long n, int* dbad, cudaStream_t st);
+
+// k_cnnm.cu: the CNNM baseline (Eq. cnnm) solved with SVT through the Gram of B.
+struct CnnmProblem {
+  int H, W, T, k1, k2, k3;
+  const float* dM;          // device, m
+  const uint8_t* dmask;     // device, m
+  float* dL;                // device output, m
+  int iters;
+  double theta0, rho, theta_max;   // theta0 <= 0: 1/||A_k(P_Omega M)||_2
+  bool count_sweeps;        // synchronise each iteration to count Jacobi sweeps
+};
+struct CnnmResult {
+  double seconds, theta, objective;   // device time; final penalty; ||A_k(L)||_*
+  int timed_out, sweeps;
+};
+size_t cnnm_state_bytes(int H, int W, int T, int k1, int k2, int k3);
+cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res);
 cudaError_t learn_gram_streamed(int b, const float* const* dptrs, const int* ddims, int k1, int k2, int k3,
                                 double* dpart, int nblk, double* dlagsum, double* dgram, cudaStream_t st);
 cudaError_t check_observed(const float* M, const uint8_t* mask, long long n, int* dcount_bad,

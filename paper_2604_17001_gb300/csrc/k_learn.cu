@@ -599,6 +599,13 @@ cudaError_t diag_spectral(const double* dG, const double* dV, int k, double tol,
   return cudaGetLastError();
 }
 
+cudaError_t diag_spectral_products(const double* dG, const double* dV, int k, double* dT, double* dP, cudaStream_t st) {
+  const unsigned nb = (unsigned)(((long long)k * k + 255) / 256);
+  gv_kernel<<<nb, 256, 0, st>>>(dG, dV, k, dT);
+  vt_kernel<<<nb, 256, 0, st>>>(dV, dT, k, dP);
+  return cudaGetLastError();
+}
+
 cudaError_t check_finite(const float* x, long long n, int* dbad, cudaStream_t st) {
   finite_check_kernel<<<256, 256, 0, st>>>(x, n, dbad);
   return cudaGetLastError();

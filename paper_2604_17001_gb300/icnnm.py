@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
         "icnnm_cancel": ([P, U64], I32),
         "icnnm_profile_enable": ([P, I32], I32),
         "icnnm_profile_read": ([P, I32, C.POINTER(D), C.POINTER(I64)], I32),
+        "icnnm_cnnm_solve": ([P, C.POINTER(icnnm_shape), P, P, C.POINTER(icnnm_params), P,
+                              C.POINTER(icnnm_stats)], I32),
         "icnnm_spectral_diagnostics": ([P, C.POINTER(icnnm_shape), P, P, D, P, C.POINTER(I32), C.POINTER(D),
                                         C.POINTER(D)], I32),
         "icnnm_learn_V_noalloc": ([C.POINTER(I64), I32, C.POINTER(icnnm_shape), C.POINTER(P), P, P, P], I32),
@@ -203,6 +205,22 @@ class Context:
         if own:
             return V_out.T.copy(), eig_out
         return V_out, eig_out
+
+    def icnnm_cnnm_solve(self, M, mask, kdims, dims=None, L_out=None, **kw):
+        """CNNM (no V): M (float32) and mask (uint8) as for icnnm_solve; FP32, fixed
+        iteration count. Returns (L, stats dict)."""
+        shp = tuple(M.shape)
+        if dims is None:
+            dims = (shp[1], shp[2], shp[0]) if len(shp) == 3 else (shp[0], shp[1])
+        s = make_shape(dims, kdims)
+        kw.setdefault("prec", "fp32")
+        p = params(**kw)
+        if L_out is None:
+            L_out = np.zeros(shp, dtype=np.float32) if isinstance(M, np.ndarray) else M.new_zeros(shp)
+        st = icnnm_stats()
+        self._check(self.lib.icnnm_cnnm_solve(self.h, C.byref(s), _ptr(M), _ptr(mask), C.byref(p), _ptr(L_out),
+                                              C.byref(st)))
+        return L_out, st.as_dict()
 
     def icnnm_spectral_diagnostics(self, L0, V, kdims, rank_tol=1e-6, dims=None):
         """Relative convolution eigenvalues sigma (in V's column order), r_K, alpha_K and
