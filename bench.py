@@ -575,6 +575,12 @@ def run_serving(args, local):
                        "mean_iters": float(np.mean(iters32)), "mode": "one at a time, FCFS on the same arrivals"}}))
 
 
+# sigma_i below 1e-4 sigma_max count as zero in the Table I analog: learn_V's Gram (FP32
+# products) leaves the eigenvectors of the smallest eigenvalues too inexact to resolve
+# those directions, which would otherwise lift the G.T. scheme's alpha_K above 1.
+RANK_TOL_TABLE1 = 1e-4
+
+
 def run_image(args, local):
     """Image completion (Sec. V-A shape): 200x200 images, 13x13 kernel, 4x4-pixel blocks
     missing at 50%, 500 iterations, V from 7 reference images. BF16 and FP32 solves/s of
@@ -625,7 +631,7 @@ def run_image(args, local):
     for name, V in schemes.items():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dg = ctx.icnnm_spectral_diagnostics(L0d, V, kd, rank_tol=1e-6)
+        dg = ctx.icnnm_spectral_diagnostics(L0d, V, kd, rank_tol=RANK_TOL_TABLE1)
         torch.cuda.synchronize()
         table[name] = {"alpha_K": dg["alpha_K"], "r_K": dg["r_K"], "mu_K": dg["mu_K"],
                        "ms": 1e3 * (time.perf_counter() - t0)}
@@ -636,7 +642,7 @@ def run_image(args, local):
                       "batch24_bf16": {"images_per_s": len(jobs) * args.steps / secb,
                                        "ms_per_batch": 1e3 * secb / args.steps,
                                        "mean_rel_err_vs_target": float(np.mean(errs))},
-                      "alpha_K_schemes": table}))
+                      "alpha_K_schemes": table, "alpha_K_rank_tol": RANK_TOL_TABLE1}))
 
 
 def run_cnnm(args, local):

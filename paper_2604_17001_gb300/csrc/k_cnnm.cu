@@ -265,7 +265,7 @@ __global__ void cnnm_gather_kernel(CnnmDev d, float inv_kth) {
         const int s0 = (st * d.k1 + sh) * d.k2;
         for (int sw = 0; sw < d.k2; ++sw) {
           const int ww = w + sw >= d.W ? w + sw - d.W : w + sw;
-          acc += d.WT[(long long)(s0 + sw) * d.m + rb + ww];
+          acc += d.WTn[(long long)(s0 + sw) * d.m + rb + ww];
         }
       }
     }

@@ -7,8 +7,8 @@ alpha_K^2 = lambda_max(D V^T G V D); the oracle takes column norms and the opera
 norm of the explicit A_k(L0) V D. Squaring makes a sigma that is zero in exact
 arithmetic come out near sqrt(k eps) sigma_max on the GPU, so the sigma bar is
 1e-7 sigma_max absolute; alpha_K agrees to 1e-7 relative while every sigma in the
-support is well above the rank threshold (checked); r_K is compared only where no
-sigma lies within a factor 100 of the threshold, so that both sides decide alike."""
+support is well above the rank threshold; r_K is compared only where no sigma lies
+within 10x the sigma bar of the threshold, so that both sides decide alike."""
 import numpy as np
 import pytest
 
@@ -41,7 +41,8 @@ def compare(ctx, L0, V, kd, tol=1e-6):
     smax = so.max()
     assert np.max(np.abs(g["sigma"] - so)) <= 1e-7 * smax
     thr = tol * max(1.0, smax)
-    assert not np.any((so > thr / 100) & (so < thr * 100)), "a sigma too close to the rank threshold"
+    # both sides decide alike when no sigma lies within 10x the sigma bar of the threshold
+    assert not np.any(np.abs(so - thr) <= 10 * 1e-7 * smax), "a sigma too close to the rank threshold"
     assert g["r_K"] == O.relative_rank(L, V, kd, tol)
     ao = O.spectral_correlation(L, V, kd, tol)
     assert abs(g["alpha_K"] - ao) <= 1e-7 * ao
@@ -75,7 +76,9 @@ def test_ground_truth_K_rank_deficient(ctx):
     kd = (6, 5, 1)
     P = plane_wave(48, 40, 3, 2)
     V, _ = O.learn_V([P], kd)
-    g, _ = compare(ctx, P, V, kd, tol=1e-6)
+    # the null directions come out near 1e-6 sigma_max (the FP32 rounding of P), so the
+    # rank threshold sits well above them
+    g, _ = compare(ctx, P, V, kd, tol=1e-5)
     assert g["r_K"] == 3
     assert g["alpha_K"] == pytest.approx(1.0, abs=1e-9)
 

@@ -252,11 +252,15 @@ def test_bf16_tolerance_finishes_in_fp32(ctx, serve):
 
 
 def test_bf16_tolerance_batch_mixed_phases(ctx):
-    # Jobs of one batch reach the FP32 finish at different checks, so BF16 and FP32
-    # lists step side by side; each job still stops on an exact residual <= tol and agrees
-    # with the oracle under the same rule.
+    # Jobs of one batch reach the FP32 finish at different checks, so BF16 and FP32 lists
+    # step side by side. Each job stops on an exact residual <= tol, near the oracle's
+    # stopping iteration, and equals the same job solved alone (to the BF16 bar). (The
+    # oracle's values are compared in the single-job test above: on small, sparsely
+    # observed jobs that run for hundreds of iterations the BF16 phase drifts past 1e-3
+    # from FP64, batched or not.) The residual is checked every iteration, so that the
+    # stopping points of the batch and of the single solves are at most an iteration apart.
     kd = (5, 5, 3)
-    kw = dict(max_iters=1000, tol=1e-3, check_every=10)
+    kw = dict(max_iters=1000, tol=1e-3, check_every=1)
     probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 24, 8), 0.5, 41), ((16, 40, 6), 0.3, 42),
                                                          ((24, 24, 5), 0.7, 43)]]
     V = probs[0][2]
@@ -266,5 +270,6 @@ def test_bf16_tolerance_batch_mixed_phases(ctx):
         _, so = O.icnnm_solve(M, mask, V, kd, **kw)
         assert abs(st["iters"] - so["iters"]) <= 30
         assert np.array_equal(L[mask.astype(bool)], M[mask.astype(bool)])
-        Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=st["iters"])
-        assert rel(L, Lo) <= TOL["bf16"]
+        Ls, sts = ctx.icnnm_solve(M, mask, V, kd, prec="bf16", **kw)
+        assert abs(st["iters"] - sts["iters"]) <= 1
+        assert rel(L, Ls) <= TOL["bf16"]
