@@ -295,7 +295,8 @@ size_t cnnm_state_bytes(int H, int W, int T, int k1, int k2, int k3) {
 }
 
 // The whole CNNM solve on one stream. dM, dmask: device inputs; dL: device output (m).
-// eig(C) uses the one-block Jacobi for k <= 128 and the grid-wide one above.
+// eig(C) uses the grid-wide Jacobi (measured several times faster than the one-block
+// version per round, also at k = 75).
 cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res) {
   const int k = P.k1 * P.k2 * P.k3;
   const long long m = (long long)P.H * P.W * P.T;
@@ -342,7 +343,7 @@ cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res) {
   if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, 2 * sizeof(int), st);
   auto eig = [&](double* A, double* Vacc, double* Vout) {
     if (e != cudaSuccess) return;
-    e = k <= 128 ? learn_eig(A, Vacc, k, evals, Vout, info, st) : learn_eig_grid(A, Vacc, k, evals, Vout, info, scr, st);
+    e = learn_eig_grid(A, Vacc, k, evals, Vout, info, scr, st);
   };
   // Nuclear norm / spectral norm of A_k(X) from the exact Gram of X (FP64 autocorrelations).
   auto gram_eigs = [&](const float* X) {

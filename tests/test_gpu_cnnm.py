@@ -30,7 +30,7 @@ CASES = [
     ((20, 16, 1), (5, 4, 1), dict(frac=0.6), 150),       # image, ragged tiles
     ((16, 16, 6), (5, 5, 3), dict(frac=0.5), 60),        # k = 75
     ((16, 12, 6), (3, 3, 2), dict(last=2), 80),          # prediction mask
-    ((24, 20, 3), (7, 7, 3), dict(frac=0.5), 40),        # k = 147: grid-wide eigensolver
+    ((24, 20, 3), (7, 7, 3), dict(frac=0.5), 40),        # k = 147
 ]
 
 
