@@ -137,7 +137,9 @@ struct icnnm_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t budget = 0;
-  size_t used = 0;
+  // device bytes of job state in use: charged and released under mu; the serving thread's
+  // admission test also reads it under qmu (advisory; alloc_job checks again under mu)
+  std::atomic<size_t> used{0};
   std::recursive_mutex mu;         // serialises device work of API calls and the server
   std::mutex err_mu;
   std::string last_err;
