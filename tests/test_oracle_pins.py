@@ -319,6 +319,26 @@ def test_icnnm_with_cnnm_eigvectors_reaches_cnnm_value():
     assert np.array_equal(Lc[mask.astype(bool)], M[mask.astype(bool)])
 
 
+def test_cnnm_feasible_objective_and_low_rank_recovery():
+    # Eq. (cnnm): L0 is feasible, so the minimiser's ||A_k(L)||_* is at most L0's; the
+    # observed entries are kept; a convolutionally low-rank target (a whole-period plane
+    # wave: convolution rank 3) is recovered from most of its entries (the exact-recovery
+    # property CNNM is built on, Sec. I).
+    nuc = lambda X, kd: np.linalg.svd(O.conv_matrix(X, kd), compute_uv=False).sum()
+    L0 = synth.video(8, 8, 3, seed=41).astype(np.float64)
+    mask = synth.mask_uniform(8, 8, 3, 0.6, seed=42)
+    M = np.where(mask.astype(bool), L0, 0.0)
+    kd = (3, 3, 2)
+    L = O.cnnm_solve(M, mask, kd, max_iters=300)
+    assert np.array_equal(L[mask.astype(bool)], M[mask.astype(bool)])
+    assert nuc(L, kd) <= nuc(L0, kd) * (1 + 1e-4)
+    hh, ww = np.meshgrid(np.arange(12), np.arange(12), indexing="ij")
+    P = (0.5 + 0.4 * np.cos(2 * np.pi * (hh + 2 * ww) / 12.0)).reshape(1, 12, 12)
+    pm = synth.mask_uniform(12, 12, 1, 0.85, seed=77)
+    Lp = O.cnnm_solve(np.where(pm.astype(bool), P, 0.0), pm, (4, 4, 1), max_iters=400)
+    assert np.linalg.norm(Lp - P) / np.linalg.norm(P) < 1e-4
+
+
 # -------------------------------------------------------------------------------
 # Planted mistakes: a plausible bug in the oracle must make a pin above fail.
 # -------------------------------------------------------------------------------
