@@ -61,3 +61,19 @@ def test_cnnm_rejects_what_it_does_not_implement(ctx):
             ctx.icnnm_cnnm_solve(M, mask, (3, 3, 2), max_iters=5, **kw)
     with pytest.raises(icnnm.ICNNMError):
         ctx.icnnm_cnnm_solve(M, np.zeros_like(mask), (3, 3, 2), max_iters=5)
+
+
+def test_cnnm_image_full_size(ctx):
+    # the image-completion inputs (200x200, 13x13 kernel, k = 169) against the stored
+    # oracle CNNM run (tests/golden/make_cnnm_image_reference.py)
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "cnnm_image_200x200_k13x13.npz")
+    if not os.path.exists(path):
+        pytest.skip("stored oracle run not present")
+    g = np.load(path)
+    w = synth.workload(6, n_ref=0)
+    L, st = ctx.icnnm_cnnm_solve(w["M"], w["mask"], w["kdims"], max_iters=int(g["iters"]))
+    msk = w["mask"].astype(bool)
+    assert np.array_equal(L[msk], w["M"][msk])
+    assert rel(L, g["L"]) <= 1e-5, rel(L, g["L"])
+    assert st["objective"] == pytest.approx(float(g["nuclear_norm"]), rel=1e-5)
