@@ -273,3 +273,22 @@ def test_bf16_tolerance_batch_mixed_phases(ctx):
         Ls, sts = ctx.icnnm_solve(M, mask, V, kd, prec="bf16", **kw)
         assert abs(st["iters"] - sts["iters"]) <= 1
         assert rel(L, Ls) <= TOL["bf16"]
+
+
+def test_bf16_batch_with_long_mixed_phase(ctx):
+    # An easy job (90% observed) reaches the FP32 finish long before a hard one (35%
+    # observed) leaves BF16, so the blocking batch steps a BF16 list and an FP32 list side
+    # by side for many iterations (each with its own device job table). Every job must end
+    # as it does alone.
+    kd = (5, 5, 3)
+    kw = dict(max_iters=1000, tol=1e-3, check_every=1)
+    probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 24, 8), 0.9, 51), ((24, 40, 6), 0.35, 52)]]
+    V = probs[0][2]
+    outs, stats = ctx.icnnm_solve_batch([p[0] for p in probs], [p[1] for p in probs], V, kd, prec="bf16", **kw)
+    assert stats[1]["iters"] > stats[0]["iters"] + 20
+    for (M, mask, _, _), L, st in zip(probs, outs, stats):
+        assert st["residual"] <= 1e-3
+        assert np.array_equal(L[mask.astype(bool)], M[mask.astype(bool)])
+        Ls, sts = ctx.icnnm_solve(M, mask, V, kd, prec="bf16", **kw)
+        assert abs(st["iters"] - sts["iters"]) <= 1
+        assert rel(L, Ls) <= TOL["bf16"]
