@@ -276,19 +276,27 @@ def test_bf16_tolerance_batch_mixed_phases(ctx):
 
 
 def test_bf16_batch_with_long_mixed_phase(ctx):
-    # An easy job (90% observed) reaches the FP32 finish long before a hard one (35%
-    # observed) leaves BF16, so the blocking batch steps a BF16 list and an FP32 list side
-    # by side for many iterations (each with its own device job table). Every job must end
-    # as it does alone.
+    # Two jobs whose BF16 phases end far apart (the FP64 oracle under the same rule stops
+    # them after 32 and 71 iterations): the first finishes in FP32 while the second is
+    # still in BF16, so the blocking batch steps a BF16 list and an FP32 list side by side
+    # (each with its own device job table). Every job must end as it does alone.
     kd = (5, 5, 3)
-    kw = dict(max_iters=1000, tol=1e-3, check_every=1)
-    probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 24, 8), 0.9, 51), ((24, 40, 6), 0.35, 52)]]
-    V = probs[0][2]
-    outs, stats = ctx.icnnm_solve_batch([p[0] for p in probs], [p[1] for p in probs], V, kd, prec="bf16", **kw)
+    kw = dict(max_iters=1000, tol=1e-4, check_every=1)
+    V, _ = O.learn_V([synth.video(32, 24, 8, seed=61 + j) for j in range(3)], kd)
+    jobs = []
+    for (H, W, T), mk in (((24, 24, 8), lambda: synth.mask_uniform(24, 24, 8, 0.2, seed=61)),
+                          ((32, 32, 16), lambda: synth.mask_last_frames(32, 32, 16, 6))):
+        L0 = synth.video(H, W, T, seed=60)
+        mask = mk()
+        jobs.append((np.where(mask.astype(bool), L0, 0).astype(np.float32), mask))
+    outs, stats = ctx.icnnm_solve_batch([j[0] for j in jobs], [j[1] for j in jobs], V, kd, prec="bf16", **kw)
     assert stats[1]["iters"] > stats[0]["iters"] + 20
-    for (M, mask, _, _), L, st in zip(probs, outs, stats):
-        assert st["residual"] <= 1e-3
+    for (M, mask), L, st in zip(jobs, outs, stats):
+        assert st["residual"] <= 1e-4
         assert np.array_equal(L[mask.astype(bool)], M[mask.astype(bool)])
         Ls, sts = ctx.icnnm_solve(M, mask, V, kd, prec="bf16", **kw)
-        assert abs(st["iters"] - sts["iters"]) <= 1
-        assert rel(L, Ls) <= TOL["bf16"]
+        # batch and single solve differ only in the order of FP32 additions of the col2im
+        # (measured 2e-8 apart here); stepping the BF16 list with the FP32 list's job
+        # table once put them 1.4e-4 apart and one iteration off
+        assert st["iters"] == sts["iters"]
+        assert rel(L, Ls) <= 1e-5
