@@ -179,9 +179,9 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* ctx, const icnnm_shape* shape, const fl
  *             the nonzero sigma_i; rank_tol is the numerical reading of "nonzero")
  *   alpha_K = ||A_k(L0) V D|| (operator norm), D_ii = 1/sigma_i on I, 0 elsewhere
  *   mu_K    = mu_1(V_I), V_I the columns of V on I: (k / r_K) max_s sum_{i in I} V[i*k+s]^2
- * Computed on the GPU through G = A_k(L0)^T A_k(L0) (circular autocorrelations, FP64
- * products and sums): sigma_i^2 = v_i^T G v_i, and alpha_K^2 is the largest eigenvalue of
- * D V^T G V D (FP64 Jacobi). Squaring limits the resolution: a sigma_i that is zero
+ * Computed on the GPU through G = A_k(L0)^T A_k(L0) (circular autocorrelations of exact
+ * products, summed to ~2^-48 relative): sigma_i^2 = v_i^T G v_i, and alpha_K^2 is the
+ * largest eigenvalue of D V^T G V D (FP64 Jacobi). Squaring limits the resolution: a sigma_i that is zero
  * in exact arithmetic comes out near sqrt(k * 1e-16) * max sigma, so rank_tol should be
  * at least 1e-6.
  *   shape    : dims and kdims of L0

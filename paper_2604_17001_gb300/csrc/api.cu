@@ -62,6 +62,7 @@ struct VData {
   int k1, k2, k3, k, kc;
   std::vector<double> V64;   // column-major k x k
   float* dVf = nullptr;      // [k][kc]
+  double* dV64 = nullptr;    // V64 on the device (column norms through the Gram)
   TcVData tc;                // BF16 images (tc_api.h)
   bool tc_ready = false;
 };
@@ -166,6 +167,9 @@ struct icnnm_ctx {
   JobDev* dlist[2] = {nullptr, nullptr};
   int* dtile0[2] = {nullptr, nullptr};
   int list_cap[2] = {0, 0};
+  // scratch of the Gram route to column norms (autocorrelation partials, k x k Gram)
+  double* gscr = nullptr;
+  size_t gscr_bytes = 0;
 };
 
 namespace {
@@ -295,6 +299,8 @@ VData* get_vdata(icnnm_ctx* c, const double* V, int k1, int k2, int k3, int prec
       for (int ch = 0; ch < k; ++ch) vf[(size_t)s * nv->kc + ch] = (float)nv->V64[(size_t)ch * k + s];
     CK(cudaMalloc(&nv->dVf, vf.size() * 4));
     CK(cudaMemcpy(nv->dVf, vf.data(), vf.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&nv->dV64, nv->V64.size() * 8));
+    CK(cudaMemcpy(nv->dV64, nv->V64.data(), nv->V64.size() * 8, cudaMemcpyHostToDevice));
     vd = nv.get();
     c->vcache[key] = std::move(nv);
   } else {
@@ -463,6 +469,36 @@ int fwd_slots(const Shared& sh, int prec, const TcVData* tcv) {
   return prec == ICNNM_BF16 ? tc_fwd_slots(sh, *tcv) : 0;
 }
 
+// Column norms ||A_k(L) v_c||^2 of each job's current L into its colseg through the
+// Gram A_k(L)^T A_k(L) (autocorrelations of exact products, then v_c^T G v_c in FP64):
+// FP64-accurate and far cheaper than the FP32 m x k x k forward pass it replaces for
+// theta0 and the objective. Returns false (nothing launched) where the autocorrelation
+// kernel's limits do not admit the kernel size.
+bool gram_colnorms(icnnm_ctx* c, const std::vector<Job*>& js) {
+  const VData* vd = js[0]->vd;
+  const int k1 = vd->k1, k2 = vd->k2, k3 = vd->k3, k = vd->k;
+  const long long nlag = (long long)(2 * k1 - 1) * (2 * k2 - 1) * (2 * k3 - 1);
+  if (nlag > learn_max_lags() || learn_smem_bytes(k1, k2, k3) > 220 * 1024) return false;
+  int sms = 1;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  const int nblk = 2 * sms;
+  const size_t need = sizeof(double) * ((size_t)nblk * nlag + (size_t)k * k);
+  if (need > c->gscr_bytes) {
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->gscr) cudaFree(c->gscr);
+    c->gscr = nullptr;
+    c->gscr_bytes = 0;
+    CK(cudaMalloc(&c->gscr, need));
+    c->gscr_bytes = need;
+  }
+  double* part = c->gscr;
+  double* G = part + (size_t)nblk * nlag;
+  PassScope ps(c, 3, 3 * (int)js.size());
+  for (const Job* j : js)
+    CK(gram_colsq(j->dev.L, j->H, j->W, j->T, k1, k2, k3, vd->dV64, vd->kc, part, nblk, G, j->dev.colseg, c->stream));
+  return true;
+}
+
 #define OTHER(n, expr)            \
   do {                            \
     PassScope ps__(c, 3, (n));    \
@@ -476,8 +512,10 @@ void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
   const TcVData* tcv = &js[0]->vd->tc;
   Shared sh = upload_list(c, js);
   OTHER(1, launch_init_L(sh, c->stream));
-  run_fwd(c, sh, ICNNM_FP32, 0, tcv);
-  OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
+  if (!gram_colnorms(c, js)) {
+    run_fwd(c, sh, ICNNM_FP32, 0, tcv);
+    OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
+  }
   OTHER(1, launch_theta0(sh, js[0]->p.theta0, c->stream));
   OTHER(1, launch_scale_X(sh, c->stream));
   if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
@@ -509,13 +547,16 @@ void engine_step(icnnm_ctx* c, const Shared& sh, int prec, const TcVData* tcv, b
   OTHER(1, launch_reduce_cols(sh, 1, fwd_slots(sh, prec, tcv), c->stream));
 }
 
-// ||A_k(L)V||_{2,1} of the returned L, from the FP32 forward pass for every job: the l2,1
-// norm sums k column norms, most of them small for smooth data, and BF16 rounding of L
-// lifts each small one in quadrature (measured: +1.5% on the video-prediction workload).
+// ||A_k(L)V||_{2,1} of the returned L, in FP64-accurate arithmetic for every job (not from
+// the BF16 forward pass: the l2,1 norm sums k column norms, most of them small for smooth
+// data, and BF16 rounding of L lifts each small one in quadrature, +1.5% measured on the
+// video-prediction workload).
 void engine_objective(icnnm_ctx* c, const std::vector<Job*>& js) {
   const Shared sh = upload_list(c, js);
-  run_fwd(c, sh, ICNNM_FP32, 4, nullptr);
-  OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
+  if (!gram_colnorms(c, js)) {
+    run_fwd(c, sh, ICNNM_FP32, 4, nullptr);
+    OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
+  }
   OTHER(1, launch_finish(sh, 2, c->stream));
 }
 
@@ -892,12 +933,14 @@ void icnnm_destroy(icnnm_ctx* c) {
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (auto& kv : c->vcache) {
     if (kv.second->dVf) cudaFree(kv.second->dVf);
+    if (kv.second->dV64) cudaFree(kv.second->dV64);
     if (kv.second->tc_ready) tc_free_vdata(&kv.second->tc);
   }
   for (int sl = 0; sl < 2; ++sl) {
     if (c->dlist[sl]) cudaFree(c->dlist[sl]);
     if (c->dtile0[sl]) cudaFree(c->dtile0[sl]);
   }
+  if (c->gscr) cudaFree(c->gscr);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -147,8 +147,8 @@ cudaError_t launch_adj_gemm_fp32(const Shared& sh, cudaStream_t st);
 int fwd_fp32_nrp(int k);
 
 // k_learn.cu
-// exact: FP64 products and sums (diagnostics); otherwise FP32 products summed over 64
-// voxels, then in FP64.
+// exact: exact products summed to ~2^-48 relative (diagnostics, column norms); otherwise
+// FP32 products summed over 64 voxels, then in FP64.
 cudaError_t learn_gram(int b, const float* const* dL, const int* ddims, int k1, int k2, int k3,
                        double* dpart, int nblk, double* dgram, cudaStream_t st, bool exact = false);
 // P = V^T G V (dT: k*k scratch), sigma_i = sqrt(P_ii), the support I (sigma_i > tol *
@@ -165,6 +165,11 @@ cudaError_t learn_eig(double* dA, double* dV, int k, double* devals, double* dVo
 size_t learn_eig_grid_scratch(int dev);
 cudaError_t learn_eig_grid(double* dA, double* dV, int k, double* devals, double* dVout, int* dinfo, void* scratch,
                            cudaStream_t st);
+// Column norms ||A_k(L) v_c||^2 of one tensor through its Gram (autocorrelations of
+// exact products), written into colseg (NSEG x kc: segment 0, the others zero). dpart:
+// nblk * (2k1-1)(2k2-1)(2k3-1) doubles, dG: k*k doubles; dV: V column-contiguous (FP64).
+cudaError_t gram_colsq(const float* dL, int H, int W, int T, int k1, int k2, int k3, const double* dV, int kc,
+                       double* dpart, int nblk, double* dG, double* colseg, cudaStream_t st);
 // P = V^T G V (dT: k*k scratch); column j of V is V[j*k ...].
 cudaError_t diag_spectral_products(const double* dG, const double* dV, int k, double* dT, double* dP, cudaStream_t st);
 cudaError_t check_finite(const float* x, long long n, int* dbad, cudaStream_t st);

@@ -345,7 +345,7 @@ cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res) {
     if (e != cudaSuccess) return;
     e = learn_eig_grid(A, Vacc, k, evals, Vout, info, scr, st);
   };
-  // Nuclear norm / spectral norm of A_k(X) from the exact Gram of X (FP64 autocorrelations).
+  // Nuclear norm / spectral norm of A_k(X) from the Gram of X (autocorrelations of exact products).
   auto gram_eigs = [&](const float* X) {
     if (e != cudaSuccess) return;
     const float* xp = X;

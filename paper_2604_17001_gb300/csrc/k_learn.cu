@@ -23,8 +23,10 @@ constexpr int AC_MAXLAG_PER_THREAD = 16;     // supports up to 4096 lags
 
 struct LearnArgs {
   int b;
-  const float* const* L;     // device array of b device pointers
+  const float* const* L;     // device array of b device pointers (NULL: the one tensor L1)
   const int* dims;           // device, 3*b: H, W, T
+  const float* L1;           // b = 1 without device arrays: the tensor and its dims
+  int H1, W1, T1;
   int k1, k2, k3;
   int nl1, nl2, nl3, nlag;   // 2k-1 per dim and their product
   int nblk;                  // blocks per tensor
@@ -32,14 +34,14 @@ struct LearnArgs {
 };
 
 // Lag index l <-> (dt, dh, dw) with dt in [-(k3-1), k3-1] etc, l = ((dt+k3-1)*nl1 + dh+k1-1)*nl2 + dw+k2-1.
-// EXACT: products and sums in FP64 (the product of two floats is exact in FP64), for the
-// diagnostics, whose smallest eigenvalues need the extra range.
+// EXACT: every product kept exactly and summed to about 2^-48 relative (float pairs, see
+// below), for the diagnostics and the column norms, whose smallest entries need it.
 template <bool EXACT>
 __global__ void __launch_bounds__(AC_THREADS) autocorr_kernel(LearnArgs a) {
   extern __shared__ float sL[];
   const int j = blockIdx.x;
-  const int H = a.dims[3 * j], W = a.dims[3 * j + 1], T = a.dims[3 * j + 2];
-  const float* L = a.L[j];
+  const int H = a.L ? a.dims[3 * j] : a.H1, W = a.L ? a.dims[3 * j + 1] : a.W1, T = a.L ? a.dims[3 * j + 2] : a.T1;
+  const float* L = a.L ? a.L[j] : a.L1;
   const int ew = BW + 2 * (a.k2 - 1), eh = BH + 2 * (a.k1 - 1), et = BT + 2 * (a.k3 - 1);
   const int nbw = (W + BW - 1) / BW, nbh = (H + BH - 1) / BH, nbt = (T + BT - 1) / BT;
   const int nbr = nbw * nbh * nbt;
@@ -66,14 +68,26 @@ __global__ void __launch_bounds__(AC_THREADS) autocorr_kernel(LearnArgs a) {
     const int vw = min(BW, W - bw * BW), vh = min(BH, H - bh * BH), vt = min(BT, T - bt * BT);
     for (int q = 0; q < nmy; ++q) {
       if (EXACT) {
-        double part = 0.0;
+        // every product a*b is split exactly into p + e (p = a*b rounded, e = fma(a, b, -p))
+        // and summed over the brick as an unevaluated float pair hi + lo (Knuth's TwoSum
+        // for p, e added to lo): about 2^-48 relative per term, on the FP32 pipe; the pair
+        // goes to FP64 once per brick
+        float hi = 0.f, lo = 0.f;
         for (int z = 0; z < vt; ++z)
           for (int y = 0; y < vh; ++y) {
             const int base = ((z + a.k3 - 1) * eh + (y + a.k1 - 1)) * ew + (a.k2 - 1);
-            for (int x = 0; x < vw; ++x)
-              part = fma((double)sL[base + x], (double)sL[base + x + lagoff[q]], part);
+            for (int x = 0; x < vw; ++x) {
+              const float av = sL[base + x], bv = sL[base + x + lagoff[q]];
+              const float p = __fmul_rn(av, bv);
+              const float e = __fmaf_rn(av, bv, -p);
+              const float s = __fadd_rn(hi, p);
+              const float bb = __fsub_rn(s, hi);
+              const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+              hi = s;
+              lo = __fadd_rn(lo, __fadd_rn(err, e));
+            }
           }
-        acc[q] += part;
+        acc[q] += (double)hi + (double)lo;
         continue;
       }
       float part = 0.f;
@@ -493,6 +507,29 @@ diag_support_kernel(const double* P, const double* V, int k, double tol, double*
   }
 }
 
+// colsq[c] = v_c^T G v_c = ||A_k(L) v_c||^2 (G = A_k(L)^T A_k(L), V[c*k + s] = tap s of
+// column c), written as the first of the NSEG column segments of a job (the others zero)
+// so that the per-job reductions over segments read it like a forward pass's sums. One
+// block per channel c < kc (zero past k); FP64, fixed order.
+__global__ void gram_colsq_kernel(const double* G, const double* V, int k, int kc, double* colseg) {
+  const int c = blockIdx.x;
+  __shared__ double red[256];
+  double q = 0.0;
+  if (c < k)
+    for (int srow = threadIdx.x; srow < k; srow += blockDim.x) {
+      double y = 0.0;
+      for (int u = 0; u < k; ++u) y = fma(G[(long long)srow * k + u], V[(long long)c * k + u], y);
+      q = fma(V[(long long)c * k + srow], y, q);
+    }
+  red[threadIdx.x] = q;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  for (int sg = threadIdx.x; sg < NSEG; sg += blockDim.x) colseg[(long long)sg * kc + c] = (sg == 0) ? red[0] : 0.0;
+}
+
 __global__ void finite_check_kernel(const float* x, long long n, int* bad) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     if (!isfinite(x[i])) { atomicExch(bad, 1); return; }
@@ -596,6 +633,23 @@ cudaError_t diag_spectral(const double* dG, const double* dV, int k, double tol,
   gv_kernel<<<nb, 256, 0, st>>>(dG, dV, k, dT);
   vt_kernel<<<nb, 256, 0, st>>>(dV, dT, k, dP);
   diag_support_kernel<<<1, EIG_THREADS, 0, st>>>(dP, dV, k, tol, dsigma, dS, dout);
+  return cudaGetLastError();
+}
+
+cudaError_t gram_colsq(const float* dL, int H, int W, int T, int k1, int k2, int k3, const double* dV, int kc,
+                       double* dpart, int nblk, double* dG, double* colseg, cudaStream_t st) {
+  LearnArgs a{};
+  a.b = 1; a.L = nullptr; a.dims = nullptr; a.L1 = dL; a.H1 = H; a.W1 = W; a.T1 = T;
+  a.k1 = k1; a.k2 = k2; a.k3 = k3;
+  a.nl1 = 2 * k1 - 1; a.nl2 = 2 * k2 - 1; a.nl3 = 2 * k3 - 1;
+  a.nlag = a.nl1 * a.nl2 * a.nl3;
+  a.nblk = nblk; a.part = dpart;
+  const size_t smem = learn_smem_bytes(k1, k2, k3);
+  cudaFuncSetAttribute(autocorr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  autocorr_kernel<true><<<dim3(1, nblk), AC_THREADS, smem, st>>>(a);
+  const long long kk = (long long)k1 * k2 * k3;
+  gram_kernel<<<(unsigned)((kk * kk + 255) / 256), 256, 0, st>>>(a, dG);
+  gram_colsq_kernel<<<kc, 256, 0, st>>>(dG, dV, (int)kk, kc, colseg);
   return cudaGetLastError();
 }
 
