@@ -7,8 +7,8 @@
 //   Y' = Y + theta (Z - A_k(L')),  theta' = min(rho theta, theta_max).
 //
 // GPU form. The SVD of the m x k matrix B = A_k(L) - Y/theta goes through its k x k Gram
-// C = B^T B = W Sigma^2 W^T (FP64 sums of exact products of the FP32 entries of B, then
-// the FP64 Jacobi eigensolver), so SVT(B) = B Phi with Phi = W diag(max(0, 1 -
+// C = B^T B = W Sigma^2 W^T (exact products of the FP32 entries of B, summed to about
+// 2^-48 relative per tile and in FP64 across tiles, then the FP64 Jacobi eigensolver), so SVT(B) = B Phi with Phi = W diag(max(0, 1 -
 // 1/(theta sigma_i))) W^T. The Jacobi method starts each iteration from the previous
 // iteration's W (it diagonalises W_prev^T C W_prev, then rotates W_prev), which leaves
 // few sweeps once the iteration settles.
@@ -81,7 +81,8 @@ __device__ __forceinline__ float halo_at(const CnnmDev& d, const float* sX, int 
 
 // Partial Gram blocks: block pair (ib <= jb) of 64 taps, over the voxel tiles
 // blockIdx.y, blockIdx.y + gridDim.y, ... part[(split * npair + pair) * 4096 + a * 64 + b]
-// = sum_v B[v][ib*64 + a] B[v][jb*64 + b] (FP64 sums of exact products).
+// = sum_v B[v][ib*64 + a] B[v][jb*64 + b] (exact products, summed per tile as float pairs
+// and across tiles in FP64).
 __global__ void __launch_bounds__(CG_THREADS)
 cnnm_gram_kernel(CnnmDev d, float acoef, float inv_th, int nb, double* part) {
   extern __shared__ float smem[];
@@ -119,16 +120,36 @@ cnnm_gram_kernel(CnnmDev d, float acoef, float inv_th, int nb, double* part) {
       (side ? sBj : sBi)[vv * CG_PITCH + ss] = b;
     }
     __syncthreads();
+    // the tile's 128 products per output, each split exactly into p + e (p = x*y rounded,
+    // e = fma(x, y, -p)) and summed as a float pair hi + lo with Knuth's TwoSum (about
+    // 2^-48 relative, on the FP32 pipe), then added into the FP64 sums once per tile
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.f;
     for (int vv = 0; vv < TILE_VOX; ++vv) {
       const float4 bi = *reinterpret_cast<const float4*>(sBi + vv * CG_PITCH + ti * 4);
       const float4 bj = *reinterpret_cast<const float4*>(sBj + vv * CG_PITCH + tj * 4);
-      const double xi[4] = {bi.x, bi.y, bi.z, bi.w};
-      const double xj[4] = {bj.x, bj.y, bj.z, bj.w};
+      const float xi[4] = {bi.x, bi.y, bi.z, bi.w};
+      const float xj[4] = {bj.x, bj.y, bj.z, bj.w};
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xi[a], xj[b], acc[a][b]);
+        for (int b = 0; b < 4; ++b) {
+          const float p = __fmul_rn(xi[a], xj[b]);
+          const float e = __fmaf_rn(xi[a], xj[b], -p);
+          const float sum = __fadd_rn(hi[a][b], p);
+          const float bb = __fsub_rn(sum, hi[a][b]);
+          const float err = __fadd_rn(__fsub_rn(hi[a][b], __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+          hi[a][b] = sum;
+          lo[a][b] = __fadd_rn(lo[a][b], __fadd_rn(err, e));
+        }
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += (double)hi[a][b] + (double)lo[a][b];
   }
   const int npair = nb * (nb + 1) / 2;
   double* out = part + ((long long)blockIdx.y * npair + blockIdx.x) * (CG * CG);
