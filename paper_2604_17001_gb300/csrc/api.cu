@@ -1154,7 +1154,7 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* c, const icnnm_shape* shape, const floa
     CK(cudaStreamSynchronize(c->stream));
     if (h2[1]) fail(ICNNM_EINVAL, "mask entries must be 0/1 and M must be finite on Omega");
     if (h2[0] == 0) fail(ICNNM_EINVAL, "Omega is empty");
-    CnnmProblem P{H, W, T, k1, k2, k3, dM, dK, dL, p.max_iters, p.theta0, p.rho, p.theta_max, false};
+    CnnmProblem P{H, W, T, k1, k2, k3, dM, dK, dL, p.max_iters, p.theta0, p.rho, p.theta_max};
     CnnmResult r{};
     CK(cnnm_run(P, c->stream, &r));
     if (r.timed_out) fail(ICNNM_ETIMEOUT, "a bounded grid barrier of the eigensolver expired");

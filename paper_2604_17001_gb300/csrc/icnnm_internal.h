@@ -182,11 +182,10 @@ struct CnnmProblem {
   float* dL;                // device output, m
   int iters;
   double theta0, rho, theta_max;   // theta0 <= 0: 1/||A_k(P_Omega M)||_2
-  bool count_sweeps;        // synchronise each iteration to count Jacobi sweeps
 };
 struct CnnmResult {
   double seconds, theta, objective;   // device time; final penalty; ||A_k(L)||_*
-  int timed_out, sweeps;
+  int timed_out;
 };
 size_t cnnm_state_bytes(int H, int W, int T, int k1, int k2, int k3);
 cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res);

@@ -407,7 +407,6 @@ cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res) {
   double thp = 0.0;
   float *Lc = L0, *Ln = L1, *Wc = W0, *Wn = W1;
   double *Wcur = Wv, *Wnext = Wv2;
-  int total_sweeps = 0;
   for (int it = 0; it < P.iters && e == cudaSuccess; ++it) {
     d.L = Lc; d.WT = Wc; d.WTn = Wn; d.Phi = Phi; d.Lnew = Ln;
     const float acoef = (float)(1.0 + thp / theta), inv_th = (float)(1.0 / theta);
@@ -423,12 +422,6 @@ cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res) {
                                                                                          (float)theta, (float)thp);
     cnnm_gather_kernel<<<gblk * 2, 256, 0, st>>>(d, (float)(1.0 / (k * theta)));
     if ((e = cudaGetLastError()) != cudaSuccess) break;
-    if (P.count_sweeps) {
-      int hinfo[2];
-      if ((e = cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
-      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
-      total_sweeps += hinfo[0];
-    }
     std::swap(Lc, Ln);
     std::swap(Wc, Wn);
     std::swap(Wcur, Wnext);
@@ -445,7 +438,6 @@ cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res) {
   res->seconds = ms * 1e-3;
   res->theta = theta;
   res->timed_out = hinfo[1];
-  res->sweeps = total_sweeps;
   // objective ||A_k(L)||_* = sum of the singular values of A_k(L)
   gram_eigs(Lc);
   if (e == cudaSuccess) {
