@@ -472,8 +472,8 @@ int fwd_slots(const Shared& sh, int prec, const TcVData* tcv) {
 // Column norms ||A_k(L) v_c||^2 of each job's current L into its colseg through the
 // Gram A_k(L)^T A_k(L) (autocorrelations of exact products, then v_c^T G v_c in FP64):
 // FP64-accurate and far cheaper than the FP32 m x k x k forward pass it replaces for
-// theta0 and the objective. Returns false (nothing launched) where the autocorrelation
-// kernel's limits do not admit the kernel size.
+// theta0 and the objective on large jobs. Returns false (nothing launched) where the
+// autocorrelation kernel's limits do not admit the kernel size.
 bool gram_colnorms(icnnm_ctx* c, const std::vector<Job*>& js) {
   const VData* vd = js[0]->vd;
   const int k1 = vd->k1, k2 = vd->k2, k3 = vd->k3, k = vd->k;
@@ -499,6 +499,30 @@ bool gram_colnorms(icnnm_ctx* c, const std::vector<Job*>& js) {
   return true;
 }
 
+// Jobs whose FP32 forward pass would take at least 2^31 multiply-adds (m k^2) take their
+// once-per-solve column norms from the Gram; below that the Gram's fixed cost (three
+// launches, per-block partial sums) exceeds the pass. Decided per job, so a job takes the
+// same route alone and in a batch.
+void launch_reduce_cols_counted(icnnm_ctx* c, const Shared& sh) {
+  PassScope ps(c, 3, 1);
+  CK(launch_reduce_cols(sh, 0, 0, c->stream));
+}
+
+bool gram_route(const Job* j) { return (double)j->m * j->vd->k * j->vd->k >= 2147483648.0; }
+
+// Column norms of A_k(L)V for every job of js into its colseg (L = the job's current L):
+// the Gram route for the large jobs, the FP32 forward pass (mode 0 or 4) for the rest,
+// as a list of its own in the second device job table.
+void colnorms_once(icnnm_ctx* c, const std::vector<Job*>& js, int mode) {
+  std::vector<Job*> big, small;
+  for (Job* j : js) (gram_route(j) ? big : small).push_back(j);
+  if (!big.empty() && !gram_colnorms(c, big)) small.insert(small.end(), big.begin(), big.end());
+  if (small.empty()) return;
+  const Shared shs = upload_list(c, small, 1);
+  run_fwd(c, shs, ICNNM_FP32, mode, nullptr);
+  launch_reduce_cols_counted(c, shs);
+}
+
 #define OTHER(n, expr)            \
   do {                            \
     PassScope ps__(c, 3, (n));    \
@@ -512,10 +536,7 @@ void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
   const TcVData* tcv = &js[0]->vd->tc;
   Shared sh = upload_list(c, js);
   OTHER(1, launch_init_L(sh, c->stream));
-  if (!gram_colnorms(c, js)) {
-    run_fwd(c, sh, ICNNM_FP32, 0, tcv);
-    OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
-  }
+  colnorms_once(c, js, 0);
   OTHER(1, launch_theta0(sh, js[0]->p.theta0, c->stream));
   OTHER(1, launch_scale_X(sh, c->stream));
   if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
@@ -553,10 +574,7 @@ void engine_step(icnnm_ctx* c, const Shared& sh, int prec, const TcVData* tcv, b
 // video-prediction workload).
 void engine_objective(icnnm_ctx* c, const std::vector<Job*>& js) {
   const Shared sh = upload_list(c, js);
-  if (!gram_colnorms(c, js)) {
-    run_fwd(c, sh, ICNNM_FP32, 4, nullptr);
-    OTHER(1, launch_reduce_cols(sh, 0, 0, c->stream));
-  }
+  colnorms_once(c, js, 4);
   OTHER(1, launch_finish(sh, 2, c->stream));
 }
 
