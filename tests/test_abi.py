@@ -49,5 +49,8 @@ def test_null_arguments_are_errors_not_crashes(lib):
     assert lib.icnnm_create(None, 0, 0, None) == icnnm.EINVAL
     assert lib.icnnm_solve(None, None, None, None, None, None, None, None) == icnnm.EINVAL
     assert lib.icnnm_poll(None, 1, None, None) == icnnm.EINVAL
+    assert lib.icnnm_learn_V(None, None, 0, None, None, None, None) == icnnm.EINVAL
+    assert lib.icnnm_cnnm_solve(None, None, None, None, None, None, None) == icnnm.EINVAL
+    assert lib.icnnm_spectral_diagnostics(None, None, None, None, 1e-6, None, None, None, None) == icnnm.EINVAL
     lib.icnnm_destroy(None)
     assert lib.icnnm_last_error(None) == b""
