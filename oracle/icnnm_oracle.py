@@ -31,7 +31,7 @@ __all__ = [
     "P_Omega", "column_norms", "norm_21", "gram", "learn_V", "canonical_signs",
     "prox_21", "icnnm_init", "icnnm_iteration", "icnnm_solve", "cnnm_solve",
     "relative_eigvals", "spectral_correlation", "relative_rank", "active_coherence",
-    "theta0_default",
+    "theta0_default", "primal_residual",
 ]
 
 CHUNK_ROWS = 8192
@@ -253,6 +253,14 @@ def prox_21(R: np.ndarray, tau: float) -> np.ndarray:
     return R * scale[None, :]
 
 
+def primal_residual(Z, Q, L, k) -> float:
+    """Stopping quantity (a reading; the paper states no stopping rule): the primal
+    residual of the split Z = A_k(L)K, ||Z - A_k(L)K||_F, relative to
+    ||A_k(L)K||_F = sqrt(k)||L||_F (A_k^*A_k = kI and K orthogonal), with Q = A_k(L)K
+    of the current L."""
+    return float(np.linalg.norm(Z - Q) / (np.sqrt(k) * max(np.linalg.norm(L), 1e-300)))
+
+
 def theta0_default(M, mask, V, kdims) -> float:
     """Initial penalty (a reading; the paper is silent): 1/||A_k(P_Omega M) V||_{2,inf}."""
     Q0 = conv_matrix_times(P_Omega(M, mask), V, kdims)
@@ -320,11 +328,11 @@ def icnnm_solve(M, mask, V, kdims, lam=np.inf, theta0=None, rho=1.1, theta_max=1
         if return_history:
             hist.append(dict(objective=norm_21(Q), L=L.copy()))
         if tol > 0 and it % check_every == 0:
-            resid = float(np.linalg.norm(Z - Q) / (np.sqrt(k) * max(np.linalg.norm(L), 1e-300)))
+            resid = primal_residual(Z, Q, L, k)
             if resid <= tol:
                 break
     if not (tol > 0 and it % check_every == 0):
-        resid = float(np.linalg.norm(Z - Q) / (np.sqrt(k) * max(np.linalg.norm(L), 1e-300)))
+        resid = primal_residual(Z, Q, L, k)
     stats = dict(iters=it, residual=resid, objective=norm_21(Q), theta=theta)
     if return_history:
         stats["history"] = hist

@@ -411,3 +411,103 @@ def test_active_coherence_bounds_and_special_cases():
     assert 1 - 1e-12 <= mu <= 16 / 3 + 1e-12
     # K = I (unit taps) keeps full support on a generic tensor, so mu = 1 again
     assert O.active_coherence(L0, np.eye(k), kd) == pytest.approx(1.0, abs=1e-12)
+
+
+# -------------------------------------------------------------------------------
+# theta0 and the stopping rule (readings of the silent Sec. III-D): hand-derived values
+# on the rank-2 cosine, and the residual through the multiplier history.
+# -------------------------------------------------------------------------------
+def _cosine_case():
+    c = json.load(open(os.path.join(GOLDEN, "closed_forms.json")))["theta0"]
+    H, W, T = c["dims_HWT"]
+    L = np.cos(2 * np.pi * c["f"] * np.arange(W) / W).reshape(T, H, W)
+    return c, L, tuple(c["kdims"])
+
+
+def test_theta0_default_hand_values():
+    c, L, kd = _cosine_case()
+    k = int(np.prod(kd))
+    full = np.ones(L.shape, dtype=np.uint8)
+    assert O.theta0_default(L, full, np.eye(k), kd) == pytest.approx(c["full_mask_identity_V"]["theta0"], rel=1e-12)
+    V, _ = O.learn_V([L], kd)
+    assert O.theta0_default(L, full, V, kd) == pytest.approx(c["full_mask_own_V"]["theta0"], rel=1e-12)
+    even = np.zeros(L.shape, dtype=np.uint8)
+    even[..., 0::2] = 1
+    # M carries the full cosine: theta0 must see only its observed entries
+    assert O.theta0_default(L, even, np.eye(k), kd) == pytest.approx(c["even_w_observed_identity_V"]["theta0"],
+                                                                     rel=1e-12)
+
+
+def test_residual_closed_form_full_mask():
+    c, L, kd = _cosine_case()
+    r = c["residual_full_mask_identity_V"]
+    k = int(np.prod(kd))
+    full = np.ones(L.shape, dtype=np.uint8)
+    _, s1 = O.icnnm_solve(L, full, np.eye(k), kd, max_iters=1)
+    assert s1["residual"] == pytest.approx(r["residual_iter1"], rel=1e-12)
+    _, s2 = O.icnnm_solve(L, full, np.eye(k), kd, max_iters=2)
+    assert abs(s2["residual"] - r["residual_iter2"]) <= 1e-14
+    # the stopping rule: the first check at or below tol ends the run
+    _, s = O.icnnm_solve(L, full, np.eye(k), kd, max_iters=50, tol=0.5, check_every=1)
+    assert s["iters"] == 2
+
+
+def test_residual_equals_multiplier_step():
+    # Independent route: the multiplier step Y' = Y + theta(Z - A_k(L')K) gives
+    # Z - A_k(L')K = (Y' - Y)/theta, so the residual after iteration t is
+    # ||Y_t - Y_{t-1}||_F / (theta_{t-1} sqrt(k) ||L_t||_F); the run stops at the first
+    # multiple of check_every where that is <= tol.
+    L0 = synth.video(10, 8, 4, seed=91).astype(np.float64)
+    mask = synth.mask_uniform(10, 8, 4, 0.45, seed=92)
+    M = np.where(mask.astype(bool), L0, 0.0)
+    kd = (3, 3, 2)
+    k = 18
+    V, _ = O.learn_V([synth.video(10, 8, 4, seed=93)], kd)
+    L, Y, th = O.icnnm_init(M, mask, V, kd)
+    Q = None
+    res = []
+    for _ in range(40):
+        Ln, Yn, Z, Q = O.icnnm_iteration(L, Y, th, M, mask, V, kd, np.inf, Q)
+        res.append(np.linalg.norm(Yn - Y) / (th * np.sqrt(k) * np.linalg.norm(Ln)))
+        L, Y, th = Ln, Yn, 1.1 * th
+    for n in (1, 7, 40):
+        _, s = O.icnnm_solve(M, mask, V, kd, max_iters=n)
+        assert s["residual"] == pytest.approx(res[n - 1], rel=1e-9)
+    srt = np.sort(res[5:30])
+    tol, every = float(0.5 * (srt[12] + srt[13])), 3      # between two residuals: no ties
+    want = next(t for t in range(every, 41, every) if res[t - 1] <= tol)
+    _, s = O.icnnm_solve(M, mask, V, kd, max_iters=40, tol=tol, check_every=every)
+    assert s["iters"] == want and s["residual"] == pytest.approx(res[want - 1], rel=1e-9)
+
+
+def test_planted_theta0_row_norms_is_caught(monkeypatch):
+    def rows(M, mask, V, kdims):   # ||.||_{2,inf} taken over rows instead of columns
+        Q0 = O.conv_matrix_times(O.P_Omega(M, mask), V, kdims)
+        return 1.0 / float(O.column_norms(Q0.T).max())
+
+    monkeypatch.setattr(O, "theta0_default", rows)
+    with pytest.raises(AssertionError):
+        test_theta0_default_hand_values()
+
+
+def test_planted_theta0_without_projection_is_caught(monkeypatch):
+    def no_proj(M, mask, V, kdims):   # P_Omega forgotten
+        return 1.0 / float(O.column_norms(O.conv_matrix_times(M, V, kdims)).max())
+
+    monkeypatch.setattr(O, "theta0_default", no_proj)
+    with pytest.raises(AssertionError):
+        test_theta0_default_hand_values()
+
+
+@pytest.mark.parametrize("mistake", ["no_sqrt_k", "norm_of_Z", "squared"])
+def test_planted_residual_mistakes_are_caught(monkeypatch, mistake):
+    orig = O.primal_residual
+    wrong = {
+        "no_sqrt_k": lambda Z, Q, L, k: orig(Z, Q, L, 1),
+        "norm_of_Z": lambda Z, Q, L, k: orig(Z, 0 * Q, L, k),
+        "squared": lambda Z, Q, L, k: orig(Z, Q, L, k) ** 2,
+    }[mistake]
+    monkeypatch.setattr(O, "primal_residual", wrong)
+    with pytest.raises(AssertionError):
+        test_residual_closed_form_full_mask()
+        test_residual_equals_multiplier_step()
