@@ -1,18 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark of the GB300 ICNNM library on the video-prediction workload.
+"""Benchmark of the GB300 ICNNM library on the serving workload (the default line).
 
-Workload (synthetic stand-in for the paper's CDNet 2014 prediction experiment,
-Sec. V-C): one 128x128x32 video (sinusoids + moving blobs), frames 24..31 missing,
-kernel 9x9x5 (k = 405), V learned from 64 reference tensors, 500 ADMM iterations.
+Serving workload (the metric's configuration): a stream of 2000 completion requests,
+H, W uniform in 32..256 step 16, T uniform in 8..64 (synthetic videos: sinusoids + moving
+blobs), the four mask families (30-70% uniform, last frames missing, every other frame
+missing, 16x16 block holes), kernel 7x7x3 (k = 147) with one shared V learned from 32
+reference tensors, each request run to a relative residual of 1e-3 (checked every 10
+iterations, at most 1000). Requests are submitted to the continuous-batching server
+(icnnm_submit / icnnm_wait) in BF16; plain FP32 solves requests one at a time.
 
-A step is one complete solve (all 500 iterations of the forward pass, the shrinkage,
-the adjoint pass and the projection) with V fixed; learning V is timed separately and
-reported under "learn_V". `value` is BF16 solves/s with the inputs resident in HBM;
-"e2e" is the same through the C ABI with host buffers (copies inside the timed
-region); "fp32_plain" is the plain FP32 path, one solve at a time.
+A step is one wave of requests (the stream cut into K waves of consecutive requests),
+all submitted at once and collected; `value` is served BF16 solves/s over the K timed
+waves with inputs and outputs resident in HBM; "e2e" is the same through the C ABI with
+host buffers; "latency_ms" is the submit-to-done p50/p99 of a Poisson stream at 0.8x the
+measured served rate; "fp32_plain" the plain FP32 path one request at a time;
+"rel_err_vs_oracle" the served results against stored FP64 oracle iterates of the same
+iteration count; "prediction" the video-prediction workload (128x128x32, k = 405, 500
+iterations) as blocking solves.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --workload completion|interpolation|batch|serving   (the other workload families)
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--requests R]
+    python bench.py --workload prediction|completion|interpolation|batch|image|cnnm
 """
 from __future__ import annotations
 
@@ -49,9 +56,13 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learn", action="store_true")
-    ap.add_argument("--workload", default="prediction", choices=["prediction", "completion", "interpolation", "batch", "serving", "image", "cnnm"],
-                    help="prediction (the default line); the others print their own line")
-    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--workload", default="serving",
+                    choices=["serving", "prediction", "completion", "interpolation", "batch", "image", "cnnm"],
+                    help="serving (the default line); the others print their own line")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
+    ap.add_argument("--latency-requests", type=int, default=400, help="serving: requests of the Poisson run")
+    ap.add_argument("--fp32-requests", type=int, default=12, help="serving: requests solved in plain FP32")
+    ap.add_argument("--no-prediction", action="store_true", help="serving: skip the prediction sub-run")
     return ap.parse_args()
 
 
@@ -148,26 +159,42 @@ def load_V(w):
 
 
 def run_reference(args, ws, rank):
+    """The FP64 oracle on the host cores, on the serving workload: each step times oracle
+    ADMM iterations of one sampled request of the stream (bounded to a few seconds) and
+    scales the cost per voxel-iteration to the stream's mean request (mean voxels x the
+    stored oracle runs' mean stopping iteration)."""
     if rank != 0:
         return
-    w = workload_inputs()
-    V, _ = load_V(w)
-    if V is None:
+    from paper_2604_17001_gb300 import synth
+    R = args.requests
+    shapes = synth.serving_shapes(R)
+    mean_vox = float(np.mean([np.prod(s_) for s_ in shapes]))
+    if os.path.exists(SERVING_GOLDEN):
+        g = np.load(SERVING_GOLDEN)
+        V = g["V"]
+        stops = [int(g[f"r{int(j)}_stop"]) for j in g["sample"] if f"r{int(j)}_stop" in g.files]
+        mean_it = float(np.mean(stops)) if stops else 60.0
+    else:
         from oracle import icnnm_oracle as O
-        V, _ = O.learn_V(w["refs"][:4], w["kdims"])
+        V, _ = O.learn_V(synth.serving_refs()[:4], synth.WORKLOADS[5]["kdims"])
+        mean_it = 60.0
     for _ in range(args.warmup):
-        oracle_iteration_seconds(w, V, 1)
-    ts = [oracle_iteration_seconds(w, V, 1)[0] for _ in range(args.steps)]
-    t_solve = statistics.mean(ts) * args.iters
-    value = 1.0 / t_solve
+        serving_cpu_baseline(V, budget_s=1.0)
+    spv = []
+    for _ in range(args.steps):
+        x, sample = serving_cpu_baseline(V, budget_s=6.0)
+        spv.append(x)
+    per_req = float(np.mean(spv)) * mean_vox * mean_it
+    value = 1.0 / per_req
     cores = os.cpu_count()
-    sample = f"1 of {args.iters} ADMM iterations of the 128x128x32 k=405 solve per step, scaled to a solve"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_req * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "prediction_128x128x32_k9x9x5", "iters": args.iters},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "config": {"workload": f"serving_poisson{R}_k7x7x3", "requests": R,
+                   "scaled_to": f"mean request {mean_vox:.0f} voxels x {mean_it:.0f} iterations"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample + " (per step)"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -180,7 +207,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def run_ours(args, ws, rank, local):
+def run_ours(args, ws, rank, local, sub=False):
     import torch
     from paper_2604_17001_gb300 import icnnm
     torch.cuda.set_device(local)
@@ -331,7 +358,7 @@ def run_ours(args, ws, rank, local):
 
     ctx.close()
     if rank != 0:
-        return
+        return None
     lat_sorted = sorted(lat)
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -352,6 +379,8 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": int(nall.value),
         "learn_V": learn,
     }
+    if sub:
+        return out
     print(json.dumps(out))
 
 
@@ -508,101 +537,6 @@ def run_batch(args, local):
                                      "mode": "one job at a time"}}))
 
 
-def run_serving(args, local):
-    """A Poisson stream of requests (H, W in 32..256 step 16, T in 8..64, kernel 7x7x3,
-    mixed masks), each run to a relative residual of 1e-3 (checked every 10 iterations,
-    at most 1000). Plain FP32 solves every request one at a time (its service times give
-    its capacity and, through a first-come-first-served queue on the same arrival times,
-    its latencies); served BF16 admits the same stream into the continuous-batching
-    server at 0.7x and 0.9x the FP32 capacity, and once more with every request arriving
-    at once (throughput)."""
-    import threading
-    import torch
-    from paper_2604_17001_gb300 import icnnm, synth
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(local)
-    kd = synth.WORKLOADS[5]["kdims"]
-    n = args.requests
-    jobs = synth.batch_jobs(n, cfg=5, hw_range=(32, 256), t_range=(8, 64))
-    refs = [synth.video(64, 64, 16, synth.seed_for(5, j)) for j in range(1, synth.WORKLOADS[5]["n_ref"] + 1)]
-    kw = dict(max_iters=1000, tol=1e-3, check_every=10)
-    ctx = icnnm.Context(local)
-    V = _learn_V_gpu(ctx, refs, kd, dev)
-    # plain FP32 service times (host buffers, blocking, one at a time)
-    ctx.icnnm_solve(jobs[0]["M"], jobs[0]["mask"], V, kd, prec="fp32", **kw)
-    svc, iters32 = [], []
-    for j in jobs:
-        t0 = time.perf_counter()
-        _, st = ctx.icnnm_solve(j["M"], j["mask"], V, kd, prec="fp32", **kw)
-        svc.append(time.perf_counter() - t0)
-        iters32.append(st["iters"])
-    cap32 = n / sum(svc)
-    rng = np.random.default_rng(synth.seed_for(5, 77))
-    gaps = rng.exponential(1.0, size=n)          # unit-rate Poisson gaps, scaled per load
-
-    def fcfs32(arr):
-        # FP32 one at a time on the same arrivals (first come, first served)
-        done, lat = 0.0, []
-        for a, sv in zip(arr, svc):
-            start = max(a, done)
-            done = start + sv
-            lat.append(done - a)
-        return lat
-
-    def serve(arr):
-        lat = [None] * n
-        its = [None] * n
-        ids = [None] * n
-        t0 = time.perf_counter()
-
-        def submitter():
-            for i, a in enumerate(arr):
-                dt = a - (time.perf_counter() - t0)
-                if dt > 0:
-                    time.sleep(dt)
-                ids[i] = (ctx.icnnm_submit(jobs[i]["M"], jobs[i]["mask"], V, kd, prec="bf16", **kw),
-                          time.perf_counter())
-        th = threading.Thread(target=submitter)
-        th.start()
-        outs = [np.zeros_like(j["M"]) for j in jobs]
-        left = set(range(n))
-        while left:
-            for i in sorted(left):
-                if ids[i] is None:
-                    continue
-                r, st = ctx.icnnm_wait(ids[i][0], L_out=outs[i], timeout_ms=0)
-                if r == icnnm.OK:
-                    lat[i] = time.perf_counter() - ids[i][1]
-                    its[i] = st["iters"]
-                    left.discard(i)
-            time.sleep(0.0005)
-        th.join()
-        return lat, time.perf_counter() - t0, its
-
-    pct = lambda x, q: float(np.percentile(np.asarray(x) * 1e3, q))
-    loads = {}
-    for load in (0.7, 0.9):
-        rate = load * cap32
-        arrivals = np.cumsum(gaps / rate)
-        lat_p, span_p, _ = serve(arrivals)
-        lat32 = fcfs32(arrivals)
-        loads[f"{load:.1f}x_fp32_capacity"] = {
-            "rate_per_s": rate, "served_bf16": {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
-                                                 "solves_per_s": n / span_p},
-            "plain_fp32": {"p50_ms": pct(lat32, 50), "p99_ms": pct(lat32, 99)}}
-    lat_s, span_s, its_s = serve(np.zeros(n))
-    ctx.close()
-    print(json.dumps({
-        "metric": METRIC, "workload": f"serving_poisson{n}_k7x7x3", "value": n / span_s, "unit": "solves/s",
-        "higher_is_better": True, "dtype": "bf16", "data": "synthetic", "requests": n,
-        "stop": "relative residual <= 1e-3, checked every 10 iterations, at most 1000",
-        "served_bf16": {"saturated": {"solves_per_s": n / span_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99)},
-                        "mean_iters": float(np.mean(its_s))},
-        "plain_fp32": {"solves_per_s": cap32, "mean_iters": float(np.mean(iters32)),
-                       "mode": "one at a time, FCFS on the same arrivals"},
-        "poisson": loads}))
-
-
 # sigma_i below 1e-4 sigma_max count as zero in the Table I analog: learn_V's Gram (FP32
 # products) leaves the eigenvectors of the smallest eigenvalues too inexact to resolve
 # those directions, which would otherwise lift the G.T. scheme's alpha_K above 1.
@@ -719,6 +653,290 @@ def run_cnnm(args, local):
                       "paper_kodak_13x13_s": {"cnnm": 18.643, "icnnm": 11.189}}))
 
 
+# -- the serving workload (default line) -------------------------------------------
+SERVING_GOLDEN = os.path.join(ROOT, "tests", "golden", "serving_k7x7x3_sample.npz")
+SERVING_KW = dict(max_iters=1000, tol=1e-3, check_every=10)
+
+
+def _gen_requests(lo, hi, n):
+    from paper_2604_17001_gb300 import synth
+    shapes = synth.serving_shapes(n)
+    out = []
+    for j in range(lo, hi):
+        r = synth.serving_job(j, shapes)
+        out.append((r["M"], r["mask"], r["family"]))
+    return out
+
+
+def serving_inputs(n):
+    """The first n requests of the serving stream, generated by a spawn-started process
+    pool (before any CUDA call in this process)."""
+    import multiprocessing as mp
+    procs = max(1, min(16, os.cpu_count() or 1))
+    bounds = np.linspace(0, n, min(n, 4 * procs) + 1).astype(int)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        parts = pool.starmap(_gen_requests, [(int(a), int(b), n) for a, b in zip(bounds[:-1], bounds[1:]) if b > a])
+    return [x for part in parts for x in part]
+
+
+def serving_cpu_baseline(V, budget_s=12.0):
+    """The FP64 oracle as it stands on a bounded sample: ADMM iterations of request 69 of
+    the stream (32x32x8, block holes) until budget_s seconds have passed; returns seconds
+    per voxel-iteration and the sample's description."""
+    from oracle import icnnm_oracle as O
+    from paper_2604_17001_gb300 import synth
+    kd = synth.WORKLOADS[5]["kdims"]
+    shapes = synth.serving_shapes(2000)
+    r = synth.serving_job(69, shapes)
+    m = int(np.prod(r["dims"]))
+    L, Y, th = O.icnnm_init(r["M"], r["mask"], V, kd)
+    Q = O.conv_matrix_times(L, V, kd)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or n < 2:
+        L, Y, Z, Q = O.icnnm_iteration(L, Y, th, r["M"], r["mask"], V, kd, np.inf, Q)
+        th *= 1.1
+        n += 1
+    sec = (time.perf_counter() - t0) / n
+    return sec / m, f"{n} ADMM iterations (FP64 numpy, explicit A_k rows) of request 69 of the stream " \
+                    f"(32x32x8, k=147), {sec:.3f} s each, scaled per voxel-iteration to the stream"
+
+
+def run_serving_bench(args, ws, rank, local):
+    R = args.requests
+    reqs = serving_inputs(R)                  # host inputs; no CUDA call before this
+    import threading
+    import torch
+    import ctypes as C
+    from paper_2604_17001_gb300 import icnnm, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kd = synth.WORKLOADS[5]["kdims"]
+    k = int(np.prod(kd))
+    shapes = synth.serving_shapes(R)
+    vox = np.array([int(np.prod(s)) for s in shapes], dtype=np.int64)
+    g = np.load(SERVING_GOLDEN) if os.path.exists(SERVING_GOLDEN) else None
+    ctx = icnnm.Context(local)
+    # learn_V on the GPU (timed; the solves use the stored oracle V when present so that
+    # the served results can be compared with the stored oracle iterates)
+    refs_d = [torch.from_numpy(r).to(dev) for r in synth.serving_refs()]
+    ctx.icnnm_learn_V(refs_d[:2], kd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    V_gpu, _ = ctx.icnnm_learn_V(refs_d, kd)
+    learn = {"seconds": time.perf_counter() - t0, "refs": len(refs_d), "k": k}
+    V = g["V"] if g is not None else V_gpu
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(dev)
+    Md = [torch.from_numpy(M).to(dev) for M, _, _ in reqs]
+    Kd = [torch.from_numpy(K).to(dev) for _, K, _ in reqs]
+    Ld = [torch.empty_like(M) for M in Md]
+    torch.cuda.synchronize()
+
+    def wave(ids, host=False, outs=None):
+        """Submit requests ids at once and collect them; returns (seconds, stats list)."""
+        t0 = time.perf_counter()
+        jids = [ctx.icnnm_submit(reqs[i][0] if host else Md[i], reqs[i][1] if host else Kd[i], V if host else Vd,
+                                 kd, prec="bf16", **SERVING_KW) for i in ids]
+        sts = []
+        for n_, (i, jid) in enumerate(zip(ids, jids)):
+            r_, st = ctx.icnnm_wait(jid, L_out=outs[n_] if host else Ld[i], timeout_ms=-1)
+            sts.append(st)
+        if not host:
+            torch.cuda.synchronize()
+        return time.perf_counter() - t0, sts
+
+    K = max(1, args.steps)
+    bounds = np.linspace(0, R, K + 1).astype(int)
+    waves = [list(range(a, b)) for a, b in zip(bounds[:-1], bounds[1:])]
+    for wi in range(args.warmup):
+        wave(list(range(min(8, R))))
+    ctx.lib.icnnm_profile_enable(ctx.h, 0)          # resets the launch counters
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    stats = [None] * R
+    times = []
+    for ids in waves:
+        sec, sts = wave(ids)
+        times.append(sec)
+        for i, st in zip(ids, sts):
+            stats[i] = st
+    barrier(ws)
+    clk = clocks.stop()
+    nall = C.c_int64()
+    ctx.lib.icnnm_profile_read(ctx.h, -1, None, C.byref(nall))
+    total = max_over_ranks(sum(times), ws)
+    value = ws * R / total
+    iters = np.array([st["iters"] for st in stats])
+    resid = np.array([st["residual"] for st in stats])
+
+    # accuracy: served results against the stored FP64 oracle iterates of the same count
+    rel = {}
+    if g is not None:
+        for j in [int(x) for x in g["sample"] if int(x) < R and f"r{int(x)}_iters" in g.files]:
+            its = list(g[f"r{j}_iters"])
+            n_ = int(stats[j]["iters"])
+            if n_ in its:
+                ref = g[f"r{j}_L"][its.index(n_)]
+                got = Ld[j].reshape(-1)[torch.from_numpy(g[f"r{j}_idx"]).to(dev)].double().cpu().numpy()
+                rel[str(j)] = {"iters": n_, "oracle_stop": int(g[f"r{j}_stop"]),
+                               "rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+            else:
+                rel[str(j)] = {"iters": n_, "oracle_stop": int(g[f"r{j}_stop"]), "rel_err": None}
+    obs_ok = all(bool(torch.equal(Ld[i][Kd[i].bool()], Md[i][Kd[i].bool()])) for i in range(0, R, max(1, R // 64)))
+
+    # per-request latency under Poisson arrivals at 0.8x the measured served rate
+    P = min(R, args.latency_requests)
+    rate = 0.8 * value / ws
+    rng = np.random.default_rng(synth.seed_for(5, 77))
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=P))
+    jid_lat = [None] * P
+    t_start = time.perf_counter()
+
+    def submitter():
+        for i in range(P):
+            dt = arr[i] - (time.perf_counter() - t_start)
+            if dt > 0:
+                time.sleep(dt)
+            jid_lat[i] = ctx.icnnm_submit(Md[i], Kd[i], Vd, kd, prec="bf16", **SERVING_KW)
+    th_ = threading.Thread(target=submitter)
+    th_.start()
+    lat = []
+    for i in range(P):
+        while jid_lat[i] is None:
+            time.sleep(0.0005)
+        _, st = ctx.icnnm_wait(jid_lat[i], L_out=Ld[i], timeout_ms=-1)
+        lat.append(st["latency"])
+    th_.join()
+    lat_ms = np.array(lat) * 1e3
+
+    # roofline of the dominant pass over one profiled wave
+    ctx.lib.icnnm_profile_enable(ctx.h, 1)
+    prof_sec, _ = wave(waves[0])
+    prof = {}
+    for p_, name in ((0, "forward"), (1, "adjoint"), (2, "gather"), (3, "other")):
+        ms, n_, vx = C.c_double(), C.c_int64(), C.c_int64()
+        ctx.lib.icnnm_profile_read(ctx.h, p_, C.byref(ms), C.byref(n_))
+        ctx.lib.icnnm_profile_voxels(ctx.h, p_, C.byref(vx))
+        prof[name] = (ms.value, n_.value, vx.value)
+    ctx.lib.icnnm_profile_enable(ctx.h, 0)
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tfl = peaks.get("bf16_tflops_sustained", 1700.0)
+    dom = max(("forward", "adjoint"), key=lambda n: prof[n][0])
+    ms, n_, vx = prof[dom]
+    per_ms = ms / max(n_, 1)
+    vox_per_launch = vx / max(n_, 1)
+    alg_bytes = (4 if dom == "forward" else 2) * k * vox_per_launch     # BF16 U read (+ write)
+    alg_flops = 2.0 * k * k * vox_per_launch
+    gbs = alg_bytes / (per_ms * 1e-3) / 1e9
+    tfs = alg_flops / (per_ms * 1e-3) / 1e12
+    src = "measured" if peaks else "fallback"
+    if gbs / hbm >= tfs / tfl:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+    else:
+        roof = {"bound": "tensor", "achieved": tfs, "peak": tfl, "unit": "TFLOP/s", "frac": tfs / tfl}
+    traffic = None
+    if os.path.exists(TRAFFIC):
+        ent = json.load(open(TRAFFIC)).get(f"serving_{dom}")
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            traffic = ent.get("bytes_per_launch")
+    roof.update({"traffic": traffic, "kernel": dom, "peak_source": src, "ms_per_launch": per_ms, "launches": n_,
+                 "voxels_per_launch": vox_per_launch, "hbm_gbs_alg": gbs, "tensor_tflops_alg": tfs,
+                 "profiled_wave_s": prof_sec,
+                 "share_of_step": {k_: prof[k_][0] / max(1e-9, sum(v[0] for v in prof.values())) for k_ in prof}})
+
+    # end to end through the C ABI with host buffers: the first wave again
+    e2e_ids = waves[0]
+    outs = [np.empty_like(reqs[i][0]) for i in e2e_ids]
+    e2e_s, _ = wave(e2e_ids, host=True, outs=outs)
+    e2e_s = max_over_ranks(e2e_s, ws)
+    e2e = {"value": ws * len(e2e_ids) / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": int(sum(5 * vox[i] + k * k * 8 for i in e2e_ids)),
+           "d2h_bytes_per_step": int(sum(4 * vox[i] for i in e2e_ids)),
+           "sample": f"wave 0 ({len(e2e_ids)} requests) from host buffers"}
+
+    # plain FP32, one request at a time, on a sample; its time per request is modelled as
+    # a + b * voxels * iterations (least squares over the sample) for the whole stream
+    S = min(R, args.fp32_requests)
+    t32, x32, it32 = [], [], []
+    ctx.icnnm_solve(Md[0], Kd[0], Vd, kd, L_out=Ld[0], prec="fp32", **SERVING_KW)
+    for i in range(S):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = ctx.icnnm_solve(Md[i], Kd[i], Vd, kd, L_out=Ld[i], prec="fp32", **SERVING_KW)
+        torch.cuda.synchronize()
+        t32.append(time.perf_counter() - t0)
+        x32.append(vox[i] * st["iters"])
+        it32.append(st["iters"])
+    A = np.stack([np.ones(S), np.array(x32, dtype=np.float64)], axis=1)
+    coef = np.linalg.lstsq(A, np.array(t32), rcond=None)[0]
+    model32 = np.maximum(coef[0] + coef[1] * vox[:R] * np.maximum(iters, 1), 1e-4)
+    cap32 = R / float(model32.sum())
+
+    def fcfs(arrivals, svc):
+        done, out = 0.0, []
+        for a, s_ in zip(arrivals, svc):
+            start = max(a, done)
+            done = start + s_
+            out.append(done - a)
+        return np.array(out) * 1e3
+    lat32_same = fcfs(arr, model32[:P])
+    arr32 = np.cumsum(rng.exponential(1.0 / (0.8 * cap32), size=P))
+    lat32_own = fcfs(arr32, model32[:P])
+    fp32 = {"value": cap32, "unit": "solves/s", "measured_requests": S, "measured_s": float(sum(t32)),
+            "measured_solves_per_s": S / float(sum(t32)), "mean_iters_sample": float(np.mean(it32)),
+            "model": "t = a + b * voxels * iterations fitted on the sample, applied to every request with its "
+                     "served iteration count", "a_s": float(coef[0]), "b_s_per_voxel_iter": float(coef[1]),
+            "latency_ms_same_arrivals": {"p50": float(np.percentile(lat32_same, 50)),
+                                         "p99": float(np.percentile(lat32_same, 99))},
+            "latency_ms_at_0.8x_own_capacity": {"p50": float(np.percentile(lat32_own, 50)),
+                                                "p99": float(np.percentile(lat32_own, 99))}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        spv, sample = serving_cpu_baseline(V)
+        per_req = spv * float(np.mean(vox[:R] * iters))
+        cpu = {"value": 1.0 / per_req, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample}
+    ctx.close()
+    pred = None
+    if not args.no_prediction:
+        pa = argparse.Namespace(**vars(args))
+        pa.steps, pa.warmup, pa.fp32_steps, pa.no_cpu_baseline, pa.no_learn = 3, 3, 1, True, True
+        pred = run_ours(pa, ws, rank, local, sub=True)
+    if rank != 0:
+        return
+    errs = [v["rel_err"] for v in rel.values() if v["rel_err"] is not None]
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"serving_poisson{R}_k7x7x3", "requests": R, "kdims": list(kd),
+                   "dims": "H, W uniform in 32..256 step 16, T uniform in 8..64",
+                   "masks": "30-70% uniform / last frames / every other frame / 16x16 holes",
+                   "stop": "relative residual <= 1e-3, checked every 10 iterations, at most 1000",
+                   "V": "FP64 oracle V of the 32 reference tensors (64x64x16) of the family",
+                   "step": f"a wave of ~{R // K} consecutive requests submitted at once and collected",
+                   "timing": "host wall clock around each wave (the server synchronises its stream every "
+                             "step); inputs and outputs resident in HBM",
+                   "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (the stream holds "
+                   f"{int(vox[:R].sum()) // 1000000} M voxels)"},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "mean": float(lat_ms.mean()), "requests": P, "arrival_rate_per_s": rate,
+                       "arrivals": "Poisson at 0.8x the measured served rate, the first requests of the stream"},
+        "rel_err_vs_oracle": max(errs) if errs else None,
+        "rel_err_vs_oracle_sample": rel,
+        "rel_err_note": "relative L2 error on 4096 seeded unobserved voxels per sampled request, against the "
+                        "stored FP64 oracle iterate of the same iteration count; observed entries are exact",
+        "observed_entries_exact": obs_ok,
+        "served": {"mean_iters": float(iters.mean()), "max_iters": int(iters.max()),
+                   "max_residual": float(resid.max()), "wave_seconds": times},
+        "fp32_plain": fp32, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": int(nall.value), "learn_V": learn, "prediction": pred,
+    }
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -730,14 +948,14 @@ def main():
         run_interpolation(args, local)
     elif args.workload == "batch":
         run_batch(args, local)
-    elif args.workload == "serving":
-        run_serving(args, local)
+    elif args.workload == "prediction":
+        run_ours(args, ws, rank, local)
     elif args.workload == "image":
         run_image(args, local)
     elif args.workload == "cnnm":
         run_cnnm(args, local)
     else:
-        run_ours(args, ws, rank, local)
+        run_serving_bench(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -49,13 +49,24 @@ typedef enum {
   ICNNM_ECUDA = 5,       /* a CUDA runtime/driver call or a kernel failed */
   ICNNM_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
   ICNNM_ECANCELED = 7,   /* the job was cancelled */
-  ICNNM_EUNSUPPORTED = 8 /* a valid request this build does not implement */
+  ICNNM_EUNSUPPORTED = 8, /* a valid request this build does not implement */
+  ICNNM_ENOCONV = 9      /* the FP64 Jacobi eigensolver reached its sweep cap with the
+                            off-diagonal norm still above 1e-10 of the matrix norm */
 } icnnm_status;
 
 typedef enum {
   ICNNM_FP32 = 0,        /* every product in FP32 on CUDA cores (the plain baseline) */
-  ICNNM_BF16 = 1         /* A_k(.)V and A_k^*(. V^T) on tcgen05 tensor cores: BF16
-                            operands, FP32 accumulation; L, norms and updates in FP32 */
+  ICNNM_BF16 = 1,        /* A_k(.)V and A_k^*(. V^T) on tcgen05 tensor cores: BF16
+                            operands, FP32 accumulation; L, norms and updates in FP32.
+                            With tol > 0 a job finishes in BF16X3 (where built for its
+                            kernel, else in FP32), since BF16 rounding floors the residual
+                            near 1e-3 */
+  ICNNM_BF16X3 = 2       /* as BF16, but the forward pass A_k(X)V splits X and V into hi +
+                            lo BF16 pairs (three products into one FP32 accumulator, about
+                            2^-16 relative) and keeps U as a hi + lo pair; the adjoint stays
+                            BF16. About 1e-6 from the FP64 oracle where BF16 is near 1e-3.
+                            Built where the split forward fits in shared memory (k up to
+                            about 150); EUNSUPPORTED otherwise */
 } icnnm_precision;
 
 typedef struct {
@@ -83,7 +94,10 @@ typedef struct {
   double residual;       /* ||Z - A_k(L)V||_F/(sqrt(k)||L||_F) at the last check */
   double objective;      /* ||A_k(L)V||_{2,1} of the returned L */
   double theta;          /* final penalty */
-  double seconds;        /* device time of the solve (CUDA events) */
+  double seconds;        /* blocking solves: device time of the solve (CUDA events);
+                            served jobs: seconds from admission to completion */
+  double latency;        /* served jobs: seconds from icnnm_submit to completion (queueing
+                            included); blocking solves: the same as seconds */
 } icnnm_stats;
 
 /* Fill *p with the defaults: lambda = INFINITY, theta0 = 0 (automatic), rho = 1.1,
@@ -119,6 +133,9 @@ const char* icnnm_last_error(icnnm_ctx* ctx);
  *   eig_out : k doubles, the eigenvalues (the ensemble convolution eigenvalues
  *             sigma_i of Definition 3), or NULL
  * EINVAL: b < 1, k < 1, k > 1024, a dim smaller than the kernel, non-finite entry.
+ * EUNSUPPORTED: more autocorrelation lags or a larger halo than the Gram kernel takes.
+ * ENOCONV: the eigensolver did not converge (V_out and eig_out are then unreliable).
+ * ETIMEOUT: a bounded grid barrier of the eigensolver expired.
  */
 icnnm_status icnnm_learn_V(icnnm_ctx* ctx, const int64_t kdims[3], int32_t b,
                            const icnnm_shape* shapes, const float* const* tensors,
@@ -165,7 +182,8 @@ icnnm_status icnnm_solve_batch(icnnm_ctx* ctx, int32_t n, const icnnm_shape* sha
  *   stats  : iters, objective = ||A_k(L)||_* of the result, theta = final penalty,
  *            seconds; residual is 0 (not computed). May be NULL.
  * EINVAL as for icnnm_solve; ENOMEM if the state (two k x m FP32 arrays plus O(m + k^2))
- * exceeds the budget; ETIMEOUT if a bounded grid barrier of the eigensolver expired.
+ * exceeds the budget; ETIMEOUT if a bounded grid barrier of the eigensolver expired;
+ * ENOCONV if the eigensolver failed to converge in any iteration.
  */
 icnnm_status icnnm_cnnm_solve(icnnm_ctx* ctx, const icnnm_shape* shape, const float* M,
                               const uint8_t* mask, const icnnm_params* params, float* L_out,
@@ -191,7 +209,8 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* ctx, const icnnm_shape* shape, const fl
  *   sigma_out: k doubles in V's column order (host or device), or NULL
  *   r_K, alpha_K, mu_K : host outputs, each may be NULL (alpha_K = mu_K = 0 when I is empty)
  * EINVAL: bad shape, V not orthonormal to 1e-6, non-finite L0, rank_tol outside (0, 1).
- * ETIMEOUT: a bounded grid barrier of the eigensolver expired.
+ * ETIMEOUT: a bounded grid barrier of the eigensolver expired. ENOCONV: the eigensolver
+ * that gives alpha_K did not converge.
  */
 icnnm_status icnnm_spectral_diagnostics(icnnm_ctx* ctx, const icnnm_shape* shape, const float* L0,
                                         const double* V, double rank_tol, double* sigma_out,
@@ -233,28 +252,55 @@ icnnm_status icnnm_cancel(icnnm_ctx* ctx, uint64_t job_id);
  */
 icnnm_status icnnm_profile_enable(icnnm_ctx* ctx, int32_t enable);
 icnnm_status icnnm_profile_read(icnnm_ctx* ctx, int32_t pass, double* ms_total, int64_t* launches);
+/* Voxels the launches of a pass processed since profiling was last enabled or disabled
+ * (the sum over its launches of the voxels of the jobs each launch stepped); pass ids as
+ * for icnnm_profile_read (-1: all passes). Counted whether or not timing is enabled. */
+icnnm_status icnnm_profile_voxels(icnnm_ctx* ctx, int32_t pass, int64_t* voxels);
+
+/*
+ * Device bytes of the state of one job of this shape in this precision (the amount the
+ * HBM budget is charged at admission; a BF16 job with a tolerance may take more for its
+ * FP32 finish). For callers that size a context's budget. V is not needed: kdims decide.
+ * EINVAL: bad shape or precision; EUNSUPPORTED: BF16 is not built for these kernel dims.
+ */
+icnnm_status icnnm_job_bytes(icnnm_ctx* ctx, const icnnm_shape* shape, int32_t prec, size_t* bytes);
+
+/*
+ * Check of the bounded device-side waits (no counterpart in the paper): one thread block
+ * waits, through the same bounded wait as the solve kernels, on a barrier that nothing
+ * completes, for limit_ns nanoseconds (1 ms .. 10 s). Returns ETIMEOUT once that wait has
+ * given up and the kernel has returned, which is what a solve reports when one of its
+ * waits expires; the context stays usable. EINVAL for a limit outside the range.
+ */
+icnnm_status icnnm_check_bounded_wait(icnnm_ctx* ctx, int64_t limit_ns);
 
 /*
  * Allocation-free learning of V (the paper has no counterpart; this is an interface for
- * callers, not a step of the method). It computes what icnnm_learn_V computes (same
- * Gram accumulation and FP64 eigensolver, summed in a different fixed order) but never
- * allocates: it calls no cudaMalloc/cudaFree, creates no context, and uses no
- * allocating library routine. It is meant for callers that cannot allocate device
- * memory: code that runs while a CUDA graph is being captured, code that lives inside a
- * framework that hands out device memory only from its own pool, and latency-critical
- * code that must avoid the device-wide synchronisation an allocation can cause.
+ * callers, not a step of the method). It computes what icnnm_learn_V computes (the same
+ * Gram accumulation and FP64 eigensolver, summed in a different fixed order, on one
+ * thread block) but never allocates: it calls no cudaMalloc/cudaFree, creates no
+ * context, and uses no allocating library routine. It is meant for callers that cannot
+ * allocate device memory themselves: code inside a framework that hands out device
+ * memory only from its own pool (so a cudaMalloc behind its back would break its
+ * accounting or fail against its reservation), and latency-critical code that must avoid
+ * the device-wide synchronisation a cudaMalloc/cudaFree can cause.
  *   kdims, b, shapes : as for icnnm_learn_V
- *   tensors          : b pointers to float tensors in DEVICE memory (current device)
- *   V_out, eig_out   : as for icnnm_learn_V (device or host; eig_out may be NULL)
+ *   tensors          : b pointers to float tensors in device memory of the current device
+ *   V_out, eig_out   : as for icnnm_learn_V (host memory, or device memory of the current
+ *                      device; eig_out may be NULL)
  *   cuda_stream      : cudaStream_t to run on (NULL: the legacy default stream)
  * All intermediates live in one fixed device array (about 2.1 MiB) that every GPU
  * loading this library keeps until the process exits. Limits: k <= 256,
  * (2k1-1)(2k2-1)(2k3-1) <= 4096, 1 <= b <= 256; larger requests return EINVAL and
- * icnnm_noalloc_last_error() says which limit. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make that first call before any
- * stream capture. Every call reuses the same array and leaves its contents behind, so
- * calls that may overlap on the GPU (other streams, other threads) race and must be
- * serialised by the caller. The call returns after the results are written.
+ * icnnm_noalloc_last_error() says which limit. A kernel whose Gram halo needs more than
+ * 220 KiB of shared memory (for example 256 x 1 x 1) returns EUNSUPPORTED. A pointer on
+ * another device returns EINVAL. ENOCONV: the eigensolver did not converge.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and so must not be the first CUDA call of a thread that has no current device. The
+ * call is blocking: it synchronises cuda_stream twice (after the finiteness check of the
+ * inputs and before returning). Every call reuses the same array and leaves its contents
+ * behind, so calls that may overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.
  */
 icnnm_status icnnm_learn_V_noalloc(const int64_t kdims[3], int32_t b, const icnnm_shape* shapes,
                                    const float* const* tensors, double* V_out, double* eig_out,

@@ -307,19 +307,22 @@ def icnnm_iteration(L, Y, theta, M, mask, V, kdims, lam=np.inf, Q=None):
 
 
 def icnnm_solve(M, mask, V, kdims, lam=np.inf, theta0=None, rho=1.1, theta_max=1e10,
-                max_iters=100, tol=0.0, check_every=1, return_history=False):
+                max_iters=100, tol=0.0, check_every=1, return_history=False, record_every=0):
     """ICNNM by ADMM (Sec. III-D) from the initial state of ``icnnm_init``.
 
     After each iteration theta <- min(rho*theta, theta_max) (a reading of "updated
     according to the instructions of ADMM"). If tol > 0, every ``check_every``
     iterations the run stops once ||Z - A_k(L)K||_F / (sqrt(k)||L||_F) <= tol.
-    Returns (L, stats) with stats = dict(iters, residual, objective, theta).
+    Returns (L, stats) with stats = dict(iters, residual, objective, theta); with
+    ``record_every`` > 0, stats["checkpoints"] maps every iteration count that is a
+    multiple of it to (L, residual) after that iteration (bookkeeping only).
     """
     V = np.asarray(V, dtype=np.float64)
     k = int(np.prod(kdims))
     L, Y, theta = icnnm_init(M, mask, V, kdims, theta0)
     Q = conv_matrix_times(L, V, kdims)
     hist = []
+    ckpt = {}
     it = 0
     resid = float("nan")
     for it in range(1, max_iters + 1):
@@ -327,6 +330,8 @@ def icnnm_solve(M, mask, V, kdims, lam=np.inf, theta0=None, rho=1.1, theta_max=1
         theta = min(rho * theta, theta_max)
         if return_history:
             hist.append(dict(objective=norm_21(Q), L=L.copy()))
+        if record_every and it % record_every == 0:
+            ckpt[it] = (L.copy(), primal_residual(Z, Q, L, k))
         if tol > 0 and it % check_every == 0:
             resid = primal_residual(Z, Q, L, k)
             if resid <= tol:
@@ -336,6 +341,8 @@ def icnnm_solve(M, mask, V, kdims, lam=np.inf, theta0=None, rho=1.1, theta_max=1
     stats = dict(iters=it, residual=resid, objective=norm_21(Q), theta=theta)
     if return_history:
         stats["history"] = hist
+    if record_every:
+        stats["checkpoints"] = ckpt
     return L, stats
 
 

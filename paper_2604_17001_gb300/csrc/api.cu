@@ -78,14 +78,14 @@ struct Job {
   long long m = 0;
   icnnm_params p{};
   VData* vd = nullptr;
-  std::vector<float> hM;        // host copies (serving) of the inputs
-  std::vector<uint8_t> hmask;
+  void* dstage = nullptr;       // serving: the inputs staged on the device at submit (M, then mask)
   const float* srcM = nullptr;  // caller's buffers (blocking solves)
   const uint8_t* srcmask = nullptr;
   bool src_dev = false;
   void* block = nullptr;        // one device allocation for all of the job's state
   size_t bytes = 0;
-  int run_prec = 0;             // arithmetic of the next iterations (BF16 jobs may finish in FP32)
+  int run_prec = 0;             // arithmetic of the next iterations (BF16 jobs with a tolerance
+                                //   finish in BF16X3 where it is built for their kernel, else FP32)
   void* block2 = nullptr;       // FP32 finish: widened U and the FP32 adjoint workspace
   size_t bytes2 = 0;
   double last_resid = INFINITY; // residual at the previous check (BF16 stall detection)
@@ -97,8 +97,9 @@ struct Job {
   bool converged = false;
   double resid = NAN;
   icnnm_stats stats{};
-  std::vector<float> result;    // serving: copied-out L
+  float* dres = nullptr;        // serving: the result L on the device until collected
   std::chrono::steady_clock::time_point t_admit;
+  std::chrono::steady_clock::time_point t_submit;
   std::atomic<bool> cancel{false};
 };
 
@@ -123,6 +124,7 @@ size_t job_bytes(int H, int W, int T, int k, int kc, int prec, int nrp, const Tc
     add((size_t)k * m * 4);  // G^T
   } else {
     add(m * kc * 2);     // U (bf16)
+    if (prec == ICNNM_BF16X3) add(m * kc * 2);   // the lo part of U
     b += tc_job_extra_bytes(H, W, T, *tg);
   }
   return b;
@@ -161,12 +163,32 @@ struct icnnm_ctx {
   std::vector<std::pair<int, size_t>> pending;   // (pass, index of the start event)
   double pass_ms[4] = {0, 0, 0, 0};
   long long pass_n[5] = {0, 0, 0, 0, 0};
+  long long pass_vox[5] = {0, 0, 0, 0, 0};
   // engine scratch
   // device job tables: slot 0 for the main list, slot 1 for a list stepped beside it
-  // (the BF16 jobs finishing in FP32), so that both can be live at once
+  // (the BF16 jobs finishing in FP32), so that both can be live at once. Uploads are
+  // stream-ordered, so a slot may be rewritten after the kernels that read it are enqueued.
   JobDev* dlist[2] = {nullptr, nullptr};
   int* dtile0[2] = {nullptr, nullptr};
   int list_cap[2] = {0, 0};
+  // device memory of jobs, job tables and scratch: a pool of this context with
+  // stream-ordered allocation and release (no device-wide synchronisation)
+  cudaMemPool_t pool = nullptr;
+  // validation and staging of served inputs, on the submitting thread's side
+  cudaStream_t sub_stream = nullptr;
+  std::mutex submu;
+  // pinned host staging of host-to-device copies (job tables, tensor maps) and of the
+  // scalars read back per step; an entry is reused once its last copy has completed
+  struct Pinned {
+    char* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+  };
+  std::vector<Pinned> ring;
+  size_t ring_next = 0;
+  JobScal* hscal = nullptr;      // pinned, hscal_cap entries
+  int hscal_cap = 0;
   // scratch of the Gram route to column norms (autocorrelation partials, k x k Gram)
   double* gscr = nullptr;
   size_t gscr_bytes = 0;
@@ -177,6 +199,49 @@ namespace {
 void set_err(icnnm_ctx* c, const std::string& s) {
   std::lock_guard<std::mutex> g(c->err_mu);
   c->last_err = s;
+}
+
+// Stream-ordered device memory from the context's pool.
+void* dalloc_async(icnnm_ctx* c, size_t bytes, cudaStream_t st) {
+  void* p = nullptr;
+  CK(cudaMallocFromPoolAsync(&p, std::max<size_t>(bytes, 256), c->pool, st));
+  return p;
+}
+void dfree_async(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+// A pinned host buffer of at least n bytes for one host-to-device copy on c->stream:
+// the caller fills it, enqueues the copy and calls pinned_done. The ring entry is reused
+// only after that copy has completed (usually long before), so no stream sync is needed.
+icnnm_ctx::Pinned& pinned_take(icnnm_ctx* c, size_t n) {
+  if (c->ring.empty()) c->ring.resize(32);
+  icnnm_ctx::Pinned& e = c->ring[c->ring_next++ % c->ring.size()];
+  if (e.pending) {
+    CK(cudaEventSynchronize(e.ev));
+    e.pending = false;
+  }
+  if (!e.ev) CK(cudaEventCreateWithFlags(&e.ev, cudaEventDisableTiming));
+  if (e.cap < n) {
+    if (e.p) CK(cudaFreeHost(e.p));
+    e.p = nullptr;
+    e.cap = 0;
+    const size_t cap = std::max<size_t>(n, 64 << 10);
+    CK(cudaHostAlloc((void**)&e.p, cap, cudaHostAllocDefault));
+    e.cap = cap;
+  }
+  return e;
+}
+void pinned_done(icnnm_ctx* c, icnnm_ctx::Pinned& e) {
+  CK(cudaEventRecord(e.ev, c->stream));
+  e.pending = true;
+}
+// Host-to-device copy of n bytes through the pinned ring (stream-ordered on c->stream).
+void h2d_staged(icnnm_ctx* c, void* dst, const void* src, size_t n) {
+  icnnm_ctx::Pinned& e = pinned_take(c, n);
+  memcpy(e.p, src, n);
+  CK(cudaMemcpyAsync(dst, e.p, n, cudaMemcpyHostToDevice, c->stream));
+  pinned_done(c, e);
 }
 
 // Diagnostics: bracket a pass with events when profiling, and count launches.
@@ -193,9 +258,11 @@ struct PassScope {
   icnnm_ctx* c;
   int pass;
   size_t idx = 0;
-  PassScope(icnnm_ctx* c_, int pass_, int nkernels) : c(c_), pass(pass_) {
+  PassScope(icnnm_ctx* c_, int pass_, int nkernels, long long nvox = 0) : c(c_), pass(pass_) {
     c->pass_n[pass] += nkernels;
     c->pass_n[4] += nkernels;
+    c->pass_vox[pass] += nvox;
+    c->pass_vox[4] += nvox;
     if (c->prof) {
       idx = c->evnext;
       CK(cudaEventRecord(pool_event(c), c->stream));
@@ -253,7 +320,7 @@ void validate_params(const icnnm_params& p) {
   if (p.max_iters < 1) fail(ICNNM_EINVAL, "max_iters must be >= 1");
   if (!(p.tol >= 0) || !isfinite(p.tol)) fail(ICNNM_EINVAL, "tol must be finite and >= 0");
   if (p.check_every < 1) fail(ICNNM_EINVAL, "check_every must be >= 1");
-  if (p.prec != ICNNM_FP32 && p.prec != ICNNM_BF16) fail(ICNNM_EINVAL, "unknown precision");
+  if (p.prec != ICNNM_FP32 && p.prec != ICNNM_BF16 && p.prec != ICNNM_BF16X3) fail(ICNNM_EINVAL, "unknown precision");
   if (!isfinite(p.theta0) && p.theta0 > 0) fail(ICNNM_EINVAL, "theta0 must be finite");
 }
 
@@ -311,12 +378,14 @@ VData* get_vdata(icnnm_ctx* c, const double* V, int k1, int k2, int k3, int prec
 
 void ensure_tc(VData* vd, int prec) {
   const int k1 = vd->k1, k2 = vd->k2, k3 = vd->k3;
-  if (prec == ICNNM_BF16 && !vd->tc_ready) {
+  if (prec != ICNNM_FP32 && !vd->tc_ready) {
     std::string why;
     if (!tc_supported(k1, k2, k3, &why)) fail(ICNNM_EUNSUPPORTED, "BF16 path: " + why);
     CK(tc_build_vdata(vd->V64.data(), k1, k2, k3, vd->kc, &vd->tc));
     vd->tc_ready = true;
   }
+  if (prec == ICNNM_BF16X3 && !vd->tc.g.split_ok)
+    fail(ICNNM_EUNSUPPORTED, "BF16X3: the split forward pass does not fit in shared memory for this kernel");
 }
 
 // Engine ---------------------------------------------------------------------------
@@ -327,7 +396,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   j.bytes = job_bytes(j.H, j.W, j.T, k, kc, j.p.prec, nrp, &vd->tc.g);
   j.run_prec = j.p.prec;
   if (c->used + j.bytes > c->budget) fail(ICNNM_ENOMEM, "job state exceeds the HBM budget");
-  CK(cudaMalloc(&j.block, j.bytes));
+  j.block = dalloc_async(c, j.bytes, c->stream);
   c->used += j.bytes;
   char* b = static_cast<char*>(j.block);
   size_t off = 0;
@@ -348,7 +417,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   d.part = (float*)take((size_t)d.ntiles * PROW * kc * 4);
   d.rpart = (float*)take((size_t)d.ntiles * nrp * 4);
   d.lpart = (float*)take((size_t)d.ntiles * 4);
-  d.nlp = j.p.prec == ICNNM_FP32 ? d.ntiles : (int)((m + 1023) / 1024);
+  d.nlp = j.p.prec == ICNNM_FP32 ? d.ntiles : (int)((m + 1023) / 1024);   // gather partials
   d.colseg = (double*)take((size_t)NSEG * kc * 8);
   d.s = (float*)take(kc * 4);
   d.D = (float*)take(kc * 4);
@@ -357,58 +426,88 @@ void alloc_job(icnnm_ctx* c, Job& j) {
     d.G = (float*)take((size_t)k * m * 4);
   } else {
     d.U = take(m * kc * 2);
-    CK(tc_carve_job(&d, vd->tc, b, off, j.bytes));
+    void* ulo = j.p.prec == ICNNM_BF16X3 ? take(m * kc * 2) : nullptr;
+    icnnm_ctx::Pinned& e = pinned_take(c, tc_tmap_bytes());
+    CK(tc_carve_job(&d, vd->tc, b, off, j.bytes, e.p, c->stream));
+    pinned_done(c, e);
+    if (ulo) {
+      icnnm_ctx::Pinned& e2 = pinned_take(c, tc_tmap_bytes());
+      CK(tc_attach_ulo(&d, vd->tc, ulo, e2.p, c->stream));
+      pinned_done(c, e2);
+      CK(cudaMemsetAsync(ulo, 0, m * kc * 2, c->stream));
+    }
   }
   CK(cudaMemsetAsync(d.sc, 0, sizeof(JobScal), c->stream));
   CK(cudaMemsetAsync(d.U, 0, (size_t)m * kc * (j.p.prec == ICNNM_FP32 ? 4 : 2), c->stream));
   CK(cudaMemsetAsync(d.part, 0, (size_t)d.ntiles * PROW * kc * 4, c->stream));
   CK(cudaMemsetAsync(d.rpart, 0, (size_t)d.ntiles * nrp * 4, c->stream));
-  if (j.p.prec == ICNNM_BF16) CK(cudaMemsetAsync(d.G, 0, (size_t)m * 4, c->stream));
-  // inputs
-  const float* srcM = j.srcM ? j.srcM : j.hM.data();
-  const uint8_t* srcK = j.srcmask ? j.srcmask : j.hmask.data();
-  CK(cudaMemcpyAsync((void*)d.M, srcM, m * 4, cudaMemcpyDefault, c->stream));
-  CK(cudaMemcpyAsync((void*)d.mask, srcK, m, cudaMemcpyDefault, c->stream));
+  if (j.p.prec != ICNNM_FP32) CK(cudaMemsetAsync(d.G, 0, (size_t)m * 4, c->stream));
+  // inputs: staged on the device at submit (serving), else the caller's buffers
+  if (j.dstage) {
+    CK(cudaMemcpyAsync((void*)d.M, j.dstage, m * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync((void*)d.mask, static_cast<char*>(j.dstage) + m * 4, m, cudaMemcpyDeviceToDevice, c->stream));
+    dfree_async(j.dstage, c->stream);
+    j.dstage = nullptr;
+  } else {
+    CK(cudaMemcpyAsync((void*)d.M, j.srcM, m * 4, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync((void*)d.mask, j.srcmask, m, cudaMemcpyDefault, c->stream));
+  }
 }
 
+// Stream-ordered release of the job's device state (and of its staged inputs and
+// result, if any) on c->stream.
 void free_job(icnnm_ctx* c, Job& j) {
   if (j.block) {
-    cudaFree(j.block);
+    dfree_async(j.block, c->stream);
     c->used -= j.bytes;
     j.block = nullptr;
   }
   if (j.block2) {
-    cudaFree(j.block2);
+    dfree_async(j.block2, c->stream);
     c->used -= j.bytes2;
     j.block2 = nullptr;
   }
+  if (j.dstage) {
+    dfree_async(j.dstage, c->stream);
+    j.dstage = nullptr;
+  }
 }
 
-// Mixed-precision finish of a BF16 job with a residual tolerance. U is stored in BF16, so
-// the BF16 residual ||Z - A_k(L)V|| carries U's rounding (about 1e-3 relative) and stalls
-// near that level; a tolerance at or below it cannot be certified in BF16. When the BF16
-// residual is within 4x the tolerance or has stopped falling (less than 10% between
-// checks), the job continues on the FP32 path: U is widened exactly to FP32 (the state
-// the next iteration reads: U, L, X, theta and the column sums are unchanged) and the
-// remaining iterations and residual checks run in FP32. Returns false (the job stays in
-// BF16) when the extra state does not fit the budget.
-bool bf16_should_finish_fp32(const Job& j) {
+// Finish of a BF16 job with a residual tolerance. U is stored in BF16 and the forward
+// pass rounds its operands to BF16, so the BF16 residual ||Z - A_k(L)V|| carries a rounding
+// floor near 1e-3 relative; a tolerance at or below it cannot be certified in BF16. When
+// the BF16 residual is within 4x the tolerance or has stopped falling (less than 10%
+// between checks), the job continues in BF16X3 where that path is built for its kernel
+// (the forward with hi + lo operand pairs and U kept as a hi + lo pair: only the lo half of
+// U is added, zero, so the state the next iteration reads is unchanged), else in FP32 (U
+// widened exactly, the FP32 adjoint workspace added). Returns false (the job stays in BF16)
+// when the extra state does not fit the budget.
+bool bf16_should_finish(const Job& j) {
   return j.run_prec == ICNNM_BF16 && j.p.tol > 0 && (j.resid <= 4 * j.p.tol || j.resid > 0.9 * j.last_resid);
 }
 
-bool switch_to_fp32(icnnm_ctx* c, Job& j) {
+bool switch_to_finish(icnnm_ctx* c, Job& j) {
   const size_t m = (size_t)j.m, kc = (size_t)j.vd->kc, k = (size_t)j.vd->k;
-  const size_t ub = (m * kc * 4 + 255) / 256 * 256;
-  const size_t need = ub + k * m * 4;
+  const bool split = j.vd->tc.g.split_ok;
+  const size_t ub = (m * kc * (split ? 2 : 4) + 255) / 256 * 256;
+  const size_t need = split ? ub : ub + k * m * 4;
   if (c->used + need > c->budget) return false;
   void* b = nullptr;
-  if (cudaMalloc(&b, need) != cudaSuccess) {
+  if (cudaMallocFromPoolAsync(&b, need, c->pool, c->stream) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   c->used += need;
   j.block2 = b;
   j.bytes2 = need;
+  if (split) {
+    CK(cudaMemsetAsync(b, 0, m * kc * 2, c->stream));
+    icnnm_ctx::Pinned& e = pinned_take(c, tc_tmap_bytes());
+    CK(tc_attach_ulo(&j.dev, j.vd->tc, b, e.p, c->stream));
+    pinned_done(c, e);
+    j.run_prec = ICNNM_BF16X3;
+    return true;
+  }
   float* U32 = static_cast<float*>(b);
   CK(launch_widen_bf16(static_cast<const __nv_bfloat16*>(j.dev.U), U32, (long long)(m * kc), c->stream));
   j.dev.U = U32;
@@ -426,22 +525,29 @@ struct List {
 Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js, int slot = 0) {
   const int n = (int)js.size();
   if (n > c->list_cap[slot]) {
-    if (c->dlist[slot]) cudaFree(c->dlist[slot]);
-    if (c->dtile0[slot]) cudaFree(c->dtile0[slot]);
-    c->list_cap[slot] = std::max(n, 64);
-    CK(cudaMalloc(&c->dlist[slot], sizeof(JobDev) * c->list_cap[slot]));
-    CK(cudaMalloc(&c->dtile0[slot], sizeof(int) * (c->list_cap[slot] + 1)));
+    // stream-ordered: the old tables are released after the kernels that read them
+    dfree_async(c->dlist[slot], c->stream);
+    dfree_async(c->dtile0[slot], c->stream);
+    c->dlist[slot] = nullptr;
+    c->dtile0[slot] = nullptr;
+    const int cap = std::max(n, 2 * c->list_cap[slot]);
+    c->dlist[slot] = (JobDev*)dalloc_async(c, sizeof(JobDev) * std::max(cap, 64), c->stream);
+    c->dtile0[slot] = (int*)dalloc_async(c, sizeof(int) * (std::max(cap, 64) + 1), c->stream);
+    c->list_cap[slot] = std::max(cap, 64);
   }
-  std::vector<JobDev> hd(n);
-  std::vector<int> t0(n + 1, 0);
+  // one pinned staging buffer: the job table, then the tile prefix sums
+  const size_t tb = sizeof(JobDev) * n, pb = sizeof(int) * (n + 1);
+  icnnm_ctx::Pinned& e = pinned_take(c, tb + pb);
+  JobDev* hd = reinterpret_cast<JobDev*>(e.p);
+  int* t0 = reinterpret_cast<int*>(e.p + tb);
+  t0[0] = 0;
   for (int i = 0; i < n; ++i) {
     hd[i] = js[i]->dev;
     t0[i + 1] = t0[i] + js[i]->dev.ntiles;
   }
-  CK(cudaMemcpyAsync(c->dlist[slot], hd.data(), sizeof(JobDev) * n, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->dtile0[slot], t0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, c->stream));
-  // pageable sources: make sure the copies have consumed them before they go away
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(c->dlist[slot], hd, tb, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->dtile0[slot], t0, pb, cudaMemcpyHostToDevice, c->stream));
+  pinned_done(c, e);
   const VData* vd = js[0]->vd;
   Shared sh{};
   sh.k1 = vd->k1; sh.k2 = vd->k2; sh.k3 = vd->k3; sh.k = vd->k; sh.kc = vd->kc;
@@ -453,20 +559,24 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js, int slot = 0) {
   sh.job_tile0 = c->dtile0[slot];
   sh.total_tiles = t0[n];
   sh.max_vblk = 1;
-  for (int i = 0; i < n; ++i) sh.max_vblk = std::max(sh.max_vblk, (int)((js[i]->m + 1023) / 1024));
+  sh.nvox = 0;
+  for (int i = 0; i < n; ++i) {
+    sh.max_vblk = std::max(sh.max_vblk, (int)((js[i]->m + 1023) / 1024));
+    sh.nvox += js[i]->m;
+  }
   return sh;
 }
 
 void run_fwd(icnnm_ctx* c, const Shared& sh, int prec, int mode, const TcVData* tcv) {
   // the once-per-solve FP32 passes (theta0, objective) count as "other"
-  PassScope ps(c, mode == 0 || mode == 4 ? 3 : 0, 1);
+  PassScope ps(c, mode == 0 || mode == 4 ? 3 : 0, 1, sh.nvox);
   if (prec == ICNNM_FP32 || mode == 0 || mode == 4) CK(launch_fwd_fp32(sh, mode, c->stream));
-  else CK(tc_launch_fwd(sh, *tcv, mode, c->stream));
+  else CK(tc_launch_fwd(sh, *tcv, mode, c->stream, prec == ICNNM_BF16X3));
 }
 
 // Row groups of the column partials written by the update pass (0 = one per tile).
 int fwd_slots(const Shared& sh, int prec, const TcVData* tcv) {
-  return prec == ICNNM_BF16 ? tc_fwd_slots(sh, *tcv) : 0;
+  return prec != ICNNM_FP32 ? tc_fwd_slots(sh, *tcv) : 0;
 }
 
 // Column norms ||A_k(L) v_c||^2 of each job's current L into its colseg through the
@@ -484,11 +594,10 @@ bool gram_colnorms(icnnm_ctx* c, const std::vector<Job*>& js) {
   const int nblk = 2 * sms;
   const size_t need = sizeof(double) * ((size_t)nblk * nlag + (size_t)k * k);
   if (need > c->gscr_bytes) {
-    CK(cudaStreamSynchronize(c->stream));
-    if (c->gscr) cudaFree(c->gscr);
+    dfree_async(c->gscr, c->stream);    // stream-ordered: after its last use
     c->gscr = nullptr;
     c->gscr_bytes = 0;
-    CK(cudaMalloc(&c->gscr, need));
+    c->gscr = (double*)dalloc_async(c, need, c->stream);
     c->gscr_bytes = need;
   }
   double* part = c->gscr;
@@ -539,7 +648,7 @@ void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
   colnorms_once(c, js, 0);
   OTHER(1, launch_theta0(sh, js[0]->p.theta0, c->stream));
   OTHER(1, launch_scale_X(sh, c->stream));
-  if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
+  if (prec != ICNNM_FP32) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream, prec == ICNNM_BF16X3));
   run_fwd(c, sh, prec, 2, tcv);
   OTHER(1, launch_reduce_cols(sh, 0, fwd_slots(sh, prec, tcv), c->stream));
 }
@@ -547,23 +656,23 @@ void engine_init(icnnm_ctx* c, const std::vector<Job*>& js) {
 // One ADMM iteration for every job of the list. `check` (per list) adds the residual.
 void engine_step(icnnm_ctx* c, const Shared& sh, int prec, const TcVData* tcv, bool check) {
   OTHER(1, launch_scalars(sh, c->stream));
-  if (prec == ICNNM_BF16) OTHER(1, tc_launch_build_B2(sh, *tcv, c->stream));
+  if (prec != ICNNM_FP32) OTHER(1, tc_launch_build_B2(sh, *tcv, c->stream));
   {
-    PassScope ps(c, 1, 1);
+    PassScope ps(c, 1, 1, sh.nvox);
     if (prec == ICNNM_FP32) CK(launch_adj_gemm_fp32(sh, c->stream));
     else CK(tc_launch_adj(sh, *tcv, c->stream));
   }
   {
-    PassScope ps(c, 2, 1);
+    PassScope ps(c, 2, 1, sh.nvox);
     if (prec == ICNNM_FP32) CK(launch_gather_fp32(sh, c->stream));
     else CK(tc_launch_gather(sh, *tcv, c->stream));
   }
   if (check) {
-    if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/1, c->stream));
+    if (prec != ICNNM_FP32) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/1, c->stream, prec == ICNNM_BF16X3));
     run_fwd(c, sh, prec, 3, tcv);
     OTHER(1, launch_finish(sh, 1, c->stream));
   }
-  if (prec == ICNNM_BF16) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream));
+  if (prec != ICNNM_FP32) OTHER(1, tc_launch_prepare_X(sh, *tcv, /*from_L=*/0, c->stream, prec == ICNNM_BF16X3));
   run_fwd(c, sh, prec, 1, tcv);
   OTHER(1, launch_reduce_cols(sh, 1, fwd_slots(sh, prec, tcv), c->stream));
 }
@@ -585,6 +694,22 @@ JobScal read_scal(Job& j, cudaStream_t st) {
   return s;
 }
 
+// Enqueue the copy of every listed job's scalars into the pinned array c->hscal (entry
+// i for js[i]); they are valid after the next synchronisation of c->stream.
+void enqueue_scals(icnnm_ctx* c, const std::vector<Job*>& js) {
+  if ((int)js.size() > c->hscal_cap) {
+    CK(cudaStreamSynchronize(c->stream));        // the old array may still be a copy target
+    if (c->hscal) CK(cudaFreeHost(c->hscal));
+    c->hscal = nullptr;
+    c->hscal_cap = 0;
+    const int cap = std::max<int>((int)js.size(), 256);
+    CK(cudaHostAlloc((void**)&c->hscal, sizeof(JobScal) * cap, cudaHostAllocDefault));
+    c->hscal_cap = cap;
+  }
+  for (size_t i = 0; i < js.size(); ++i)
+    CK(cudaMemcpyAsync(&c->hscal[i], js[i]->dev.sc, sizeof(JobScal), cudaMemcpyDeviceToHost, c->stream));
+}
+
 double resid_of(const JobScal& s, int k) {
   return sqrt(s.rsq) / (sqrt((double)k) * std::max(sqrt(s.lsq), 1e-300));
 }
@@ -601,7 +726,7 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   engine_init(c, js);
   std::vector<Job*> live = js;
   Shared sh = upload_list(c, live);
-  std::vector<Job*> live32;      // BF16 jobs finishing in FP32 (see switch_to_fp32)
+  std::vector<Job*> live32;      // BF16 jobs in their finish (see switch_to_finish)
   Shared sh32{};
   int it = 0;
   const icnnm_params& p = js[0]->p;
@@ -611,7 +736,7 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   constexpr int GRAPH_ITERS = 25;
   const bool graphs = c->stream != cudaStreamLegacy && c->stream != nullptr;
   cudaGraphExec_t gexec = nullptr;
-  long long graph_counts[5] = {0, 0, 0, 0, 0};
+  long long graph_counts[5] = {0, 0, 0, 0, 0}, graph_vox[5] = {0, 0, 0, 0, 0};
   auto is_check = [&](int i) { return i >= p.max_iters || (p.tol > 0 && i % p.check_every == 0); };
   auto plain_run = [&](int from) {          // plain iterations from..from+n-1
     int n = 0;
@@ -621,8 +746,8 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   while (!live.empty()) {
     if (graphs && !c->prof && it >= 1 && live32.empty() && plain_run(it + 1) >= GRAPH_ITERS) {
       if (!gexec) {
-        long long before[5];
-        for (int i = 0; i < 5; ++i) before[i] = c->pass_n[i];
+        long long before[5], vbefore[5];
+        for (int i = 0; i < 5; ++i) before[i] = c->pass_n[i], vbefore[i] = c->pass_vox[i];
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         try {
@@ -640,10 +765,12 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
         for (int i = 0; i < 5; ++i) {
           graph_counts[i] = c->pass_n[i] - before[i];
           c->pass_n[i] = before[i];
+          graph_vox[i] = c->pass_vox[i] - vbefore[i];
+          c->pass_vox[i] = vbefore[i];
         }
       }
       CK(cudaGraphLaunch(gexec, c->stream));
-      for (int i = 0; i < 5; ++i) c->pass_n[i] += graph_counts[i];
+      for (int i = 0; i < 5; ++i) c->pass_n[i] += graph_counts[i], c->pass_vox[i] += graph_vox[i];
       it += GRAPH_ITERS;
       continue;
     }
@@ -651,19 +778,27 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
     const bool last = it >= p.max_iters;
     const bool check = is_check(it);
     engine_step(c, sh, prec, tcv, check);
-    if (!live32.empty()) engine_step(c, sh32, ICNNM_FP32, nullptr, check);
+    if (!live32.empty()) {
+      const int fp = live32[0]->run_prec;
+      engine_step(c, sh32, fp, fp == ICNNM_FP32 ? nullptr : &js[0]->vd->tc, check);
+    }
     if (check) {
       std::vector<Job*> keep, keep32;
       bool moved = false;
+      std::vector<Job*> all(live);
+      all.insert(all.end(), live32.begin(), live32.end());
+      enqueue_scals(c, all);
+      CK(cudaStreamSynchronize(c->stream));
+      size_t ai = 0;
       for (int grp = 0; grp < 2; ++grp)
         for (Job* j : grp == 0 ? live : live32) {
-          JobScal s = read_scal(*j, c->stream);
+          const JobScal s = c->hscal[ai++];
           j->resid = resid_of(s, k);
           j->iters = it;
           const bool conv = p.tol > 0 && j->resid <= p.tol && it % p.check_every == 0;
           if (conv || last) {
             j->converged = conv;
-          } else if (grp == 0 && bf16_should_finish_fp32(*j) && switch_to_fp32(c, *j)) {
+          } else if (grp == 0 && bf16_should_finish(*j) && switch_to_finish(c, *j)) {
             keep32.push_back(j);
             moved = true;
           } else {
@@ -683,14 +818,15 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
       if (live.empty() && !live32.empty()) {   // only FP32 finishers left: they become the main list
         live.swap(live32);
         std::swap(sh, sh32);
-        prec = ICNNM_FP32;
-        tcv = nullptr;
+        prec = live[0]->run_prec;
+        tcv = prec == ICNNM_FP32 ? nullptr : &js[0]->vd->tc;
       }
     }
   }
   if (gexec) cudaGraphExecDestroy(gexec);
   engine_objective(c, js);
   CK(cudaEventRecord(e1, c->stream));
+  enqueue_scals(c, js);
   CK(cudaStreamSynchronize(c->stream));
   flush_prof(c);
   float ms = 0;
@@ -699,20 +835,21 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   cudaEventDestroy(e1);
   for (size_t i = 0; i < js.size(); ++i) {
     Job& j = *js[i];
-    JobScal s = read_scal(j, c->stream);
+    const JobScal s = c->hscal[i];
     if (s.status) fail(ICNNM_ETIMEOUT, "a bounded device-side wait expired");
     j.stats.iters = j.iters;
     j.stats.residual = j.resid;
     j.stats.objective = s.objective;
     j.stats.theta = s.theta;
     j.stats.seconds = ms * 1e-3;
+    j.stats.latency = ms * 1e-3;
     if (outs && outs[i]) CK(cudaMemcpyAsync(outs[i], j.dev.L, j.m * 4, cudaMemcpyDefault, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
 }
 
 void prepare_job(icnnm_ctx* c, Job& j, const icnnm_shape* shape, const float* M, const uint8_t* mask,
-                 const double* V, const icnnm_params& p, bool copy_host) {
+                 const double* V, const icnnm_params& p) {
   int H, W, T, k1, k2, k3;
   validate_shape(shape, H, W, T, k1, k2, k3);
   validate_params(p);
@@ -726,30 +863,30 @@ void prepare_job(icnnm_ctx* c, Job& j, const icnnm_shape* shape, const float* M,
   const uint8_t* dK = mask;
   float* tM = nullptr;
   uint8_t* tK = nullptr;
-  if (!mdev) { CK(cudaMalloc(&tM, j.m * 4)); CK(cudaMemcpy(tM, M, j.m * 4, cudaMemcpyHostToDevice)); dM = tM; }
-  if (!kdev) { CK(cudaMalloc(&tK, j.m)); CK(cudaMemcpy(tK, mask, j.m, cudaMemcpyHostToDevice)); dK = tK; }
-  int* d2;
-  CK(cudaMalloc(&d2, 8));
-  CK(cudaMemset(d2, 0, 8));
+  if (!mdev) {
+    tM = (float*)dalloc_async(c, j.m * 4, c->stream);
+    CK(cudaMemcpyAsync(tM, M, j.m * 4, cudaMemcpyHostToDevice, c->stream));
+    dM = tM;
+  }
+  if (!kdev) {
+    tK = (uint8_t*)dalloc_async(c, j.m, c->stream);
+    CK(cudaMemcpyAsync(tK, mask, j.m, cudaMemcpyHostToDevice, c->stream));
+    dK = tK;
+  }
+  int* d2 = (int*)dalloc_async(c, 8, c->stream);
+  CK(cudaMemsetAsync(d2, 0, 8, c->stream));
   CK(check_observed(dM, dK, j.m, d2, c->stream));
   int h2[2];
   CK(cudaMemcpyAsync(h2, d2, 8, cudaMemcpyDeviceToHost, c->stream));
+  dfree_async(d2, c->stream);
+  dfree_async(tM, c->stream);
+  dfree_async(tK, c->stream);
   CK(cudaStreamSynchronize(c->stream));
-  cudaFree(d2);
-  if (tM) cudaFree(tM);
-  if (tK) cudaFree(tK);
   if (h2[1]) fail(ICNNM_EINVAL, "mask entries must be 0/1 and M must be finite on Omega");
   if (h2[0] == 0) fail(ICNNM_EINVAL, "Omega is empty");
   ensure_tc(j.vd, p.prec);
-  if (copy_host) {
-    j.hM.resize(j.m);
-    j.hmask.resize(j.m);
-    CK(cudaMemcpy(j.hM.data(), M, j.m * 4, cudaMemcpyDefault));
-    CK(cudaMemcpy(j.hmask.data(), mask, j.m, cudaMemcpyDefault));
-  } else {
-    j.srcM = M;
-    j.srcmask = mask;
-  }
+  j.srcM = M;
+  j.srcmask = mask;
 }
 
 icnnm_params defaults() {
@@ -759,33 +896,61 @@ icnnm_params defaults() {
 }
 
 // Serving thread ---------------------------------------------------------------------
+// One step: admit queued jobs in FIFO order while their state fits the budget, initialise
+// the admitted ones, run one iteration of every running job (grouped by V and by the
+// arithmetic of their next iteration, each group as a plain and a check list), read the
+// scalars of the checked jobs back with one stream synchronisation, then retire the jobs
+// that converged, hit their cap or were cancelled: their objective is computed, L is kept
+// on the device until the caller collects it, and their state is released (stream-ordered).
 void server_loop(icnnm_ctx* c) {
-  CK(cudaSetDevice(c->device));
+  if (cudaSetDevice(c->device) != cudaSuccess) return;
   while (true) {
     std::vector<std::shared_ptr<Job>> admitted;
     {
       std::unique_lock<std::mutex> lk(c->qmu);
       c->qcv.wait(lk, [&] { return c->stop || !c->queue.empty() || !c->active.empty(); });
       if (c->stop && c->queue.empty() && c->active.empty()) return;
-      // admit in FIFO order while the state fits the budget and the group matches
+      // FIFO admission while the state fits the budget; jobs of other groups (V,
+      // precision) are admitted too and stepped as lists of their own
+      size_t planned = c->used;
       while (!c->queue.empty()) {
         auto j = c->queue.front();
-        if (j->cancel) { j->phase = CANCELED; j->st = ICNNM_ECANCELED; c->queue.pop_front(); continue; }
-        if (!c->active.empty()) {
-          const Job& a = *c->active[0];
-          if (a.vd != j->vd || a.p.prec != j->p.prec) break;
+        if (j->cancel) {
+          c->queue.pop_front();
+          if (j->dstage) { dfree_async(j->dstage, c->stream); j->dstage = nullptr; }
+          j->phase = CANCELED;
+          j->st = ICNNM_ECANCELED;
+          continue;
         }
         const int nrp = std::max(fwd_fp32_nrp(j->vd->k), tc_nrp(j->vd->k));
         const size_t need = job_bytes(j->H, j->W, j->T, j->vd->k, j->vd->kc, j->p.prec, nrp, &j->vd->tc.g);
-        if (c->used + need > c->budget) break;
+        if (planned + need > c->budget) break;
+        planned += need;
         c->queue.pop_front();
         admitted.push_back(j);
         c->active.push_back(j);
         j->phase = ADMITTED;
       }
     }
+    c->qcv.notify_all();
     std::lock_guard<std::recursive_mutex> g(c->mu);
     try {
+      // groups of jobs that can share a launch list: same V and same arithmetic
+      auto groups = [](const std::vector<Job*>& js, bool by_run_prec) {
+        std::vector<std::vector<Job*>> out;
+        for (Job* j : js) {
+          const int pr = by_run_prec ? j->run_prec : j->p.prec;
+          bool put = false;
+          for (auto& gr : out)
+            if (gr[0]->vd == j->vd && (by_run_prec ? gr[0]->run_prec : gr[0]->p.prec) == pr) {
+              gr.push_back(j);
+              put = true;
+              break;
+            }
+          if (!put) out.push_back({j});
+        }
+        return out;
+      };
       std::vector<Job*> fresh;
       for (auto& j : admitted) {
         try {
@@ -793,73 +958,89 @@ void server_loop(icnnm_ctx* c) {
           j->t_admit = std::chrono::steady_clock::now();
           fresh.push_back(j.get());
         } catch (StatusFail& f) {
+          std::lock_guard<std::mutex> lk(c->qmu);
+          free_job(c, *j);
           j->phase = FAILED; j->st = f.st; j->err = f.msg;
         }
       }
-      if (!fresh.empty()) {
-        engine_init(c, fresh);
-        for (Job* j : fresh) j->phase = RUNNING;
-      }
+      for (auto& gr : groups(fresh, false)) engine_init(c, gr);
+      for (Job* j : fresh) j->phase = RUNNING;
       // one iteration for every running job
-      std::vector<Job*> run, chk;
+      std::vector<Job*> run;
       for (auto& j : c->active)
         if (j->phase == RUNNING) run.push_back(j.get());
-      if (!run.empty()) {
-        // the jobs step in groups of one arithmetic (BF16 jobs that finish in FP32 move)
-        for (int prec : {(int)ICNNM_BF16, (int)ICNNM_FP32}) {
-          std::vector<Job*> plain, chk1;
-          for (Job* j : run) {
-            if (j->run_prec != prec) continue;
-            const int it = j->iters + 1;
-            const bool check = it >= j->p.max_iters || (j->p.tol > 0 && it % j->p.check_every == 0) || j->cancel;
-            (check ? chk1 : plain).push_back(j);
-          }
-          const TcVData* tcv = prec == ICNNM_BF16 ? &run[0]->vd->tc : nullptr;
-          if (!plain.empty()) engine_step(c, upload_list(c, plain), prec, tcv, false);
-          if (!chk1.empty()) engine_step(c, upload_list(c, chk1), prec, tcv, true);
-          chk.insert(chk.end(), chk1.begin(), chk1.end());
+      std::vector<Job*> chk;
+      for (auto& gr : groups(run, true)) {
+        const int prec = gr[0]->run_prec;
+        std::vector<Job*> plain, chk1;
+        for (Job* j : gr) {
+          const int it = j->iters + 1;
+          const bool check = it >= j->p.max_iters || (j->p.tol > 0 && it % j->p.check_every == 0) || j->cancel;
+          (check ? chk1 : plain).push_back(j);
         }
-        for (Job* j : run) j->iters += 1;
-        std::vector<Job*> fin;
-        for (Job* j : chk) {
-          JobScal s = read_scal(*j, c->stream);
-          j->resid = resid_of(s, j->vd->k);
-          const bool conv = j->p.tol > 0 && j->resid <= j->p.tol && j->iters % j->p.check_every == 0;
-          if (conv || j->iters >= j->p.max_iters || j->cancel) {
-            j->converged = conv;
-            fin.push_back(j);
-          } else if (bf16_should_finish_fp32(*j)) {
-            switch_to_fp32(c, *j);
-          }
-          j->last_resid = j->resid;
+        const TcVData* tcv = prec != ICNNM_FP32 ? &gr[0]->vd->tc : nullptr;
+        if (!plain.empty()) engine_step(c, upload_list(c, plain), prec, tcv, false);
+        if (!chk1.empty()) engine_step(c, upload_list(c, chk1), prec, tcv, true);
+        chk.insert(chk.end(), chk1.begin(), chk1.end());
+      }
+      for (Job* j : run) j->iters += 1;
+      enqueue_scals(c, chk);
+      CK(cudaStreamSynchronize(c->stream));          // the one synchronisation of a step
+      flush_prof(c);
+      std::vector<Job*> fin;
+      for (size_t i = 0; i < chk.size(); ++i) {
+        Job* j = chk[i];
+        const JobScal& sc = c->hscal[i];
+        j->resid = resid_of(sc, j->vd->k);
+        const bool conv = j->p.tol > 0 && j->resid <= j->p.tol && j->iters % j->p.check_every == 0;
+        if (conv || j->iters >= j->p.max_iters || j->cancel || sc.status) {
+          j->converged = conv;
+          fin.push_back(j);
+        } else if (bf16_should_finish(*j)) {
+          switch_to_finish(c, *j);
         }
-        if (!fin.empty()) {
-          engine_objective(c, fin);
-          for (Job* j : fin) {
-            JobScal s = read_scal(*j, c->stream);
-            j->result.resize(j->m);
-            CK(cudaMemcpyAsync(j->result.data(), j->dev.L, j->m * 4, cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            j->stats.iters = j->iters;
-            j->stats.residual = j->resid;
-            j->stats.objective = s.objective;
-            j->stats.theta = s.theta;
-            j->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - j->t_admit).count();
-            free_job(c, *j);
-            if (s.status) { j->st = ICNNM_ETIMEOUT; j->phase = FAILED; }
-            else if (j->cancel) { j->st = ICNNM_ECANCELED; j->phase = CANCELED; }
-            else j->phase = DONE;
-          }
+        j->last_resid = j->resid;
+      }
+      if (!fin.empty()) {
+        for (auto& gr : groups(fin, false)) engine_objective(c, gr);
+        for (Job* j : fin) {
+          j->dres = (float*)dalloc_async(c, (size_t)j->m * 4, c->stream);
+          CK(cudaMemcpyAsync(j->dres, j->dev.L, j->m * 4, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        enqueue_scals(c, fin);
+        for (Job* j : fin) free_job(c, *j);
+        CK(cudaStreamSynchronize(c->stream));
+        const auto now = std::chrono::steady_clock::now();
+        std::lock_guard<std::mutex> lk(c->qmu);
+        for (size_t i = 0; i < fin.size(); ++i) {
+          Job* j = fin[i];
+          const JobScal& sc = c->hscal[i];
+          j->stats.iters = j->iters;
+          j->stats.residual = j->resid;
+          j->stats.objective = sc.objective;
+          j->stats.theta = sc.theta;
+          j->stats.seconds = std::chrono::duration<double>(now - j->t_admit).count();
+          j->stats.latency = std::chrono::duration<double>(now - j->t_submit).count();
+          if (sc.status) { j->st = ICNNM_ETIMEOUT; j->phase = FAILED; }
+          else if (j->cancel) { j->st = ICNNM_ECANCELED; j->phase = CANCELED; }
+          else j->phase = DONE;
+          if (j->phase != DONE) { dfree_async(j->dres, c->stream); j->dres = nullptr; }
         }
       }
     } catch (CudaFail& f) {
       report(c, f);
       std::lock_guard<std::mutex> lk(c->qmu);
-      for (auto& j : c->active) { free_job(c, *j); j->phase = FAILED; j->st = ICNNM_ECUDA; }
+      for (auto& j : c->active) {
+        free_job(c, *j);
+        if (j->phase < DONE) { j->phase = FAILED; j->st = ICNNM_ECUDA; }
+      }
     } catch (StatusFail& f) {
       report(c, f);
       std::lock_guard<std::mutex> lk(c->qmu);
-      for (auto& j : c->active) { free_job(c, *j); j->phase = FAILED; j->st = f.st; }
+      for (auto& j : c->active) {
+        free_job(c, *j);
+        if (j->phase < DONE) { j->phase = FAILED; j->st = f.st; j->err = f.msg; }
+      }
     }
     {
       std::lock_guard<std::mutex> lk(c->qmu);
@@ -869,6 +1050,47 @@ void server_loop(icnnm_ctx* c) {
     }
     c->qcv.notify_all();
   }
+}
+
+// Submit-side preparation of a served job: validation of the shape and parameters on the
+// host, V looked up (or uploaded) under the engine's mutex, and the inputs copied into a
+// device staging buffer on the submitting side's stream, where they are checked (mask
+// 0/1, M finite on Omega, Omega non-empty) before the job is queued.
+void prepare_submit(icnnm_ctx* c, Job& j, const icnnm_shape* shape, const float* M, const uint8_t* mask,
+                    const double* V, const icnnm_params& p) {
+  int H, W, T, k1, k2, k3;
+  validate_shape(shape, H, W, T, k1, k2, k3);
+  validate_params(p);
+  if (!M || !mask) fail(ICNNM_EINVAL, "M and mask must not be NULL");
+  j.H = H; j.W = W; j.T = T; j.m = (long long)H * W * T;
+  j.p = p;
+  {
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    j.vd = get_vdata(c, V, k1, k2, k3, p.prec);
+    ensure_tc(j.vd, p.prec);
+  }
+  std::lock_guard<std::mutex> sg(c->submu);
+  const size_t mb = (size_t)j.m * 4, kb = (size_t)j.m;
+  const size_t flag_off = (mb + kb + 15) / 16 * 16;
+  void* st = nullptr;
+  CK(cudaMallocFromPoolAsync(&st, flag_off + 8, c->pool, c->sub_stream));
+  char* b = static_cast<char*>(st);
+  int h2[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(b, M, mb, cudaMemcpyDefault, c->sub_stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + mb, mask, kb, cudaMemcpyDefault, c->sub_stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + flag_off, 0, 8, c->sub_stream);
+  if (e == cudaSuccess)
+    e = check_observed((const float*)b, (const uint8_t*)(b + mb), j.m, (int*)(b + flag_off), c->sub_stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h2, b + flag_off, 8, cudaMemcpyDeviceToHost, c->sub_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->sub_stream);
+  if (e != cudaSuccess || h2[1] || h2[0] == 0) {
+    cudaFreeAsync(st, c->sub_stream);
+    cudaStreamSynchronize(c->sub_stream);
+    if (e != cudaSuccess) throw CudaFail{e, "staging of the submitted inputs"};
+    if (h2[1]) fail(ICNNM_EINVAL, "mask entries must be 0/1 and M must be finite on Omega");
+    fail(ICNNM_EINVAL, "Omega is empty");
+  }
+  j.dstage = st;
 }
 
 }  // namespace
@@ -902,6 +1124,7 @@ const char* icnnm_strerror(icnnm_status st) {
     case ICNNM_ETIMEOUT: return "a bounded device-side wait expired";
     case ICNNM_ECANCELED: return "job cancelled";
     case ICNNM_EUNSUPPORTED: return "not supported by this build";
+    case ICNNM_ENOCONV: return "the eigensolver did not converge within its sweep cap";
   }
   return "unknown status";
 }
@@ -931,7 +1154,24 @@ icnnm_status icnnm_create(icnnm_ctx** out, int device, size_t budget, void* stre
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   c->budget = budget ? budget : (size_t)(0.9 * fr);
-  if (budget > fr) { if (c->own_stream) cudaStreamDestroy(c->stream); delete c; return ICNNM_ENOMEM; }
+  auto undo = [&](icnnm_status st) {
+    if (c->sub_stream) cudaStreamDestroy(c->sub_stream);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return st;
+  };
+  if (budget > fr) return undo(ICNNM_ENOMEM);
+  if (cudaStreamCreateWithFlags(&c->sub_stream, cudaStreamNonBlocking) != cudaSuccess) return undo(ICNNM_ECUDA);
+  // the context's own pool: memory freed by finished jobs stays reserved (up to the
+  // budget) for the next ones instead of going back to the driver at every synchronisation
+  cudaMemPoolProps pp{};
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = device;
+  if (cudaMemPoolCreate(&c->pool, &pp) != cudaSuccess) { cudaGetLastError(); c->pool = nullptr; return undo(ICNNM_ECUDA); }
+  uint64_t keep = c->budget;
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   *out = c;
   return ICNNM_OK;
 }
@@ -947,7 +1187,11 @@ void icnnm_destroy(icnnm_ctx* c) {
   if (c->server.joinable()) c->server.join();
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  for (auto& kv : c->jobs) free_job(c, *kv.second);
+  for (auto& kv : c->jobs) {
+    free_job(c, *kv.second);
+    if (kv.second->dres) cudaFreeAsync(kv.second->dres, c->stream);
+    kv.second->dres = nullptr;
+  }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (auto& kv : c->vcache) {
     if (kv.second->dVf) cudaFree(kv.second->dVf);
@@ -955,10 +1199,20 @@ void icnnm_destroy(icnnm_ctx* c) {
     if (kv.second->tc_ready) tc_free_vdata(&kv.second->tc);
   }
   for (int sl = 0; sl < 2; ++sl) {
-    if (c->dlist[sl]) cudaFree(c->dlist[sl]);
-    if (c->dtile0[sl]) cudaFree(c->dtile0[sl]);
+    dfree_async(c->dlist[sl], c->stream);
+    dfree_async(c->dtile0[sl], c->stream);
   }
-  if (c->gscr) cudaFree(c->gscr);
+  for (int sl = 0; sl < 2; ++sl) c->dlist[sl] = nullptr, c->dtile0[sl] = nullptr;
+  dfree_async(c->gscr, c->stream);
+  cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->sub_stream);
+  for (auto& e : c->ring) {
+    if (e.p) cudaFreeHost(e.p);
+    if (e.ev) cudaEventDestroy(e.ev);
+  }
+  if (c->hscal) cudaFreeHost(c->hscal);
+  if (c->pool) cudaMemPoolDestroy(c->pool);
+  cudaStreamDestroy(c->sub_stream);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1034,6 +1288,7 @@ icnnm_status icnnm_learn_V(icnnm_ctx* c, const int64_t kdims[3], int32_t b, cons
     CK(cudaMemcpyAsync(hinfo, dinfo, sizeof hinfo, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (hinfo[1]) fail(ICNNM_ETIMEOUT, "a bounded grid barrier of the eigensolver expired");
+    if (hinfo[0] < 0) fail(ICNNM_ENOCONV, "the FP64 Jacobi eigensolver did not converge within 30 sweeps");
     for (void* p : tmp) cudaFree(p);
     return ICNNM_OK;
   } catch (StatusFail& f) {
@@ -1118,6 +1373,7 @@ icnnm_status icnnm_spectral_diagnostics(icnnm_ctx* c, const icnnm_shape* shape, 
     CK(cudaMemcpyAsync(hinfo, dinfo, sizeof hinfo, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (hinfo[1]) fail(ICNNM_ETIMEOUT, "a bounded grid barrier of the eigensolver expired");
+    if (hinfo[0] < 0) fail(ICNNM_ENOCONV, "the FP64 Jacobi eigensolver did not converge within 30 sweeps");
     if (r_K) *r_K = (int32_t)hout[0];
     if (mu_K) *mu_K = hout[1];
     if (alpha_K) *alpha_K = hout[0] > 0 ? sqrt(fmax(lmax, 0.0)) : 0.0;
@@ -1176,6 +1432,7 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* c, const icnnm_shape* shape, const floa
     CnnmResult r{};
     CK(cnnm_run(P, c->stream, &r));
     if (r.timed_out) fail(ICNNM_ETIMEOUT, "a bounded grid barrier of the eigensolver expired");
+    if (r.unconverged) fail(ICNNM_ENOCONV, "the FP64 Jacobi eigensolver did not converge within 30 sweeps");
     CK(cudaMemcpyAsync(L_out, dL, m * 4, cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (stats) {
@@ -1184,6 +1441,7 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* c, const icnnm_shape* shape, const floa
       stats->objective = r.objective;
       stats->theta = r.theta;
       stats->seconds = r.seconds;
+      stats->latency = r.seconds;
     }
     for (void* q : tmp) cudaFree(q);
     return ICNNM_OK;
@@ -1209,7 +1467,7 @@ icnnm_status icnnm_solve_batch(icnnm_ctx* c, int32_t n, const icnnm_shape* shape
     std::vector<Job*> js;
     for (int i = 0; i < n; ++i) {
       jobs.push_back(std::make_unique<Job>());
-      prepare_job(c, *jobs.back(), &shapes[i], M[i], mask[i], V, p, false);
+      prepare_job(c, *jobs.back(), &shapes[i], M[i], mask[i], V, p);
       if (i > 0 && (shapes[i].kdims[0] != shapes[0].kdims[0] || shapes[i].kdims[1] != shapes[0].kdims[1] ||
                     shapes[i].kdims[2] != shapes[0].kdims[2]))
         fail(ICNNM_EINVAL, "all problems of a batch share kernel dims");
@@ -1248,14 +1506,22 @@ icnnm_status icnnm_submit(icnnm_ctx* c, const icnnm_shape* shape, const float* M
                           const double* V, const icnnm_params* params, uint64_t* job_id) {
   if (!c || !job_id) return ICNNM_EINVAL;
   auto j = std::make_shared<Job>();
+  j->t_submit = std::chrono::steady_clock::now();
   try {
-    std::lock_guard<std::recursive_mutex> g(c->mu);
     CK(cudaSetDevice(c->device));
     const icnnm_params p = params ? *params : defaults();
-    prepare_job(c, *j, shape, M, mask, V, p, true);
-    const int nrp = std::max(fwd_fp32_nrp(j->vd->k), tc_nrp(j->vd->k));
-    if (job_bytes(j->H, j->W, j->T, j->vd->k, j->vd->kc, p.prec, nrp, &j->vd->tc.g) > c->budget)
-      fail(ICNNM_ENOMEM, "the job alone exceeds the HBM budget");
+    int H, W, T, k1, k2, k3;
+    validate_shape(shape, H, W, T, k1, k2, k3);
+    validate_params(p);
+    {
+      std::lock_guard<std::recursive_mutex> g(c->mu);
+      VData* vd = get_vdata(c, V, k1, k2, k3, p.prec);
+      ensure_tc(vd, p.prec);
+      const int nrp = std::max(fwd_fp32_nrp(vd->k), tc_nrp(vd->k));
+      if (job_bytes(H, W, T, vd->k, vd->kc, p.prec, nrp, &vd->tc.g) > c->budget)
+        fail(ICNNM_ENOMEM, "the job alone exceeds the HBM budget");
+    }
+    prepare_submit(c, *j, shape, M, mask, V, p);
   } catch (StatusFail& f) {
     return report(c, f);
   } catch (CudaFail& f) {
@@ -1275,8 +1541,18 @@ icnnm_status icnnm_submit(icnnm_ctx* c, const icnnm_shape* shape, const float* M
 
 static icnnm_status collect(icnnm_ctx* c, std::shared_ptr<Job> j, float* L_out, icnnm_stats* stats) {
   if (j->phase == DONE) {
-    if (L_out) {
-      if (cudaMemcpy(L_out, j->result.data(), j->m * 4, cudaMemcpyDefault) != cudaSuccess) return ICNNM_ECUDA;
+    // the server synchronised its stream after writing dres, so a plain copy is ordered
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaSuccess;
+    if (L_out) e = cudaMemcpy(L_out, j->dres, j->m * 4, cudaMemcpyDefault);
+    {
+      std::lock_guard<std::mutex> sg(c->submu);
+      cudaFreeAsync(j->dres, c->sub_stream);
+    }
+    j->dres = nullptr;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return ICNNM_ECUDA;
     }
     if (stats) *stats = j->stats;
     return ICNNM_OK;
@@ -1313,7 +1589,14 @@ icnnm_status icnnm_profile_enable(icnnm_ctx* c, int32_t enable) {
   c->pending.clear();
   c->evnext = 0;
   for (int i = 0; i < 4; ++i) c->pass_ms[i] = 0;
-  for (int i = 0; i < 5; ++i) c->pass_n[i] = 0;
+  for (int i = 0; i < 5; ++i) c->pass_n[i] = 0, c->pass_vox[i] = 0;
+  return ICNNM_OK;
+}
+
+icnnm_status icnnm_profile_voxels(icnnm_ctx* c, int32_t pass, int64_t* voxels) {
+  if (!c || pass < -1 || pass > 3) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  if (voxels) *voxels = c->pass_vox[pass < 0 ? 4 : pass];
   return ICNNM_OK;
 }
 
@@ -1323,6 +1606,53 @@ icnnm_status icnnm_profile_read(icnnm_ctx* c, int32_t pass, double* ms_total, in
   if (ms_total) *ms_total = pass < 0 ? 0.0 : c->pass_ms[pass];
   if (launches) *launches = pass < 0 ? c->pass_n[4] : c->pass_n[pass];
   return ICNNM_OK;
+}
+
+icnnm_status icnnm_job_bytes(icnnm_ctx* c, const icnnm_shape* shape, int32_t prec, size_t* bytes) {
+  if (!c || !bytes) return ICNNM_EINVAL;
+  try {
+    int H, W, T, k1, k2, k3;
+    validate_shape(shape, H, W, T, k1, k2, k3);
+    if (prec != ICNNM_FP32 && prec != ICNNM_BF16 && prec != ICNNM_BF16X3) fail(ICNNM_EINVAL, "unknown precision");
+    const int k = k1 * k2 * k3, kc = round_up(k, 16);
+    TcGeom g{};
+    if (prec != ICNNM_FP32) {
+      std::string why;
+      if (!tc_supported(k1, k2, k3, &why)) fail(ICNNM_EUNSUPPORTED, "BF16 path: " + why);
+      g = tc_geom(k1, k2, k3, kc);
+      if (prec == ICNNM_BF16X3 && !g.split_ok) fail(ICNNM_EUNSUPPORTED, "BF16X3 is not built for these kernel dims");
+    }
+    const int nrp = std::max(fwd_fp32_nrp(k), tc_nrp(k));
+    *bytes = job_bytes(H, W, T, k, kc, prec, nrp, &g);
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    return report(c, f);
+  }
+}
+
+icnnm_status icnnm_check_bounded_wait(icnnm_ctx* c, int64_t limit_ns) {
+  if (!c) return ICNNM_EINVAL;
+  if (limit_ns < 1000000 || limit_ns > 10000000000ll) {
+    set_err(c, "limit_ns must be in [1e6, 1e10]");
+    return ICNNM_EINVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  try {
+    CK(cudaSetDevice(c->device));
+    int* d = (int*)dalloc_async(c, sizeof(int), c->stream);
+    CK(cudaMemsetAsync(d, 0, sizeof(int), c->stream));
+    CK(tc_bounded_wait_check((uint64_t)limit_ns, d, c->stream));
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    dfree_async(d, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+    if (h) fail(ICNNM_ETIMEOUT, "the bounded wait expired (expected: nothing completes its barrier)");
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    return report(c, f);
+  } catch (CudaFail& f) {
+    return report(c, f);
+  }
 }
 
 icnnm_status icnnm_cancel(icnnm_ctx* c, uint64_t id) {

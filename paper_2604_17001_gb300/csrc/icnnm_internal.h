@@ -69,6 +69,8 @@ struct JobDev {
   const void* tmapX;    // BF16 path: TMA map (CUtensorMap, device memory) of Xc, 8 copies
   const void* tmapX2;   // BF16 path: the same with k2 - 8 copies (kernels wider than 8)
   const void* tmapU;    // BF16 path: TMA map of U (box: one tile x 64 channels)
+  void* Ulo;            // split forward: the lo part of U (BF16, like U), or null
+  const void* tmapUlo;  // split forward: TMA map of Ulo
   int xTp, xHp, xWp;    // BF16 path: dims of each copy in Xc
 };
 
@@ -84,6 +86,7 @@ struct Shared {
   const int* job_tile0;  // device, njobs + 1 prefix sums of ntiles
   int total_tiles;
   int max_vblk;          // most 1024-voxel blocks of one job in the list
+  long long nvox;        // voxels of all jobs in the list (host-side bookkeeping)
 };
 
 // Binary search: the job that owns global tile `t`.
@@ -186,6 +189,7 @@ struct CnnmProblem {
 struct CnnmResult {
   double seconds, theta, objective;   // device time; final penalty; ||A_k(L)||_*
   int timed_out;
+  int unconverged;   // the eigensolver hit its sweep cap unconverged in some iteration
 };
 size_t cnnm_state_bytes(int H, int W, int T, int k1, int k2, int k3);
 cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res);

@@ -438,6 +438,7 @@ cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res) {
   res->seconds = ms * 1e-3;
   res->theta = theta;
   res->timed_out = hinfo[1];
+  res->unconverged = hinfo[0] < 0;
   // objective ||A_k(L)||_* = sum of the singular values of A_k(L)
   gram_eigs(Lc);
   if (e == cudaSuccess) {

@@ -108,7 +108,13 @@ __global__ void __launch_bounds__(AC_THREADS) autocorr_kernel(LearnArgs a) {
     a.part[((long long)j * a.nblk + blockIdx.y) * a.nlag + l] = acc[q];
 }
 
-// Gram[u][s] = sum_j sum_blk part[j][blk][lag(u - s)], summed in a fixed order.
+// Gram[u][s] = sum_j sum_blk part[j][blk][lag(u - s)], summed in a fixed order. The
+// circular autocorrelation is even, R(d) = R(-d), but the two lags are summed from
+// different products, so they agree only to rounding (about 1e-7 relative with FP32
+// products); G takes their average, which makes it exactly symmetric (IEEE addition
+// commutes), as the symmetric Jacobi eigensolver needs: an antisymmetric part survives
+// every rotation and would hold the off-diagonal norm at its size. The lag index of
+// s - u is nlag - 1 - lag(u - s).
 __global__ void gram_kernel(LearnArgs a, double* gram) {
   const int k = a.k1 * a.k2 * a.k3;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,10 +123,14 @@ __global__ void gram_kernel(LearnArgs a, double* gram) {
   const int uw = u % a.k2, uh = (u / a.k2) % a.k1, ut = u / (a.k1 * a.k2);
   const int sw = s % a.k2, shh = (s / a.k2) % a.k1, st = s / (a.k1 * a.k2);
   const int l = ((ut - st + a.k3 - 1) * a.nl1 + (uh - shh + a.k1 - 1)) * a.nl2 + (uw - sw + a.k2 - 1);
-  double g = 0.0;
+  const int lm = a.nlag - 1 - l;
+  double g = 0.0, gm = 0.0;
   for (int j = 0; j < a.b; ++j)
-    for (int bb = 0; bb < a.nblk; ++bb) g += a.part[((long long)j * a.nblk + bb) * a.nlag + l];
-  gram[idx] = g;
+    for (int bb = 0; bb < a.nblk; ++bb) {
+      g += a.part[((long long)j * a.nblk + bb) * a.nlag + l];
+      gm += a.part[((long long)j * a.nblk + bb) * a.nlag + lm];
+    }
+  gram[idx] = 0.5 * (g + gm);
 }
 
 // ---------------------------------------------------------------------------------
@@ -128,7 +138,13 @@ __global__ void gram_kernel(LearnArgs a, double* gram) {
 // overwritten; V (k x k) accumulates the rotations. Each sweep runs n-1 rounds of the
 // circle (round-robin) schedule on n = k rounded up to even; index k is a dummy.
 // Stops when the off-diagonal Frobenius norm is <= tol * ||A||_F or after max_sweeps.
+// info[0] = sweeps run, or JACOBI_UNCONVERGED if after max_sweeps the off-diagonal norm
+// is still above JACOBI_ACCEPT * ||A||_F (a cyclic Jacobi converges quadratically, so
+// that only happens when something is wrong); the flag is sticky while the caller does
+// not reset info[0] (CNNM runs the solver every iteration and reads info once).
 // ---------------------------------------------------------------------------------
+constexpr int JACOBI_UNCONVERGED = -1;
+constexpr double JACOBI_ACCEPT = 1e-10;
 constexpr int EIG_THREADS = 1024;
 constexpr int EIG_MAXK = 1024;
 
@@ -183,7 +199,8 @@ jacobi_kernel(double* A, double* V, int k, int max_sweeps, double tol, double* e
   const double normA = sqrt(red[0]);
   __syncthreads();
   int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
+  bool unconv = false;
+  for (;; ++sweep) {
     double off = 0.0;
     for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x)
       if (e / k != e % k) off += A[e] * A[e];
@@ -196,6 +213,10 @@ jacobi_kernel(double* A, double* V, int k, int max_sweeps, double tol, double* e
     const double offn = sqrt(red[0]);
     __syncthreads();
     if (offn <= tol * normA) break;
+    if (sweep == max_sweeps) {
+      unconv = offn > JACOBI_ACCEPT * normA;
+      break;
+    }
     for (int r = 0; r < n - 1; ++r) {
       for (int i = threadIdx.x; i < npair; i += blockDim.x) {
         int p, q;
@@ -244,7 +265,7 @@ jacobi_kernel(double* A, double* V, int k, int max_sweeps, double tol, double* e
     }
   }
   eig_sort_sign(A, V, k, evals_out, Vout, ev, order);
-  if (threadIdx.x == 0) info[0] = sweep;
+  if (threadIdx.x == 0) info[0] = (unconv || info[0] == JACOBI_UNCONVERGED) ? JACOBI_UNCONVERGED : sweep;
 }
 
 
@@ -353,7 +374,8 @@ jacobi_grid_kernel(double* A, double* V, int k, int max_sweeps, double tol, unsi
   const double normA = sqrt(grid_total(part, red));
   double* offpart = part + gridDim.x;
   int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
+  bool unconv = false;
+  for (;; ++sweep) {
     double off = 0.0;
     for (long long e = gt; e < (long long)k * k; e += nt)
       if (e / k != e % k) {
@@ -362,7 +384,12 @@ jacobi_grid_kernel(double* A, double* V, int k, int max_sweeps, double tol, unsi
       }
     block_partial(off, offpart, red);
     grid_sync(bar);
-    if (sqrt(grid_total(offpart, red)) <= tol * normA) break;
+    const double offn = sqrt(grid_total(offpart, red));
+    if (offn <= tol * normA) break;
+    if (sweep == max_sweeps) {
+      unconv = offn > JACOBI_ACCEPT * normA;
+      break;
+    }
     for (int r = 0; r < n - 1; ++r) {
       for (int i = threadIdx.x; i < npair; i += blockDim.x) jacobi_pair(A, k, n, r, i, pp[i], qq[i], cs[i], sn[i]);
       __syncthreads();
@@ -392,7 +419,7 @@ jacobi_grid_kernel(double* A, double* V, int k, int max_sweeps, double tol, unsi
     }
   }
   if (gt == 0) {
-    info[0] = sweep;
+    info[0] = (unconv || info[0] == JACOBI_UNCONVERGED) ? JACOBI_UNCONVERGED : sweep;
     info[1] = (int)bar[2];
   }
 }
@@ -423,7 +450,9 @@ __global__ void gram_from_lags_kernel(const double* lagsum, int k1, int k2, int 
   const int u = (int)(idx / k), s = (int)(idx % k);
   const int uw = u % k2, uh = (u / k2) % k1, ut = u / (k1 * k2);
   const int sw = s % k2, shh = (s / k2) % k1, st = s / (k1 * k2);
-  gram[idx] = lagsum[((ut - st + k3 - 1) * nl1 + (uh - shh + k1 - 1)) * nl2 + (uw - sw + k2 - 1)];
+  const int l = ((ut - st + k3 - 1) * nl1 + (uh - shh + k1 - 1)) * nl2 + (uw - sw + k2 - 1);
+  const int nlag = (2 * k3 - 1) * nl1 * nl2;
+  gram[idx] = 0.5 * (lagsum[l] + lagsum[nlag - 1 - l]);    // exactly symmetric (see gram_kernel)
 }
 
 // Diagnostics (Sec. III-A, Definition 2). With G = A_k(L0)^T A_k(L0) and K = V:
@@ -484,9 +513,12 @@ diag_support_kernel(const double* P, const double* V, int k, double tol, double*
   }
   const double r = red[0];
   __syncthreads();
+  // S = D P D from the symmetric part of P: V^T (G V) is symmetric only to rounding, and
+  // the scaling by 1/sigma lifts that asymmetry far above the eigensolver's tolerance
   for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
     const int i = (int)(e / k), j = (int)(e % k);
-    S[e] = d[i] * P[e] * d[j];
+    const double pij = 0.5 * (P[e] + P[(long long)j * k + i]);
+    S[e] = d[i] * pij * d[j];
   }
   double rowmax = 0.0;
   for (int srow = threadIdx.x; srow < k; srow += blockDim.x) {

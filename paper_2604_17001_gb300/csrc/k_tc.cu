@@ -58,7 +58,7 @@ constexpr uint32_t TMEM_COLS = 256;
 constexpr int SMEM_LIMIT = 227 * 1024;
 
 int rup(int x, int a) { return (x + a - 1) / a * a; }
-size_t fwd_smem_n(const TcGeom& g, int nus);
+size_t fwd_smem_n(const TcGeom& g, int nus, bool split = false);
 
 TcGeom make_geom(int k1, int k2, int k3) {
   TcGeom g{};
@@ -113,14 +113,24 @@ TcGeom make_geom(int k1, int k2, int k3) {
   g.HBp = k3 * g.Hb * g.pitch;
   g.nus = FWD_USTAGES;
   while (g.nus > 1 && fwd_smem_n(g, g.nus) > SMEM_LIMIT) --g.nus;
+  // the lo copies start on a 128-byte boundary (tiled TMA destinations must)
+  g.lo_off = rup(k2 * g.region_bytes + 16 * 16, 128);
+  g.stage_bytes_s = rup(g.lo_off + k2 * g.region_bytes + 16 * 16, 1024);
+  g.nus_s = FWD_USTAGES;
+  while (g.nus_s > 1 && fwd_smem_n(g, g.nus_s, true) > SMEM_LIMIT) --g.nus_s;
+  g.split_ok = fwd_smem_n(g, g.nus_s, true) <= SMEM_LIMIT;
   return g;
 }
 
-size_t fwd_smem_n(const TcGeom& g, int nus) {
-  return 1024 + (size_t)g.nch_f * CHUNK + 2 * (size_t)g.stage_bytes + (size_t)nus * USTAGE + EPI_WARPS * 32 * 4 +
+size_t fwd_smem_n(const TcGeom& g, int nus, bool split) {
+  const int img = split ? 2 : 1;
+  const size_t stage = split ? (size_t)g.stage_bytes_s : (size_t)g.stage_bytes;
+  return 1024 + (size_t)img * g.nch_f * CHUNK + 2 * stage + (size_t)nus * img * USTAGE + EPI_WARPS * 32 * 4 +
          64 * 16 + 256;
 }
-size_t fwd_smem(const TcGeom& g) { return fwd_smem_n(g, g.nus); }
+size_t fwd_smem(const TcGeom& g, bool split = false) {
+  return split ? fwd_smem_n(g, g.nus_s, true) : fwd_smem_n(g, g.nus);
+}
 size_t adj_smem(const TcGeom& g) {
   return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 2 * (size_t)g.HBp * 4 + 128 * 4 + 256;
 }
@@ -198,24 +208,35 @@ __device__ __forceinline__ void warp_colsum_store(float (&a)[32], int lane, floa
 // ---------------------------------------------------------------------------------
 // Forward pass
 // ---------------------------------------------------------------------------------
+// SPLIT: the operand copies, V^T and U come as hi + lo BF16 pairs (lo = bf16(x - hi)),
+// and each tile takes three products into one accumulator, A_k(X_hi)V_hi + A_k(X_lo)V_hi
+// + A_k(X_hi)V_lo, i.e. A_k(X)V to about 2^-16 relative instead of 2^-8; U' is stored as
+// hi = bf16(U'), lo = bf16(U' - hi). The halo stage holds the hi copies (and 16 zero
+// rows) and then the lo copies (and 16 zero rows); a U stage holds the hi tile and then
+// the lo tile; shared memory holds both V^T images.
+template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_constant__ FwdArgs a) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1k(smraw);
   const TcGeom& g = a.g;
   const Shared& sh = a.sh;
-  uint8_t* sA = sm;                                              // V^T image of this channel tile
-  uint8_t* sH = sA + (size_t)g.nch_f * CHUNK;                    // [2] halo stages
-  uint8_t* sU = sH + 2 * (size_t)g.stage_bytes;                  // [g.nus] U tiles
-  float* sD = reinterpret_cast<float*>(sU + (size_t)g.nus * USTAGE);   // [EPI_WARPS][32]
+  constexpr int NIMG = SPLIT ? 2 : 1;
+  const int stage_bytes = SPLIT ? g.stage_bytes_s : g.stage_bytes;
+  const int nus = SPLIT ? g.nus_s : g.nus;
+  const int ustage = NIMG * USTAGE;
+  uint8_t* sA = sm;                                              // V^T image(s) of this channel tile
+  uint8_t* sH = sA + (size_t)NIMG * g.nch_f * CHUNK;             // [2] halo stages
+  uint8_t* sU = sH + 2 * (size_t)stage_bytes;                    // [nus] U tiles
+  float* sD = reinterpret_cast<float*>(sU + (size_t)nus * ustage);   // [EPI_WARPS][32]
   ulonglong2* sDesc = reinterpret_cast<ulonglong2*>(sD + EPI_WARPS * 32);  // [64] MMA descriptors
   uint64_t* bars = reinterpret_cast<uint64_t*>(sDesc + 64);
   uint64_t* full = bars;                   // [2] halo landed
   uint64_t* empty = bars + 2;              // [2] halo consumed by the MMAs
   uint64_t* tfull = bars + 4;              // [2] accumulator ready
   uint64_t* tempty = bars + 6;             // [2] accumulator read out
-  uint64_t* ufull = bars + 8;              // [g.nus] U tile landed
-  uint64_t* uempty = bars + 8 + g.nus;   // [g.nus] U stage free again
-  uint64_t* abar = bars + 8 + 2 * g.nus;
+  uint64_t* ufull = bars + 8;              // [nus] U tile landed
+  uint64_t* uempty = bars + 8 + nus;       // [nus] U stage free again
+  uint64_t* abar = bars + 8 + 2 * nus;
   uint64_t* dbar = abar + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(dbar + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
@@ -234,7 +255,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       ptx::mbar_init(&tfull[i], 1);
       ptx::mbar_init(&tempty[i], EPI_WARPS);
     }
-    for (int i = 0; i < g.nus; ++i) {
+    for (int i = 0; i < nus; ++i) {
       ptx::mbar_init(&ufull[i], 1);
       ptx::mbar_init(&uempty[i], 1);
     }
@@ -248,8 +269,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     ptx::tmem_relinquish();
   }
   // zero rows after the copies of each stage (read by the padded taps, times zero)
-  for (int i = threadIdx.x; i < 2 * 64; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(sH + (i / 64) * g.stage_bytes + g.k2 * g.region_bytes)[i % 64] = 0u;
+  for (int i = threadIdx.x; i < 2 * NIMG * 64; i += blockDim.x) {
+    const int st = i / (NIMG * 64), half = (i / 64) % NIMG;
+    reinterpret_cast<uint32_t*>(sH + (size_t)st * stage_bytes + (size_t)half * g.lo_off +
+                                g.k2 * g.region_bytes)[i % 64] = 0u;
+  }
   ptx::fence_proxy_async_smem();
   ptx::tc_fence_before();
   __syncthreads();
@@ -259,10 +283,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 
   if (warp == 0) {
     if (lane == 0) {
-      ptx::mbar_arrive_expect_tx(abar, (uint32_t)g.nch_f * CHUNK);
-      const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.VtImg) + (size_t)ct * g.nch_f * CHUNK;
-      for (int c = 0; c < g.nch_f; ++c) ptx::bulk_g2s(sA + (size_t)c * CHUNK, src + (size_t)c * CHUNK, CHUNK, abar);
-      const uint32_t hbytes = (uint32_t)(g.k2 * g.region_bytes);
+      ptx::mbar_arrive_expect_tx(abar, (uint32_t)(NIMG * g.nch_f * CHUNK));
+      for (int im = 0; im < NIMG; ++im) {
+        // image im of channel tile ct: the lo images follow the nct hi images
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.VtImg) + ((size_t)im * g.nct + ct) * g.nch_f * CHUNK;
+        for (int c = 0; c < g.nch_f; ++c)
+          ptx::bulk_g2s(sA + ((size_t)im * g.nch_f + c) * CHUNK, src + (size_t)c * CHUNK, CHUNK, abar);
+      }
+      const uint32_t hbytes = (uint32_t)(NIMG * g.k2 * g.region_bytes);
       int it = 0;
       for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
         const int s = it & 1;
@@ -275,25 +303,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         ptx::mbar_arrive_expect_tx(&full[s], hbytes);
         // w-chunk q holds the copies of taps sw = 8q .. min(8q + 7, k2 - 1); the last
         // chunk of a kernel wider than 8 uses the map whose box has only k2 - 8 copies
-        for (int q = 0; q < g.nwc; ++q)
-          ptx::tma_load_4d(sH + (size_t)s * g.stage_bytes + (size_t)q * g.ncopy * g.region_bytes,
-                           (q > 0) ? J.tmapX2 : J.tmapX, t * 8, th * TH, tw + (g.nwc - 1) - q, 0, &full[s]);
+        // (SPLIT: the lo copies are copies ncopy..2 ncopy-1 of the same maps)
+        for (int half = 0; half < NIMG; ++half)
+          for (int q = 0; q < g.nwc; ++q)
+            ptx::tma_load_4d(sH + (size_t)s * stage_bytes + (size_t)half * g.lo_off + (size_t)q * g.ncopy * g.region_bytes,
+                             (q > 0) ? J.tmapX2 : J.tmapX, t * 8, th * TH, tw + (g.nwc - 1) - q, half * g.ncopy,
+                             &full[s]);
         if (rdU) {
-          const int us = it % g.nus;
-          const uint32_t uph = (it / g.nus) & 1;
+          const int us = it % nus;
+          const uint32_t uph = (it / nus) & 1;
           if (!ptx::mbar_wait_abortable(&uempty[us], uph ^ 1, abort)) { failed = true; ++it; break; }
-          ptx::mbar_arrive_expect_tx(&ufull[us], (uint32_t)nbox * CHUNK);
-          for (int bx = 0; bx < nbox; ++bx)
-            ptx::tma_load_4d(sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, J.tmapU, ct * 128 + bx * 64, tw * TW,
-                             th * TH, t, &ufull[us]);
+          ptx::mbar_arrive_expect_tx(&ufull[us], (uint32_t)(NIMG * nbox * CHUNK));
+          for (int half = 0; half < NIMG; ++half)
+            for (int bx = 0; bx < nbox; ++bx)
+              ptx::tma_load_4d(sU + (size_t)us * ustage + (size_t)half * USTAGE + (size_t)bx * CHUNK,
+                               half ? J.tmapUlo : J.tmapU, ct * 128 + bx * 64, tw * TW, th * TH, t, &ufull[us]);
         }
       }
       // every issued load has landed before the CTA can exit
       for (int i = (it > 2 ? it - 2 : 0); i < it; ++i)
         if (!ptx::mbar_wait(&full[i & 1], (i >> 1) & 1)) failed = true;
       if (rdU)
-        for (int i = (it > g.nus ? it - g.nus : 0); i < it; ++i)
-          if (!ptx::mbar_wait(&ufull[i % g.nus], (i / g.nus) & 1)) failed = true;
+        for (int i = (it > nus ? it - nus : 0); i < it; ++i)
+          if (!ptx::mbar_wait(&ufull[i % nus], (i / nus) & 1)) failed = true;
       if (failed) *abort = 1;
     }
   } else if (warp == 1) {
@@ -323,25 +355,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         if (!ptx::mbar_wait_abortable(&tempty[b], ph ^ 1, abort)) { failed = true; break; }
         ptx::tc_fence_after();
         const uint32_t d = tbase + (uint32_t)b * 128;
-        const uint64_t sadd = (uint64_t)(((uint32_t)s * (uint32_t)g.stage_bytes) >> 4);   // start-address field
-        if (a.tab.reg) {
-          // regular tap layout: both descriptors advance by register adds (no table
-          // loads, so the issue rate is the tensor core's): A by 256 bytes inside a
-          // w-run and to the next copy's region at its end, B by 32 bytes inside a
-          // 64-tap chunk and to the next chunk at its end
-          uint64_t ad = sDesc[0].x + sadd, bd = sDesc[0].y;
-          const uint64_t a_run = (uint64_t)((g.region_bytes - (a.tab.hp - 1) * 256) >> 4);
-          int jj = 0, bq = 0;
-          for (int i = 0; i < g.nmma; ++i) {
-            ptx::mma_bf16(d, ad, bd, idesc, i > 0 ? 1u : 0u);
-            if (++jj == a.tab.hp) { jj = 0; ad += a_run; } else { ad += 16; }
-            if (++bq == 4) { bq = 0; bd += (CHUNK >> 4) - 6; } else { bd += 2; }
-          }
-        } else {
+        const uint64_t sadd = (uint64_t)(((uint32_t)s * (uint32_t)stage_bytes) >> 4);   // start-address field
+        // chains: (hi, hi); SPLIT adds (lo halo, hi V^T) and (hi halo, lo V^T)
+        for (int chn = 0; chn < (SPLIT ? 3 : 1); ++chn) {
+          const uint64_t aoff = chn == 1 ? (uint64_t)(g.lo_off >> 4) : 0;
+          const uint64_t boff = chn == 2 ? (uint64_t)((g.nch_f * CHUNK) >> 4) : 0;
+          if (a.tab.reg) {
+            // regular tap layout: both descriptors advance by register adds (no table
+            // loads, so the issue rate is the tensor core's): A by 256 bytes inside a
+            // w-run and to the next copy's region at its end, B by 32 bytes inside a
+            // 64-tap chunk and to the next chunk at its end
+            uint64_t ad = sDesc[0].x + sadd + aoff, bd = sDesc[0].y + boff;
+            const uint64_t a_run = (uint64_t)((g.region_bytes - (a.tab.hp - 1) * 256) >> 4);
+            int jj = 0, bq = 0;
+            for (int i = 0; i < g.nmma; ++i) {
+              ptx::mma_bf16(d, ad, bd, idesc, (chn > 0 || i > 0) ? 1u : 0u);
+              if (++jj == a.tab.hp) { jj = 0; ad += a_run; } else { ad += 16; }
+              if (++bq == 4) { bq = 0; bd += (CHUNK >> 4) - 6; } else { bd += 2; }
+            }
+          } else {
 #pragma unroll 4
-          for (int i = 0; i < g.nmma; ++i) {
-            const ulonglong2 dd = sDesc[i];
-            ptx::mma_bf16(d, dd.x + sadd, dd.y, idesc, i > 0 ? 1u : 0u);
+            for (int i = 0; i < g.nmma; ++i) {
+              const ulonglong2 dd = sDesc[i];
+              ptx::mma_bf16(d, dd.x + sadd + aoff, dd.y + boff, idesc, (chn > 0 || i > 0) ? 1u : 0u);
+            }
           }
         }
         ptx::mma_commit(&empty[s]);
@@ -400,9 +437,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       const bool valid = h < J.H && w < J.W;
       const int b = it & 1;
       const uint32_t ph = (it >> 1) & 1;
-      const int us = it % g.nus;
-      const uint32_t uph = (it / g.nus) & 1;
-      uint8_t* urow = sU + (size_t)us * USTAGE + (size_t)(cg >> 1) * CHUNK + (size_t)vox * 128;
+      const int us = it % nus;
+      const uint32_t uph = (it / nus) & 1;
+      uint8_t* urow = sU + (size_t)us * ustage + (size_t)(cg >> 1) * CHUNK + (size_t)vox * 128;
+      uint8_t* urow_lo = urow + USTAGE;                          // SPLIT: the lo tile
       const uint32_t u0 = (uint32_t)(cg & 1) * 4;
       if (!failed)
         failed = !ptx::mbar_wait_abortable(rdU ? &ufull[us] : &uempty[us], rdU ? uph : (uph ^ 1), abort);
@@ -420,13 +458,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         for (int u = 0; u < 4; ++u) {
           if (u < nun) {
             const uint4 x = *reinterpret_cast<const uint4*>(urow + (((u0 + u) ^ usw) << 4));
+            uint4 xl = make_uint4(0u, 0u, 0u, 0u);
+            if (SPLIT) xl = *reinterpret_cast<const uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
             const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
             const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
             const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
             const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+            const uint32_t xlw[4] = {xl.x, xl.y, xl.z, xl.w};
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const float uf = __uint_as_float((j & 1) ? (xw[j >> 1] & 0xffff0000u) : (xw[j >> 1] << 16));
+              float uf = __uint_as_float((j & 1) ? (xw[j >> 1] & 0xffff0000u) : (xw[j >> 1] << 16));
+              if (SPLIT) uf += __uint_as_float((j & 1) ? (xlw[j >> 1] & 0xffff0000u) : (xlw[j >> 1] << 16));
               const float r = fmaf(uf, dv[j], e[8 * u + j]);
               rsum = fmaf(r, r, rsum);
             }
@@ -441,11 +483,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         for (int u = 0; u < 4; ++u) {
           if (u < nun) {
             uint4* p = reinterpret_cast<uint4*>(urow + (((u0 + u) ^ usw) << 4));
+            uint4* pl = reinterpret_cast<uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
             float dv[8];
-            uint32_t xw[4] = {0u, 0u, 0u, 0u};
+            uint32_t xw[4] = {0u, 0u, 0u, 0u}, xlw[4] = {0u, 0u, 0u, 0u};
             if (mode == 1) {
               const uint4 x = *p;
               xw[0] = x.x; xw[1] = x.y; xw[2] = x.z; xw[3] = x.w;
+              if (SPLIT) {
+                const uint4 y = *pl;
+                xlw[0] = y.x; xlw[1] = y.y; xlw[2] = y.z; xlw[3] = y.w;
+              }
               const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
               const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
               dv[0] = d0.x; dv[1] = d0.y; dv[2] = d0.z; dv[3] = d0.w;
@@ -454,19 +501,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 #pragma unroll
               for (int j = 0; j < 8; ++j) dv[j] = 0.f;
             }
-            uint32_t ow[4];
+            uint32_t ow[4], olw[4];
 #pragma unroll
             for (int j2 = 0; j2 < 4; ++j2) {
-              const float ulo = __uint_as_float(xw[j2] << 16), uhi = __uint_as_float(xw[j2] & 0xffff0000u);
-              const float nlo = fmaf(ulo, dv[2 * j2], -e[8 * u + 2 * j2]);
-              const float nhi = fmaf(uhi, dv[2 * j2 + 1], -e[8 * u + 2 * j2 + 1]);
-              const __nv_bfloat162 pr = __floats2bfloat162_rn(nlo, nhi);
+              // the two channels of word j2 (its low and high halves)
+              float ua = __uint_as_float(xw[j2] << 16), ub = __uint_as_float(xw[j2] & 0xffff0000u);
+              if (SPLIT) {
+                ua += __uint_as_float(xlw[j2] << 16);
+                ub += __uint_as_float(xlw[j2] & 0xffff0000u);
+              }
+              const float na = fmaf(ua, dv[2 * j2], -e[8 * u + 2 * j2]);
+              const float nb = fmaf(ub, dv[2 * j2 + 1], -e[8 * u + 2 * j2 + 1]);
+              const __nv_bfloat162 pr = __floats2bfloat162_rn(na, nb);
               ow[j2] = *reinterpret_cast<const uint32_t*>(&pr);
-              const float rlo = __uint_as_float(ow[j2] << 16), rhi = __uint_as_float(ow[j2] & 0xffff0000u);
-              acc[8 * u + 2 * j2] = valid ? fmaf(rlo, rlo, acc[8 * u + 2 * j2]) : acc[8 * u + 2 * j2];
-              acc[8 * u + 2 * j2 + 1] = valid ? fmaf(rhi, rhi, acc[8 * u + 2 * j2 + 1]) : acc[8 * u + 2 * j2 + 1];
+              float ra = __uint_as_float(ow[j2] << 16), rb = __uint_as_float(ow[j2] & 0xffff0000u);
+              if (SPLIT) {
+                const __nv_bfloat162 pl2 = __floats2bfloat162_rn(na - ra, nb - rb);
+                olw[j2] = *reinterpret_cast<const uint32_t*>(&pl2);
+                ra += __uint_as_float(olw[j2] << 16);
+                rb += __uint_as_float(olw[j2] & 0xffff0000u);
+              }
+              acc[8 * u + 2 * j2] = valid ? fmaf(ra, ra, acc[8 * u + 2 * j2]) : acc[8 * u + 2 * j2];
+              acc[8 * u + 2 * j2 + 1] = valid ? fmaf(rb, rb, acc[8 * u + 2 * j2 + 1]) : acc[8 * u + 2 * j2 + 1];
             }
             *p = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+            if (SPLIT) *pl = make_uint4(olw[0], olw[1], olw[2], olw[3]);
           }
         }
         ptx::fence_proxy_async_smem();    // U' in shared memory -> the TMA store
@@ -474,9 +533,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       ptx::named_bar_sync(1, 32 * EPI_WARPS);
       if (ew == 0 && lane == 0) {
         if (wrU) {
-          for (int bx = 0; bx < nbox; ++bx)
-            ptx::tma_store_4d(J.tmapU, sU + (size_t)us * USTAGE + (size_t)bx * CHUNK, ct * 128 + bx * 64, tw * TW,
-                              th * TH, t);
+          for (int half = 0; half < NIMG; ++half)
+            for (int bx = 0; bx < nbox; ++bx)
+              ptx::tma_store_4d(half ? J.tmapUlo : J.tmapU, sU + (size_t)us * ustage + (size_t)half * USTAGE +
+                                (size_t)bx * CHUNK, ct * 128 + bx * 64, tw * TW, th * TH, t);
           ptx::bulk_commit_group();
           ptx::bulk_wait_group_read0();   // the stage may be refilled once the store has read it
         }
@@ -812,7 +872,8 @@ __global__ void build_B2_kernel(Shared sh, TcGeom g) {
 // stored as Xc[c][wp / 8][hp][tp][wp % 8]: the k3 frames of a 16-byte w-segment are
 // adjacent, so one TMA box row of the tile halo is k3 * 16 bytes. A thread reads the
 // NC + 7 source values of one (w-segment, hp, tp) once and writes all NC copies.
-template <int NC>
+// SPLIT: copies NC..2NC-1 hold the lo parts, bf16(x - bf16(x)), of copies 0..NC-1.
+template <int NC, bool SPLIT>
 __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
   const JobDev& J = sh.jobs[blockIdx.y];
   const float* src = from_L ? J.L : J.X;
@@ -840,9 +901,15 @@ __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       __align__(16) __nv_bfloat16 v[8];
+      __align__(16) __nv_bfloat16 vl[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(win[NC - 1 - c + e]);
+      for (int e = 0; e < 8; ++e) {
+        const float x = win[NC - 1 - c + e];
+        v[e] = __float2bfloat16(x);
+        if (SPLIT) vl[e] = __float2bfloat16(x - __bfloat162float(v[e]));
+      }
       *reinterpret_cast<uint4*>(dst + (size_t)c * plane) = *reinterpret_cast<const uint4*>(v);
+      if (SPLIT) *reinterpret_cast<uint4*>(dst + (size_t)(NC + c) * plane) = *reinterpret_cast<const uint4*>(vl);
     }
   }
 }
@@ -900,6 +967,25 @@ __global__ void __launch_bounds__(256) gather_tc_kernel(Shared sh) {
     J.lpart[blockIdx.x] = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
 }
 
+// One CTA waits, through the solve kernels' bounded wait, on an mbarrier that nothing
+// arrives on; the wait gives up after limit_ns and the kernel reports it in *status (the
+// same path a solve kernel takes when a copy or an MMA never completes). Nothing is in
+// flight and no tensor memory is held, so the kernel simply returns.
+__global__ void bounded_wait_check_kernel(uint64_t limit_ns, int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&bar, 1);
+    abort = 0;
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = ptx::mbar_wait_abortable(&bar, 0, &abort, limit_ns);
+    *status = ok ? 0 : 1;
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -922,6 +1008,12 @@ EncodeTiledFn encoder() {
 // ---------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------
+TcGeom tc_geom(int k1, int k2, int k3, int kc) {
+  TcGeom g = make_geom(k1, k2, k3);
+  g.kc = kc;
+  return g;
+}
+
 bool tc_supported(int k1, int k2, int k3, std::string* why) {
   const TcGeom g = make_geom(k1, k2, k3);
   auto no = [&](const char* m) { if (why) *why = m; return false; };
@@ -942,7 +1034,8 @@ cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, Tc
   out->g = g;
   const int k = g.k;
   const size_t per = (size_t)g.nch_f * CHUNK;
-  std::vector<uint8_t> img((size_t)g.nct * per, 0);
+  const int nimg = g.split_ok ? 2 : 1;                // hi images, then lo images
+  std::vector<uint8_t> img((size_t)nimg * g.nct * per, 0);
   const int per8 = g.R8 / 8;
   for (int ct = 0; ct < g.nct; ++ct)
     for (int r = 0; r < 128; ++r) {
@@ -955,11 +1048,17 @@ cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, Tc
         if (rr >= g.R) continue;
         const int u = g.R - 1 - rr, sh = u / k3, st = u % k3;
         const int s = (st * k1 + sh) * k2 + sw;
-        const __nv_bfloat16 b = __float2bfloat16((float)V64[(size_t)ch * k + s]);
+        const float vf = (float)V64[(size_t)ch * k + s];
+        const __nv_bfloat16 b = __float2bfloat16(vf);
         const int chunk = kap / 64, col = kap % 64;
         const size_t off = (size_t)ct * per + (size_t)chunk * CHUNK + (r / 8) * 1024 + (r % 8) * 128 +
                            (((col / 8) ^ (r % 8)) * 16) + (col % 8) * 2;
         memcpy(&img[off], &b, 2);
+        if (nimg == 2) {
+          // lo part of V^T: the remainder of the FP64 value after the hi part
+          const __nv_bfloat16 bl = __float2bfloat16((float)(V64[(size_t)ch * k + s] - (double)__bfloat162float(b)));
+          memcpy(&img[(size_t)g.nct * per + off], &bl, 2);
+        }
       }
     }
   for (int i = 0; i < 64; ++i) { out->boff[i] = 0; out->kstr[i] = 0; }
@@ -992,27 +1091,32 @@ size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g) {
   const int ntiles = ((H + TH - 1) / TH) * ((W + TW - 1) / TW) * T;
   size_t b = 0;
   auto add = [&](size_t n) { b += (n + 255) / 256 * 256; };
-  add((size_t)g.ncopy * Tp * Hp * Wp * 2);             // Xc
+  add((size_t)(g.split_ok ? 2 : 1) * g.ncopy * Tp * Hp * Wp * 2);   // Xc (and its lo copies)
   add((size_t)H * W * T * 4);                          // col2im sums (Delta)
   add((size_t)g.ntt * g.nch_a * CHUNK);                // V D images
-  add(3 * sizeof(CUtensorMap));                        // TMA maps
+  add(4 * sizeof(CUtensorMap));                        // TMA maps
   return b;
 }
 
-cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, size_t total) {
+size_t tc_tmap_bytes() { return 4 * sizeof(CUtensorMap); }
+
+cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, size_t total, void* host_tmp,
+                         cudaStream_t st) {
   const TcGeom& g = v.g;
   auto take = [&](size_t n) { void* p = base + off; off += (n + 255) / 256 * 256; return p; };
   int Tp, Hp, Wp;
   xc_dims(g, d->H, d->W, d->T, Tp, Hp, Wp);
   d->xTp = Tp; d->xHp = Hp; d->xWp = Wp;
-  d->Xc = (__nv_bfloat16*)take((size_t)g.ncopy * Tp * Hp * Wp * 2);
+  const int ncp = (g.split_ok ? 2 : 1) * g.ncopy;        // copies in Xc (hi, then lo)
+  d->Xc = (__nv_bfloat16*)take((size_t)ncp * Tp * Hp * Wp * 2);
   d->G = (float*)take((size_t)d->m * 4);
   d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * CHUNK);
-  CUtensorMap* tm = (CUtensorMap*)take(3 * sizeof(CUtensorMap));
+  CUtensorMap* tm = (CUtensorMap*)take(4 * sizeof(CUtensorMap));
   if (off > total) return cudaErrorInvalidValue;
   EncodeTiledFn enc = encoder();
   if (!enc) return cudaErrorNotSupported;
-  CUtensorMap hm[3];
+  CUtensorMap hm[4];
+  memset(hm, 0, sizeof hm);
   const cuuint32_t es[4] = {1, 1, 1, 1};
   // Xc as [c][wc][hp][tp*8]: dim0 = (tp, w%8) flattened, dim1 = hp, dim2 = wc, dim3 = c.
   // Map 0 loads all ncopy copies of a w-chunk; map 1 only the first k2 - 8 (the last
@@ -1020,7 +1124,7 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   for (int mi = 0; mi < 2; ++mi) {
     const int nwcol = Wp / 8;
     const int nc = mi == 0 ? g.ncopy : std::max(1, g.k2 - 8 * (g.nwc - 1));
-    cuuint64_t dims[4] = {(cuuint64_t)Tp * 8, (cuuint64_t)Hp, (cuuint64_t)nwcol, (cuuint64_t)g.ncopy};
+    cuuint64_t dims[4] = {(cuuint64_t)Tp * 8, (cuuint64_t)Hp, (cuuint64_t)nwcol, (cuuint64_t)ncp};
     cuuint64_t str[3] = {(cuuint64_t)Tp * 16, (cuuint64_t)Hp * Tp * 16, (cuuint64_t)nwcol * Hp * Tp * 16};
     cuuint32_t box[4] = {(cuuint32_t)(8 * g.k3), (cuuint32_t)g.Hh, 1, (cuuint32_t)nc};
     if (enc(&hm[mi], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, d->Xc, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1039,26 +1143,57 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
         CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaMemcpy(tm, hm, sizeof hm, cudaMemcpyHostToDevice);
+  memcpy(host_tmp, hm, sizeof hm);
+  cudaError_t e = cudaMemcpyAsync(tm, host_tmp, sizeof hm, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   d->tmapX = &tm[0];
   d->tmapX2 = &tm[1];
   d->tmapU = &tm[2];
+  d->tmapUlo = &tm[3];                     // encoded by tc_attach_ulo
+  d->Ulo = nullptr;
   return cudaSuccess;
 }
 
-cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st) {
+// Give a job the lo part of U (m x kc BF16 at `ulo`, zeroed by the caller when U's value
+// is to be kept) and encode its TMA map into the job's fourth map slot.
+cudaError_t tc_attach_ulo(JobDev* d, const TcVData& v, void* ulo, void* host_tmp, cudaStream_t st) {
+  EncodeTiledFn enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const TcGeom& g = v.g;
+  CUtensorMap m;
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  cuuint64_t dims[4] = {(cuuint64_t)g.kc, (cuuint64_t)d->W, (cuuint64_t)d->H, (cuuint64_t)d->T};
+  cuuint64_t str[3] = {(cuuint64_t)g.kc * 2, (cuuint64_t)d->W * g.kc * 2, (cuuint64_t)d->H * d->W * g.kc * 2};
+  cuuint32_t box[4] = {64, TW, TH, 1};
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, ulo, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  memcpy(host_tmp, &m, sizeof m);
+  cudaError_t e = cudaMemcpyAsync(const_cast<void*>(d->tmapUlo), host_tmp, sizeof m, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  d->Ulo = ulo;
+  return cudaSuccess;
+}
+
+template <bool SPLIT>
+static void launch_prepare_X_t(const Shared& sh, const TcGeom& g, int from_L, cudaStream_t st) {
   const dim3 grid(608, sh.njobs);
-  switch (v.g.ncopy) {
-    case 1: prepare_X_kernel<1><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
-    case 2: prepare_X_kernel<2><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
-    case 3: prepare_X_kernel<3><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
-    case 4: prepare_X_kernel<4><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
-    case 5: prepare_X_kernel<5><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
-    case 6: prepare_X_kernel<6><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
-    case 7: prepare_X_kernel<7><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
-    default: prepare_X_kernel<8><<<grid, 256, 0, st>>>(sh, v.g, from_L); break;
+  switch (g.ncopy) {
+    case 1: prepare_X_kernel<1, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
+    case 2: prepare_X_kernel<2, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
+    case 3: prepare_X_kernel<3, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
+    case 4: prepare_X_kernel<4, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
+    case 5: prepare_X_kernel<5, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
+    case 6: prepare_X_kernel<6, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
+    case 7: prepare_X_kernel<7, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
+    default: prepare_X_kernel<8, SPLIT><<<grid, 256, 0, st>>>(sh, g, from_L); break;
   }
+}
+
+cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st, bool split) {
+  if (split) launch_prepare_X_t<true>(sh, v.g, from_L, st);
+  else launch_prepare_X_t<false>(sh, v.g, from_L, st);
   return cudaGetLastError();
 }
 
@@ -1096,7 +1231,8 @@ int dev_sms() {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     f.sms = n > 0 ? n : 1;
-    cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     for (AdjKernel kf : {adj_tc_kernel<0>, adj_tc_kernel<3>, adj_tc_kernel<5>, adj_tc_kernel<7>, adj_tc_kernel<9>})
       cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     f.ready = true;
@@ -1105,7 +1241,8 @@ int dev_sms() {
 }
 }  // namespace
 
-cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st) {
+cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st, bool split) {
+  if (split && !v.g.split_ok) return cudaErrorInvalidValue;
   FwdArgs a;
   a.sh = sh;
   a.g = v.g;
@@ -1116,9 +1253,10 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
     if (v.kstr[i] != 128u || v.boff[i] != (uint32_t)((i / a.tab.hp) * v.g.region_bytes + (i % a.tab.hp) * 256))
       a.tab.reg = 0;
   a.mode = mode;
-  const size_t smem = fwd_smem(v.g);
+  const size_t smem = fwd_smem(v.g, split);
   const int per = tc_fwd_slots(sh, v);
-  fwd_tc_kernel<<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  if (split) fwd_tc_kernel<true><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  else fwd_tc_kernel<false><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1137,6 +1275,11 @@ cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st) {
   a.g = v.g;
   const int per = std::max(1, std::min(dev_sms() / v.g.ntt, sh.total_tiles));
   adj_kernel_for(v.g)<<<per * v.g.ntt, TC_THREADS, adj_smem(v.g), st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_bounded_wait_check(uint64_t limit_ns, int* dstatus, cudaStream_t st) {
+  bounded_wait_check_kernel<<<1, 32, 0, st>>>(limit_ns, dstatus);
   return cudaGetLastError();
 }
 

@@ -1,12 +1,14 @@
 // icnnm_learn_V_noalloc: learning V (the same Gram accumulation and FP64 Jacobi
 // eigensolver as icnnm_learn_V) without allocating any memory.
 //
-// For callers that cannot call cudaMalloc: code that runs while a CUDA graph is being
-// captured, code inside a host framework whose memory is handed out by its own pool, or
-// latency-bound code that must not trigger the device-wide synchronisation an allocation
-// can cause. The caller passes device-resident inputs and outputs; every intermediate
+// For callers that cannot call cudaMalloc themselves: code inside a host framework that
+// hands out device memory only from its own pool (an allocation behind its back would
+// break its accounting or fail against its reservation), or latency-bound code that must
+// not trigger the device-wide synchronisation a cudaMalloc/cudaFree can cause. The caller
+// passes device-resident inputs and outputs on the current device; every intermediate
 // lives in one file-scope device array of fixed size (about 2.1 MiB) that every GPU that
-// loads this library holds until the process exits.
+// loads this library holds until the process exits. The call is blocking (it
+// synchronises the caller's stream).
 #include <stdio.h>
 #include <string.h>
 
@@ -67,13 +69,16 @@ icnnm_status fail(icnnm_status st, const char* msg) {
   return st;
 }
 
-bool on_device(const void* p) {
+// 1: device (or managed) memory of device `dev`; 0: host memory; -1: device memory of
+// another device (the kernels would dereference a peer address).
+int where(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return 0;
+  return a.device == dev ? 1 : -1;
 }
 
 }  // namespace
@@ -93,20 +98,27 @@ extern "C" icnnm_status icnnm_learn_V_noalloc(const int64_t kdims[3], int32_t b,
   if (k > NA_MAXK) return fail(ICNNM_EINVAL, "k = k1*k2*k3 exceeds the static scratch limit of 256");
   if (nlag > NA_MAXLAG) return fail(ICNNM_EINVAL, "(2k1-1)(2k2-1)(2k3-1) exceeds the static scratch limit of 4096");
   if (b < 1 || b > NA_MAXB) return fail(ICNNM_EINVAL, "b must be in [1, 256]");
-  if (learn_smem_bytes(k1, k2, k3) > 220 * 1024) return fail(ICNNM_EUNSUPPORTED, "kernel too large");
+  if (learn_smem_bytes(k1, k2, k3) > 220 * 1024)
+    return fail(ICNNM_EUNSUPPORTED, "the Gram halo of this kernel needs more than 220 KiB of shared memory");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ICNNM_ECUDA, cudaGetErrorString(e));
   int ptrsdims[3 * NA_MAXB];
   for (int j = 0; j < b; ++j) {
     const icnnm_shape& s = shapes[j];
     if (s.ndim != 2 && s.ndim != 3) return fail(ICNNM_EINVAL, "ndim must be 2 or 3");
     const int H = (int)s.dims[0], W = (int)s.dims[1], T = s.ndim == 3 ? (int)s.dims[2] : 1;
     if (H < k1 || W < k2 || T < k3) return fail(ICNNM_EINVAL, "every dim must be at least the kernel's");
-    if (!tensors[j] || !on_device(tensors[j])) return fail(ICNNM_EINVAL, "reference tensors must be device memory");
+    if (!tensors[j] || where(tensors[j], dev) != 1)
+      return fail(ICNNM_EINVAL, "reference tensors must be device memory of the current device");
     ptrsdims[3 * j] = H; ptrsdims[3 * j + 1] = W; ptrsdims[3 * j + 2] = T;
   }
-  const bool vdev = on_device(V_out), edev = eig_out && on_device(eig_out);
+  const int vw = where(V_out, dev), ew = eig_out ? where(eig_out, dev) : 0;
+  if (vw < 0 || ew < 0) return fail(ICNNM_EINVAL, "V_out and eig_out must be host memory or memory of the current device");
+  const bool vdev = vw == 1, edev = ew == 1;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Scratch* S = nullptr;
-  cudaError_t e = scratch_address(&S);
+  e = scratch_address(&S);
   if (e != cudaSuccess) return fail(ICNNM_ECUDA, cudaGetErrorString(e));
   // inputs of this call into the shared scratch (plain copies; nothing is allocated)
   if ((e = cudaMemcpyAsync(S->ptrs, tensors, sizeof(float*) * b, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -128,7 +140,11 @@ extern "C" icnnm_status icnnm_learn_V_noalloc(const int64_t kdims[3], int32_t b,
     return fail(ICNNM_ECUDA, cudaGetErrorString(e));
   double* vdst = vdev ? V_out : S->vout;
   double* edst = edev ? eig_out : S->evals;
-  if ((e = learn_eig(S->gram, S->vacc, (int)k, edst, vdst, &S->info, st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(&S->info, 0, sizeof(int), st)) != cudaSuccess ||
+      (e = learn_eig(S->gram, S->vacc, (int)k, edst, vdst, &S->info, st)) != cudaSuccess)
+    return fail(ICNNM_ECUDA, cudaGetErrorString(e));
+  int info = 0;
+  if ((e = cudaMemcpyAsync(&info, &S->info, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return fail(ICNNM_ECUDA, cudaGetErrorString(e));
   if (!vdev && (e = cudaMemcpyAsync(V_out, S->vout, sizeof(double) * k * k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return fail(ICNNM_ECUDA, cudaGetErrorString(e));
@@ -136,5 +152,6 @@ extern "C" icnnm_status icnnm_learn_V_noalloc(const int64_t kdims[3], int32_t b,
       (e = cudaMemcpyAsync(eig_out, S->evals, sizeof(double) * k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return fail(ICNNM_ECUDA, cudaGetErrorString(e));
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(ICNNM_ECUDA, cudaGetErrorString(e));
+  if (info < 0) return fail(ICNNM_ENOCONV, "the FP64 Jacobi eigensolver did not converge within 30 sweeps");
   return ICNNM_OK;
 }

@@ -49,26 +49,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: returns false (and leaves the caller to record a status) after ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Limit of every bounded wait of the solve kernels.
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+// Bounded wait: returns false (and leaves the caller to record a status) after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > 2000000000ull) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
 }
 
 // Bounded wait that also gives up once another thread of the CTA has raised `abort`
 // (a shared-memory flag); a wait that times out raises it. Lets every role of a
 // pipelined kernel leave its loop promptly after one wait has failed.
-__device__ __forceinline__ bool mbar_wait_abortable(uint64_t* bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                    uint64_t limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > 2000000000ull) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort = 1;
       return false;
     }

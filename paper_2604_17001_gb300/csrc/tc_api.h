@@ -27,6 +27,12 @@ struct TcGeom {
   int slo[16];      // first frame (st) reached by each tap tile
   int rpg;          // adjoint: whole tap rows (k2 taps) per 32-column group (0: taps in order)
   int nus;          // forward U tile stages in shared memory (1 or 2)
+  // split forward (ICNNM_BF16X3 and the finish of BF16 jobs): the operand and V^T as
+  // hi + lo BF16 pairs, three products per tile, U stored as a hi + lo pair
+  int split_ok;     // 1: the split forward fits in shared memory for these kernel dims
+  int lo_off;       // byte offset of the lo copies in a split halo stage (after hi + 16 zero rows)
+  int stage_bytes_s;// one split halo stage: hi copies, 16 zero rows, lo copies, 16 zero rows
+  int nus_s;        // U tile stages (each a hi and a lo tile) of the split forward
   int pitch, HBp;   // shared-memory row pitch of the halo buffers (an odd multiple of 8,
                     // >= Wb, so 4 rows x 8 voxels hit 32 banks) and k3*Hb*pitch
 };
@@ -34,20 +40,31 @@ struct TcGeom {
 // Per-V device data of the tensor-core path.
 struct TcVData {
   TcGeom g{};
-  __nv_bfloat16* VtImg = nullptr;   // nct forward A images, nch_f * 16 KiB each
+  __nv_bfloat16* VtImg = nullptr;   // nct forward A images of V^T, nch_f * 16 KiB each; when
+                                    // g.split_ok, nct more of V^T - bf16(V^T) (the lo part)
   uint32_t boff[64];                // forward: byte offset of each MMA's first K-group
   uint32_t kstr[64];                // forward: byte distance to its second K-group
 };
 
 bool tc_supported(int k1, int k2, int k3, std::string* why);
+// Geometry of the tensor-core passes for these kernel dims (kc: the channel stride).
+TcGeom tc_geom(int k1, int k2, int k3, int kc);
 cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out);
 void tc_free_vdata(TcVData* v);
 size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g);
-// Carve the tensor-core buffers of a job from its allocation and encode its TMA maps.
-cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, size_t total);
+// Carve the tensor-core buffers of a job from its allocation and encode its TMA maps;
+// the maps are written into host_tmp (tc_tmap_bytes(), pinned) and copied to the device
+// on `st` (the caller keeps host_tmp until that copy has completed).
+size_t tc_tmap_bytes();
+cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, size_t total, void* host_tmp,
+                         cudaStream_t st);
 int tc_nrp(int k);
-cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st);
-cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st);
+// split: also write the lo copies (the operand of the split forward)
+cudaError_t tc_launch_prepare_X(const Shared& sh, const TcVData& v, int from_L, cudaStream_t st, bool split = false);
+// split: the three-product forward with U as a hi + lo pair (needs v.g.split_ok and every
+// job's Ulo attached)
+cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStream_t st, bool split = false);
+cudaError_t tc_attach_ulo(JobDev* d, const TcVData& v, void* ulo, void* host_tmp, cudaStream_t st);
 // CTA slots per channel tile of the forward launch: the update modes write one
 // column-partial row group per (slot, job), min(slots, ntiles) groups per job.
 int tc_fwd_slots(const Shared& sh, const TcVData& v);
@@ -55,5 +72,7 @@ int tc_fwd_slots(const Shared& sh, const TcVData& v);
 cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st);
 cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st);
 cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st);
+// A bounded mbarrier wait that nothing completes, given up after limit_ns: *dstatus = 1.
+cudaError_t tc_bounded_wait_check(uint64_t limit_ns, int* dstatus, cudaStream_t st);
 
 }  // namespace icnnm

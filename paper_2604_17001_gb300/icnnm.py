@@ -16,8 +16,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libicnnm.so")
 
-OK, EINVAL, ENOMEM, EAGAIN, ENOTFOUND, ECUDA, ETIMEOUT, ECANCELED, EUNSUPPORTED = range(9)
-FP32, BF16 = 0, 1
+OK, EINVAL, ENOMEM, EAGAIN, ENOTFOUND, ECUDA, ETIMEOUT, ECANCELED, EUNSUPPORTED, ENOCONV = range(10)
+FP32, BF16, BF16X3 = 0, 1, 2
 
 
 class icnnm_shape(C.Structure):
@@ -32,11 +32,11 @@ class icnnm_params(C.Structure):
 
 class icnnm_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("residual", C.c_double), ("objective", C.c_double),
-                ("theta", C.c_double), ("seconds", C.c_double)]
+                ("theta", C.c_double), ("seconds", C.c_double), ("latency", C.c_double)]
 
     def as_dict(self):
         return dict(iters=self.iters, residual=self.residual, objective=self.objective,
-                    theta=self.theta, seconds=self.seconds)
+                    theta=self.theta, seconds=self.seconds, latency=self.latency)
 
 
 class ICNNMError(RuntimeError):
@@ -74,6 +74,9 @@ def load(path: str = LIB_PATH):
         "icnnm_cancel": ([P, U64], I32),
         "icnnm_profile_enable": ([P, I32], I32),
         "icnnm_profile_read": ([P, I32, C.POINTER(D), C.POINTER(I64)], I32),
+        "icnnm_profile_voxels": ([P, I32, C.POINTER(I64)], I32),
+        "icnnm_job_bytes": ([P, C.POINTER(icnnm_shape), I32, C.POINTER(C.c_size_t)], I32),
+        "icnnm_check_bounded_wait": ([P, I64], I32),
         "icnnm_cnnm_solve": ([P, C.POINTER(icnnm_shape), P, P, C.POINTER(icnnm_params), P,
                               C.POINTER(icnnm_stats)], I32),
         "icnnm_spectral_diagnostics": ([P, C.POINTER(icnnm_shape), P, P, D, P, C.POINTER(I32), C.POINTER(D),
@@ -123,7 +126,7 @@ def params(**kw) -> icnnm_params:
         if k == "lam":
             k = "lambda_"
         if k == "prec" and isinstance(v, str):
-            v = {"fp32": FP32, "bf16": BF16}[v]
+            v = {"fp32": FP32, "bf16": BF16, "bf16x3": BF16X3}[v]
         setattr(p, k, v)
     return p
 
@@ -145,7 +148,8 @@ def icnnm_learn_V_noalloc(refs, kdims, V_out=None, eig_out=None, stream=None):
     own = V_out is None
     if own:
         V_out = np.zeros((k, k), dtype=np.float64)
-        eig_out = np.zeros(k, dtype=np.float64) if eig_out is None else eig_out
+        if eig_out is None:
+            eig_out = np.zeros(k, dtype=np.float64)
     st = lib.icnnm_learn_V_noalloc((C.c_int64 * 3)(*kd), b, shapes, ptrs, _ptr(V_out), _ptr(eig_out),
                                    C.c_void_p(stream) if stream else None)
     if st != OK:
@@ -312,3 +316,14 @@ class Context:
 
     def icnnm_cancel(self, job_id: int):
         self._check(self.lib.icnnm_cancel(self.h, job_id))
+
+    def icnnm_job_bytes(self, dims, kdims, prec="bf16") -> int:
+        s = make_shape(dims, kdims)
+        n = C.c_size_t()
+        self._check(self.lib.icnnm_job_bytes(self.h, C.byref(s), {"fp32": FP32, "bf16": BF16, "bf16x3": BF16X3}.get(prec, prec),
+                                             C.byref(n)))
+        return n.value
+
+    def icnnm_check_bounded_wait(self, limit_ns: int) -> int:
+        """Status of the bounded-wait check (ETIMEOUT when the wait gave up as it should)."""
+        return self.lib.icnnm_check_bounded_wait(self.h, int(limit_ns))

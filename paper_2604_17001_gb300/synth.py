@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "video", "mask_uniform", "mask_last_frames", "mask_every_other_frame",
     "mask_drop_frames_plus_random", "mask_block_holes", "mask_mixed",
-    "workload", "WORKLOADS", "seed_for", "image_jobs",
+    "workload", "WORKLOADS", "seed_for", "image_jobs", "serving_shapes", "serving_job", "serving_refs",
 ]
 
 
@@ -224,6 +224,32 @@ def batch_jobs(n_jobs: int, cfg: int = 4, hw_range=(32, 192), t_range=(8, 48)):
         M = np.where(mask.astype(bool), L0, 0).astype(np.float32)
         jobs.append(dict(L0=L0, M=M, mask=mask, dims=(H, W, T), family=fam))
     return jobs
+
+
+SERVING_HW = (32, 256)
+SERVING_T = (8, 64)
+
+
+def serving_shapes(n_requests: int):
+    """Shapes of the serving stream: H, W uniform in {32..256} step 16, T uniform in
+    {8..64} (the batching family's draws with the serving ranges)."""
+    return batch_shapes(n_requests, seed_for(5, 900), SERVING_HW, SERVING_T)
+
+
+def serving_job(j: int, shapes):
+    """Request j of the serving stream (shapes from serving_shapes): dict(L0, M, mask,
+    dims, family), generated on its own, identical to the j-th entry of
+    batch_jobs(n, cfg=5, hw_range=SERVING_HW, t_range=SERVING_T)."""
+    H, W, T = shapes[j]
+    L0 = video(H, W, T, seed_for(5, 2000 + j))
+    mask, fam = mask_mixed(H, W, T, seed_for(5, 500) + 13 * j)
+    M = np.where(mask.astype(bool), L0, 0).astype(np.float32)
+    return dict(L0=L0, M=M, mask=mask, dims=(H, W, T), family=fam)
+
+
+def serving_refs():
+    """Reference tensors of the serving family's shared V: 32 videos of 64x64x16."""
+    return [video(64, 64, 16, seed_for(5, j)) for j in range(1, WORKLOADS[5]["n_ref"] + 1)]
 
 
 def image_jobs(n_images: int, missing: float = 0.5, dims=(200, 200)):

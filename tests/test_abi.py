@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings_and_defaults(lib):
-    for st in range(9):
+    for st in range(10):
         assert lib.icnnm_strerror(st)
     p = icnnm.icnnm_params()
     assert lib.icnnm_params_default(C.byref(p)) == 0

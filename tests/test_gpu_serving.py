@@ -1,0 +1,118 @@
+"""Serving engine behaviour on the GPU (no paper counterpart; the serving form of the
+solver): cancellation of queued and running jobs, admission held back by the HBM budget
+until memory frees, jobs of different V and precision admitted side by side, inputs and
+outputs in device memory, and the bounded device-side wait giving up with ETIMEOUT while
+the context stays usable."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import icnnm_oracle as O
+from paper_2604_17001_gb300 import icnnm, synth
+from tests.gpu_util import need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+KD = (5, 5, 3)
+
+
+def problem(dims, frac, seed):
+    H, W, T = dims
+    L0 = synth.video(H, W, T, seed=seed)
+    mask = synth.mask_uniform(H, W, T, frac, seed=seed + 1)
+    return np.where(mask.astype(bool), L0, 0).astype(np.float32), mask
+
+
+@pytest.fixture(scope="module")
+def V():
+    need_gpu()
+    return O.learn_V([synth.video(32, 32, 8, seed=501 + j) for j in range(3)], KD)[0]
+
+
+def test_cancel_queued_and_running_jobs(V):
+    M, mask = problem((64, 64, 16), 0.5, 11)
+    with icnnm.Context(0) as c0:
+        one = c0.icnnm_job_bytes((64, 64, 16), KD, "fp32")
+    # a budget that holds one job: the second one waits in the queue
+    with icnnm.Context(0, hbm_budget_bytes=int(1.5 * one)) as ctx:
+        a = ctx.icnnm_submit(M, mask, V, KD, prec="fp32", max_iters=20000)
+        b = ctx.icnnm_submit(M, mask, V, KD, prec="fp32", max_iters=20)
+        ctx.icnnm_cancel(b)                                      # still queued behind a
+        with pytest.raises(icnnm.ICNNMError) as e:
+            ctx.icnnm_wait(b, timeout_ms=60000)
+        assert e.value.status == icnnm.ECANCELED
+        time.sleep(0.2)
+        t0 = time.time()
+        ctx.icnnm_cancel(a)                                      # running
+        with pytest.raises(icnnm.ICNNMError) as e:
+            ctx.icnnm_wait(a, timeout_ms=60000)
+        assert e.value.status == icnnm.ECANCELED
+        assert time.time() - t0 < 30
+        # the context still serves
+        jid = ctx.icnnm_submit(M, mask, V, KD, prec="fp32", max_iters=15)
+        L = np.zeros_like(M)
+        r, st = ctx.icnnm_wait(jid, L_out=L, timeout_ms=60000)
+        Ls, _ = ctx.icnnm_solve(M, mask, V, KD, prec="fp32", max_iters=15)
+        assert r == icnnm.OK and np.array_equal(L, Ls)
+        with pytest.raises(icnnm.ICNNMError) as e:
+            ctx.icnnm_cancel(123456789)
+        assert e.value.status == icnnm.ENOTFOUND
+
+
+def test_budget_gated_admission_waits_for_memory(V):
+    # the budget holds one job at a time: the second job is admitted only once the first
+    # has finished and released its state, and both give their blocking-solve results
+    probs = [problem((48, 40, 12), 0.5, 21), problem((48, 40, 12), 0.4, 22)]
+    with icnnm.Context(0) as c0:
+        one = c0.icnnm_job_bytes((48, 40, 12), KD, "fp32")
+    with icnnm.Context(0, hbm_budget_bytes=int(1.5 * one)) as ctx:
+        ids = [ctx.icnnm_submit(M, mask, V, KD, prec="fp32", max_iters=300) for M, mask in probs]
+        sts = []
+        for (M, mask), jid in zip(probs, ids):
+            L = np.zeros_like(M)
+            r, st = ctx.icnnm_wait(jid, L_out=L, timeout_ms=120000)
+            assert r == icnnm.OK
+            Ls, _ = ctx.icnnm_solve(M, mask, V, KD, prec="fp32", max_iters=300)
+            assert np.array_equal(L, Ls)
+            sts.append(st)
+        queued = sts[1]["latency"] - sts[1]["seconds"]          # time the second job waited
+        assert queued >= 0.5 * sts[0]["seconds"], (queued, sts)
+
+
+def test_mixed_groups_admitted_together_and_device_buffers(V):
+    # jobs of two V's and two precisions interleaved in the queue are all admitted and
+    # stepped (each group in its own launch list); inputs and outputs in device memory
+    import torch
+    V2 = O.learn_V([synth.video(24, 24, 6, seed=601 + j) for j in range(3)], KD)[0]
+    probs = [problem((32, 24, 8), 0.5, 31 + i) for i in range(4)]
+    cfg = [(V, "bf16"), (V2, "fp32"), (V2, "bf16"), (V, "fp32")]
+    with icnnm.Context(0) as ctx:
+        ids = []
+        for (M, mask), (Vx, pr) in zip(probs, cfg):
+            ids.append(ctx.icnnm_submit(torch.from_numpy(M).cuda(), torch.from_numpy(mask).cuda(),
+                                        torch.from_numpy(Vx).cuda(), KD, prec=pr, max_iters=40))
+        for (M, mask), (Vx, pr), jid in zip(probs, cfg, ids):
+            Ld = torch.zeros(M.shape, dtype=torch.float32, device="cuda")
+            r, st = ctx.icnnm_wait(jid, L_out=Ld, timeout_ms=120000)
+            assert r == icnnm.OK and st["iters"] == 40
+            L = Ld.cpu().numpy()
+            Ls, _ = ctx.icnnm_solve(M, mask, Vx, KD, prec=pr, max_iters=40)
+            if pr == "fp32":
+                assert np.array_equal(L, Ls)
+            else:
+                assert rel(L, Ls) <= 1e-3
+            Lo, _ = O.icnnm_solve(M, mask, Vx, KD, max_iters=40)
+            assert rel(L, Lo) <= (1e-5 if pr == "fp32" else 1e-3)
+
+
+def test_bounded_wait_expires_and_context_stays_usable(V):
+    M, mask = problem((24, 24, 6), 0.5, 41)
+    with icnnm.Context(0) as ctx:
+        t0 = time.time()
+        assert ctx.icnnm_check_bounded_wait(5_000_000) == icnnm.ETIMEOUT      # 5 ms
+        assert time.time() - t0 < 5
+        assert ctx.icnnm_check_bounded_wait(10) == icnnm.EINVAL
+        L, st = ctx.icnnm_solve(M, mask, V, KD, prec="bf16", max_iters=30)
+        Lo, _ = O.icnnm_solve(M, mask, V, KD, max_iters=30)
+        assert rel(L, Lo) <= 1e-3

@@ -12,7 +12,7 @@ from tests.gpu_util import need_gpu, rel
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "bf16": 1e-3}
+TOL = {"fp32": 1e-5, "bf16": 1e-3, "bf16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +47,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("dims,kdims,mk,iters", CASES)
 def test_solve_matches_oracle(ctx, prec, dims, kdims, mk, iters):
     M, mask, V, _ = case(dims, kdims, **mk)
@@ -63,7 +63,7 @@ def test_solve_matches_oracle(ctx, prec, dims, kdims, mk, iters):
     msk = mask.astype(bool)
     assert np.array_equal(L[msk], M[msk])                      # P_Omega(L) = P_Omega(M) exactly
     assert st["iters"] == iters
-    assert abs(st["objective"] - so["objective"]) <= 10 * TOL[prec] * so["objective"]
+    assert abs(st["objective"] - so["objective"]) <= 10 * max(TOL[prec], 1e-5) * so["objective"]
     assert abs(st["theta"] - so["theta"]) <= 1e-6 * so["theta"]
 
 
@@ -254,11 +254,10 @@ def test_bf16_tolerance_finishes_in_fp32(ctx, serve):
 def test_bf16_tolerance_batch_mixed_phases(ctx):
     # Jobs of one batch reach the FP32 finish at different checks, so BF16 and FP32 lists
     # step side by side. Each job stops on an exact residual <= tol, near the oracle's
-    # stopping iteration, and equals the same job solved alone (to the BF16 bar). (The
-    # oracle's values are compared in the single-job test above: on small, sparsely
-    # observed jobs that run for hundreds of iterations the BF16 phase drifts past 1e-3
-    # from FP64, batched or not.) The residual is checked every iteration, so that the
-    # stopping points of the batch and of the single solves are at most an iteration apart.
+    # stopping iteration, equals the same job solved alone (to the BF16 bar), and is
+    # within the BF16 bar of the FP64 oracle run for the same iteration count. The
+    # residual is checked every iteration, so that the stopping points of the batch and
+    # of the single solves are at most an iteration apart.
     kd = (5, 5, 3)
     kw = dict(max_iters=1000, tol=1e-3, check_every=1)
     probs = [case(d, kd, frac=f, seed=s) for d, f, s in [((32, 24, 8), 0.5, 41), ((16, 40, 6), 0.3, 42),
@@ -273,6 +272,8 @@ def test_bf16_tolerance_batch_mixed_phases(ctx):
         Ls, sts = ctx.icnnm_solve(M, mask, V, kd, prec="bf16", **kw)
         assert abs(st["iters"] - sts["iters"]) <= 1
         assert rel(L, Ls) <= TOL["bf16"]
+        Lo, _ = O.icnnm_solve(M, mask, V, kd, max_iters=st["iters"])
+        assert rel(L, Lo) <= TOL["bf16"], (M.shape, st["iters"], rel(L, Lo))
 
 
 def test_bf16_batch_with_long_mixed_phase(ctx):
