@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--latency-requests", type=int, default=400, help="serving: requests of the Poisson run")
     ap.add_argument("--fp32-requests", type=int, default=12, help="serving: requests solved in plain FP32")
     ap.add_argument("--no-prediction", action="store_true", help="serving: skip the prediction sub-run")
+    ap.add_argument("--kdims", default=None,
+                    help="prediction: k1,k2,k3 of a resized case (7,7,3 takes the serving family's stored V)")
+    ap.add_argument("--dims", default=None,
+                    help="prediction: H,W,T of a resized case (e.g. 128,128,16 for profiling); the stored "
+                         "oracle run is then not compared")
     return ap.parse_args()
 
 
@@ -92,8 +97,10 @@ def max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
-def workload_inputs():
+def workload_inputs(dims=None):
     from paper_2604_17001_gb300 import synth
+    if dims:
+        return synth.workload(2, dims=tuple(int(x) for x in dims.split(",")), n_ref=2)
     return synth.workload(2)
 
 
@@ -212,13 +219,16 @@ def run_ours(args, ws, rank, local, sub=False):
     from paper_2604_17001_gb300 import icnnm
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload_inputs()
+    w = workload_inputs(args.dims)
     H, W, T = w["dims"]
     m = H * W * T
+    KDIMS = tuple(int(x) for x in args.kdims.split(",")) if args.kdims else (9, 9, 5)
     k = int(np.prod(KDIMS))
     stream = torch.cuda.current_stream(dev)
     ctx = icnnm.Context(local, stream=stream.cuda_stream)
     V, golden = load_V(w)
+    if KDIMS != (9, 9, 5):
+        V, golden = (np.load(SERVING_GOLDEN)["V"], None) if KDIMS == (7, 7, 3) else (None, None)
     learn = None
     refs_d = [torch.from_numpy(r).to(dev) for r in w["refs"]]
     if not args.no_learn or V is None:
@@ -286,7 +296,7 @@ def run_ours(args, ws, rank, local, sub=False):
     # accuracy against the stored FP64 oracle run (same V, same inputs)
     L = Ld.cpu().numpy()
     rel_err = None
-    if golden is not None and int(golden["iters"]) == args.iters:
+    if golden is not None and int(golden["iters"]) == args.iters and not args.dims:
         Lo = L.astype(np.float64).copy()
         Lo[golden["frames"]] = golden["L_missing"]
         rel_err = float(np.linalg.norm(L - Lo) / np.linalg.norm(Lo))
@@ -344,7 +354,7 @@ def run_ours(args, ws, rank, local, sub=False):
         fms = f0.elapsed_time(f1) / args.fp32_steps
         Lf = Ld.cpu().numpy()
         fe = None
-        if golden is not None and int(golden["iters"]) == args.iters:
+        if golden is not None and int(golden["iters"]) == args.iters and not args.dims:
             fe = float(np.linalg.norm(Lf - Lo) / np.linalg.norm(Lo))
         fp32 = {"value": 1e3 / fms, "unit": "solves/s", "ms_per_solve": fms, "steps": args.fp32_steps,
                 "rel_err_vs_oracle": fe}
@@ -731,11 +741,14 @@ def run_serving_bench(args, ws, rank, local):
     Ld = [torch.empty_like(M) for M in Md]
     torch.cuda.synchronize()
 
+    submit_s = []
+
     def wave(ids, host=False, outs=None):
         """Submit requests ids at once and collect them; returns (seconds, stats list)."""
         t0 = time.perf_counter()
         jids = [ctx.icnnm_submit(reqs[i][0] if host else Md[i], reqs[i][1] if host else Kd[i], V if host else Vd,
                                  kd, prec="bf16", **SERVING_KW) for i in ids]
+        submit_s.append(time.perf_counter() - t0)
         sts = []
         for n_, (i, jid) in enumerate(zip(ids, jids)):
             r_, st = ctx.icnnm_wait(jid, L_out=outs[n_] if host else Ld[i], timeout_ms=-1)
@@ -930,7 +943,10 @@ def run_serving_bench(args, ws, rank, local):
                         "stored FP64 oracle iterate of the same iteration count; observed entries are exact",
         "observed_entries_exact": obs_ok,
         "served": {"mean_iters": float(iters.mean()), "max_iters": int(iters.max()),
-                   "max_residual": float(resid.max()), "wave_seconds": times},
+                   "max_residual": float(resid.max()), "wave_seconds": times,
+                   "submit_seconds": submit_s[args.warmup:args.warmup + K],
+                   "mean_resident_s": float(np.mean([st["seconds"] for st in stats])),
+                   "mean_submit_to_done_s": float(np.mean([st["latency"] for st in stats]))},
         "fp32_plain": fp32, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(nall.value), "learn_V": learn, "prediction": pred,
     }

@@ -64,7 +64,7 @@ struct VData {
   float* dVf = nullptr;      // [k][kc]
   double* dV64 = nullptr;    // V64 on the device (column norms through the Gram)
   TcVData tc;                // BF16 images (tc_api.h)
-  bool tc_ready = false;
+  std::atomic<bool> tc_ready{false};
 };
 
 // ---------------------------------------------------------------------------------
@@ -146,7 +146,8 @@ struct icnnm_ctx {
   std::recursive_mutex mu;         // serialises device work of API calls and the server
   std::mutex err_mu;
   std::string last_err;
-  std::map<std::string, std::unique_ptr<VData>> vcache;
+  std::map<std::string, std::unique_ptr<VData>> vcache;   // inserted under mu and vmu
+  std::mutex vmu;                  // lookups of vcache without mu (the submitting side)
   // serving
   std::mutex qmu;
   std::condition_variable qcv;
@@ -335,14 +336,35 @@ std::string v_key(const double* V, int k1, int k2, int k3) {
   return buf;
 }
 
-VData* get_vdata(icnnm_ctx* c, const double* V, int k1, int k2, int k3, int prec) {
+std::vector<double> read_V(const double* V, int k) {
   if (!V) fail(ICNNM_EINVAL, "V is NULL");
-  const int k = k1 * k2 * k3;
   std::vector<double> hv((size_t)k * k);
   if (is_device_ptr(V)) CK(cudaMemcpy(hv.data(), V, hv.size() * 8, cudaMemcpyDeviceToHost));
   else memcpy(hv.data(), V, hv.size() * 8);
-  const std::string key = v_key(hv.data(), k1, k2, k3);
+  return hv;
+}
+
+// The cached per-V data if it exists and is ready for `prec` (no device work, no engine
+// mutex: the submitting side must not wait for a serving step), else nullptr.
+VData* find_vdata_ready(icnnm_ctx* c, const std::string& key, int prec) {
+  std::lock_guard<std::mutex> g(c->vmu);
   auto it = c->vcache.find(key);
+  if (it == c->vcache.end()) return nullptr;
+  VData* vd = it->second.get();
+  if (prec != ICNNM_FP32 && !vd->tc_ready) return nullptr;
+  if (prec == ICNNM_BF16X3 && !vd->tc.g.split_ok) return nullptr;
+  return vd;
+}
+
+VData* get_vdata(icnnm_ctx* c, const double* V, int k1, int k2, int k3, int prec) {
+  const int k = k1 * k2 * k3;
+  std::vector<double> hv = read_V(V, k);
+  const std::string key = v_key(hv.data(), k1, k2, k3);
+  std::map<std::string, std::unique_ptr<VData>>::iterator it;
+  {
+    std::lock_guard<std::mutex> g(c->vmu);
+    it = c->vcache.find(key);
+  }
   VData* vd;
   if (it == c->vcache.end()) {
     for (double x : hv)
@@ -369,6 +391,7 @@ VData* get_vdata(icnnm_ctx* c, const double* V, int k1, int k2, int k3, int prec
     CK(cudaMalloc(&nv->dV64, nv->V64.size() * 8));
     CK(cudaMemcpy(nv->dV64, nv->V64.data(), nv->V64.size() * 8, cudaMemcpyHostToDevice));
     vd = nv.get();
+    std::lock_guard<std::mutex> g(c->vmu);
     c->vcache[key] = std::move(nv);
   } else {
     vd = it->second.get();
@@ -1052,23 +1075,16 @@ void server_loop(icnnm_ctx* c) {
   }
 }
 
-// Submit-side preparation of a served job: validation of the shape and parameters on the
-// host, V looked up (or uploaded) under the engine's mutex, and the inputs copied into a
-// device staging buffer on the submitting side's stream, where they are checked (mask
-// 0/1, M finite on Omega, Omega non-empty) before the job is queued.
+// Submit-side preparation of a served job (its V already looked up): the inputs copied
+// into a device staging buffer on the submitting side's stream, where they are checked
+// (mask 0/1, M finite on Omega, Omega non-empty) before the job is queued.
 void prepare_submit(icnnm_ctx* c, Job& j, const icnnm_shape* shape, const float* M, const uint8_t* mask,
-                    const double* V, const icnnm_params& p) {
+                    const icnnm_params& p) {
   int H, W, T, k1, k2, k3;
   validate_shape(shape, H, W, T, k1, k2, k3);
-  validate_params(p);
   if (!M || !mask) fail(ICNNM_EINVAL, "M and mask must not be NULL");
   j.H = H; j.W = W; j.T = T; j.m = (long long)H * W * T;
   j.p = p;
-  {
-    std::lock_guard<std::recursive_mutex> g(c->mu);
-    j.vd = get_vdata(c, V, k1, k2, k3, p.prec);
-    ensure_tc(j.vd, p.prec);
-  }
   std::lock_guard<std::mutex> sg(c->submu);
   const size_t mb = (size_t)j.m * 4, kb = (size_t)j.m;
   const size_t flag_off = (mb + kb + 15) / 16 * 16;
@@ -1172,6 +1188,10 @@ icnnm_status icnnm_create(icnnm_ctx** out, int device, size_t budget, void* stre
   if (cudaMemPoolCreate(&c->pool, &pp) != cudaSuccess) { cudaGetLastError(); c->pool = nullptr; return undo(ICNNM_ECUDA); }
   uint64_t keep = c->budget;
   cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  // an allocation on the submitting side's stream must not wait for memory that the
+  // serving stream frees later in its own order: no cross-stream reuse dependencies
+  int no_deps = 0;
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no_deps);
   *out = c;
   return ICNNM_OK;
 }
@@ -1514,14 +1534,21 @@ icnnm_status icnnm_submit(icnnm_ctx* c, const icnnm_shape* shape, const float* M
     validate_shape(shape, H, W, T, k1, k2, k3);
     validate_params(p);
     {
-      std::lock_guard<std::recursive_mutex> g(c->mu);
-      VData* vd = get_vdata(c, V, k1, k2, k3, p.prec);
-      ensure_tc(vd, p.prec);
+      // V: the cached data without the engine's mutex when it is ready; built under it
+      // (once per V and precision) otherwise
+      const std::vector<double> hv = read_V(V, k1 * k2 * k3);
+      VData* vd = find_vdata_ready(c, v_key(hv.data(), k1, k2, k3), p.prec);
+      if (!vd) {
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        vd = get_vdata(c, hv.data(), k1, k2, k3, p.prec);
+        ensure_tc(vd, p.prec);
+      }
       const int nrp = std::max(fwd_fp32_nrp(vd->k), tc_nrp(vd->k));
       if (job_bytes(H, W, T, vd->k, vd->kc, p.prec, nrp, &vd->tc.g) > c->budget)
         fail(ICNNM_ENOMEM, "the job alone exceeds the HBM budget");
+      j->vd = vd;
     }
-    prepare_submit(c, *j, shape, M, mask, V, p);
+    prepare_submit(c, *j, shape, M, mask, p);
   } catch (StatusFail& f) {
     return report(c, f);
   } catch (CudaFail& f) {
