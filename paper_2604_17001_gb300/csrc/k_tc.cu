@@ -60,7 +60,9 @@ constexpr int SMEM_LIMIT = 227 * 1024;
 int rup(int x, int a) { return (x + a - 1) / a * a; }
 size_t fwd_smem_n(const TcGeom& g, int nus, bool split = false);
 
-TcGeom make_geom(int k1, int k2, int k3) {
+size_t adj_smem(const TcGeom& g);
+
+TcGeom make_geom(int k1, int k2, int k3, int gpt_max) {
   TcGeom g{};
   g.k1 = k1; g.k2 = k2; g.k3 = k3; g.k = k1 * k2 * k3; g.kc = rup(g.k, 16);
   // each w-run of taps is padded to a multiple of 16 (two 8-row K-groups): every MMA then
@@ -80,22 +82,35 @@ TcGeom make_geom(int k1, int k2, int k3) {
   // adjoint tap columns: whole tap rows per 32-column group for the kernel widths with a
   // compile-time col2im (3, 5, 7, 9), taps in order otherwise
   g.rpg = (k2 == 3 || k2 == 5 || k2 == 7 || k2 == 9) ? 32 / k2 : 0;
-  g.ntt = g.rpg ? ((k1 * k3 + g.rpg - 1) / g.rpg + 3) / 4 : (g.k + 127) / 128;
   g.kcp = rup(g.kc, 64);
   g.nch_a = g.kcp / 64;
   g.Hb = TH + k1 - 1;
   g.Wb = TW + k2 - 1;
+  g.pitch = rup(g.Wb, 8);
+  if ((g.pitch / 8) % 2 == 0) g.pitch += 8;
+  g.HBp = k3 * g.Hb * g.pitch;
+  // tap tiles of 256 columns (8 groups) where the compile-time col2im applies, the
+  // taps need more than one 128-column tile and the wider V D image fits beside the U
+  // stages; 128 columns (4 groups) otherwise
+  g.gpt = 4;
+  if (gpt_max >= 8 && g.rpg && (k1 * k3 + g.rpg - 1) / g.rpg > 4) {
+    g.gpt = 8;
+    g.nta = 256;
+    if (adj_smem(g) > SMEM_LIMIT) g.gpt = 4;
+  }
+  g.nta = 32 * g.gpt;
+  g.ntt = g.rpg ? ((k1 * k3 + g.rpg - 1) / g.rpg + g.gpt - 1) / g.gpt : (g.k + 127) / 128;
   // frames (st) each tap tile's taps reach: its col2im partial keeps only those nsl
   // frames of the halo, starting at frame slo[tt]
   g.nsl = 1;
   for (int tt = 0; tt < g.ntt && tt < 16; ++tt) {
     int lo = 1 << 30, hi = -1;
-    for (int j = 0; j < 128; ++j) {
+    for (int j = 0; j < g.nta; ++j) {
       int sp = -1;
       if (g.rpg == 0) {
         sp = tt * 128 + j < g.k ? tt * 128 + j : -1;
       } else {
-        const int G = tt * 4 + j / 32, r = (j % 32) / k2, sw = (j % 32) % k2, TR = G * g.rpg + r;
+        const int G = tt * g.gpt + j / 32, r = (j % 32) / k2, sw = (j % 32) % k2, TR = G * g.rpg + r;
         sp = (r < g.rpg && TR < k1 * k3) ? TR * k2 + sw : -1;
       }
       if (sp < 0) continue;
@@ -108,9 +123,6 @@ TcGeom make_geom(int k1, int k2, int k3) {
     g.nsl = std::max(g.nsl, hi - lo + 1);
   }
   g.HB = g.Hb * g.Wb * g.nsl;
-  g.pitch = rup(g.Wb, 8);
-  if ((g.pitch / 8) % 2 == 0) g.pitch += 8;
-  g.HBp = k3 * g.Hb * g.pitch;
   g.nus = FWD_USTAGES;
   while (g.nus > 1 && fwd_smem_n(g, g.nus) > SMEM_LIMIT) --g.nus;
   // the lo copies start on a 128-byte boundary (tiled TMA destinations must)
@@ -132,7 +144,7 @@ size_t fwd_smem(const TcGeom& g, bool split = false) {
   return split ? fwd_smem_n(g, g.nus_s, true) : fwd_smem_n(g, g.nus);
 }
 size_t adj_smem(const TcGeom& g) {
-  return 1024 + (size_t)g.nch_a * CHUNK + ADJ_STAGES * (size_t)CHUNK + 2 * (size_t)g.HBp * 4 + 128 * 4 + 256;
+  return 1024 + (size_t)g.nch_a * (g.nta * 128) + ADJ_STAGES * (size_t)CHUNK + 2 * (size_t)g.HBp * 4 + 128 * 4 + 256;
 }
 
 // Byte offset of forward K-group `grp` (8 taps) inside a halo stage.
@@ -562,7 +574,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 // Adjoint pass
 // ---------------------------------------------------------------------------------
 // Tap columns of the adjoint: column j of tap tile tt belongs to 32-column group
-// G = 4 tt + j / 32, which holds rpg = floor(32 / k2) whole tap rows (st, sh) of k2 taps
+// G = gpt tt + j / 32, which holds rpg = floor(32 / k2) whole tap rows (st, sh) of k2 taps
 // each (row TR = G rpg + r, r = (j % 32) / k2, sw = (j % 32) % k2, TR = st k1 + sh);
 // the remaining 32 - rpg k2 columns of a group and the rows past k1 k3 are padding.
 // Returns the tap s = TR k2 + sw of a column, or -1 for padding.
@@ -573,7 +585,7 @@ __host__ __device__ __forceinline__ int adj_tap_of_col(const TcGeom& g, int tt, 
     const int s = tt * 128 + j;
     return s < g.k ? s : -1;
   }
-  const int G = tt * 4 + j / 32, r = (j % 32) / g.k2, sw = (j % 32) % g.k2;
+  const int G = tt * g.gpt + j / 32, r = (j % 32) / g.k2, sw = (j % 32) % g.k2;
   const int TR = G * g.rpg + r;
   if (r >= g.rpg || TR >= g.k1 * g.k3) return -1;
   return TR * g.k2 + sw;
@@ -630,8 +642,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   uint8_t* sm = align1k(smraw);
   const TcGeom& g = a.g;
   const Shared& sh = a.sh;
+  const int chunkA = g.nta * 128;                // one 64-channel chunk of the V D image
+  const uint32_t tcols = g.nta == 256 ? 512u : TMEM_COLS;   // two accumulators of nta columns
   uint8_t* sA = sm;
-  uint8_t* sU = sm + (size_t)g.nch_a * CHUNK;
+  uint8_t* sU = sm + (size_t)g.nch_a * chunkA;
   float* buf = reinterpret_cast<float*>(sU + (size_t)ADJ_STAGES * CHUNK);   // [2][HBp]
   int* toff = reinterpret_cast<int*>(buf + 2 * (size_t)g.HBp);              // [128] (K2 = 0)
   uint64_t* bars = reinterpret_cast<uint64_t*>(toff + 128);
@@ -667,7 +681,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(tslot, TMEM_COLS);
+    ptx::tmem_alloc(tslot, tcols);
     ptx::tmem_relinquish();
   }
   for (int i = threadIdx.x; i < 2 * g.HBp; i += blockDim.x) buf[i] = 0.f;
@@ -711,7 +725,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     if (lane == 0) {
       // A = U tile (voxels x channels), B = V D image (tap columns x channels), both
       // K-major SW128: G[voxel][tap column] in TMEM.
-      const uint32_t idesc = ptx::idesc_bf16(128, 128, 0, 0);
+      const uint32_t idesc = ptx::idesc_bf16(128, (uint32_t)g.nta, 0, 0);
       // descriptors of U stage 0 and image chunk 0; others differ only in the start address
       const uint64_t ubase = ptx::sdesc(ptx::smem_u32(sU), 16, 1024, 2);
       const uint64_t bbase = ptx::sdesc(ptx::smem_u32(sA), 16, 1024, 2);
@@ -726,9 +740,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
             if (!ptx::mbar_wait(dbar, dph)) { failed = true; break; }
             dph ^= 1;
           }
-          ptx::mbar_arrive_expect_tx(abar, (uint32_t)g.nch_a * CHUNK);
-          const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.jobs[jb].B2img) + (size_t)tt * g.nch_a * CHUNK;
-          for (int c = 0; c < g.nch_a; ++c) ptx::bulk_g2s(sA + (size_t)c * CHUNK, src + (size_t)c * CHUNK, CHUNK, abar);
+          ptx::mbar_arrive_expect_tx(abar, (uint32_t)(g.nch_a * chunkA));
+          const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.jobs[jb].B2img) + (size_t)tt * g.nch_a * chunkA;
+          for (int c = 0; c < g.nch_a; ++c)
+            ptx::bulk_g2s(sA + (size_t)c * chunkA, src + (size_t)c * chunkA, (uint32_t)chunkA, abar);
           if (!ptx::mbar_wait(abar, aph)) { failed = true; break; }
           aph ^= 1;
           cur = jb;
@@ -737,14 +752,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         const uint32_t bph = (i >> 1) & 1;
         if (!ptx::mbar_wait(&tempty[b], bph ^ 1)) { failed = true; break; }
         ptx::tc_fence_after();
-        const uint32_t d = tbase + (uint32_t)b * 128;
+        const uint32_t d = tbase + (uint32_t)(b * g.nta);
         for (int c = 0; c < g.nch_a; ++c, ++cnt) {
           const int s = cnt % ADJ_STAGES;
           const uint32_t ph = (cnt / ADJ_STAGES) & 1;
           if (!ptx::mbar_wait(&full[s], ph)) { failed = true; break; }
           ptx::tc_fence_after();
           const uint64_t ad0 = ubase + (uint64_t)(s * (CHUNK >> 4));
-          const uint64_t bd0 = bbase + (uint64_t)(c * (CHUNK >> 4));
+          const uint64_t bd0 = bbase + (uint64_t)(c * (chunkA >> 4));
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) ptx::mma_bf16(d, ad0 + 2 * kk, bd0 + 2 * kk, idesc, (c | kk) ? 1u : 0u);
           ptx::mma_commit(&empty[s]);
@@ -778,14 +793,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         const uint32_t bph = (i >> 1) & 1;
         if (!ptx::mbar_wait(&tfull[b], bph)) { failed = true; break; }
         ptx::tc_fence_after();
-        float v[32];
-        ptx::tmem_ld32(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cg * 32, v);
+        // the warp's column groups: cg, and cg + 4 in a 256-column tap tile (K2 = 0
+        // keeps 128-column tiles)
+        float v[32], v2[32];
+        const uint32_t tl = tbase + (uint32_t)(b * g.nta) + ((uint32_t)(q * 32) << 16);
+        ptx::tmem_ld32(tl + (uint32_t)cg * 32, v);
+        if (g.gpt == 8) ptx::tmem_ld32(tl + (uint32_t)(cg + 4) * 32, v2);
         ptx::tmem_ld_wait();
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&tempty[b]);
         if constexpr (K2 > 0) {
-          adj_col2im_rows<K2>(v, lane, hb, hoff, g, tt * 4 + cg);
+          adj_col2im_rows<K2>(v, lane, hb, hoff, g, tt * g.gpt + cg);
+          if (g.gpt == 8) adj_col2im_rows<K2>(v2, lane, hb, hoff, g, tt * g.gpt + cg + 4);
         } else {
           const int vbase = hoff + (vox & 7);
 #pragma unroll
@@ -839,7 +859,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tbase, TMEM_COLS);
+    ptx::tmem_dealloc(tbase, tcols);
   }
 }
 
@@ -851,8 +871,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
 __global__ void build_B2_kernel(Shared sh, TcGeom g) {
   const JobDev& J = sh.jobs[blockIdx.x];
   const int tt = blockIdx.y / g.nch_a, c = blockIdx.y % g.nch_a;
-  uint8_t* img = reinterpret_cast<uint8_t*>(J.B2img) + ((size_t)tt * g.nch_a + c) * CHUNK;
-  for (int u = threadIdx.x; u < 128 * 8; u += blockDim.x) {
+  uint8_t* img = reinterpret_cast<uint8_t*>(J.B2img) + ((size_t)tt * g.nch_a + c) * (g.nta * 128);
+  for (int u = threadIdx.x; u < g.nta * 8; u += blockDim.x) {
     const int r = u >> 3, j = u & 7;
     const int s = adj_tap_of_col(g, tt, r);
     __align__(16) __nv_bfloat16 v[8];
@@ -1008,14 +1028,14 @@ EncodeTiledFn encoder() {
 // ---------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------
-TcGeom tc_geom(int k1, int k2, int k3, int kc) {
-  TcGeom g = make_geom(k1, k2, k3);
+TcGeom tc_geom(int k1, int k2, int k3, int kc, int gpt_max) {
+  TcGeom g = make_geom(k1, k2, k3, gpt_max);
   g.kc = kc;
   return g;
 }
 
 bool tc_supported(int k1, int k2, int k3, std::string* why) {
-  const TcGeom g = make_geom(k1, k2, k3);
+  const TcGeom g = make_geom(k1, k2, k3, 4);
   auto no = [&](const char* m) { if (why) *why = m; return false; };
   if (g.k > 512) return no("k > 512");
   if (k2 > 16) return no("k2 > 16");
@@ -1028,8 +1048,8 @@ bool tc_supported(int k1, int k2, int k3, std::string* why) {
   return true;
 }
 
-cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out) {
-  TcGeom g = make_geom(k1, k2, k3);
+cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out, int gpt_max) {
+  TcGeom g = make_geom(k1, k2, k3, gpt_max);
   g.kc = kc;
   out->g = g;
   const int k = g.k;
@@ -1093,7 +1113,7 @@ size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g) {
   auto add = [&](size_t n) { b += (n + 255) / 256 * 256; };
   add((size_t)(g.split_ok ? 2 : 1) * g.ncopy * Tp * Hp * Wp * 2);   // Xc (and its lo copies)
   add((size_t)H * W * T * 4);                          // col2im sums (Delta)
-  add((size_t)g.ntt * g.nch_a * CHUNK);                // V D images
+  add((size_t)g.ntt * g.nch_a * g.nta * 128);          // V D images
   add(4 * sizeof(CUtensorMap));                        // TMA maps
   return b;
 }
@@ -1110,7 +1130,7 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   const int ncp = (g.split_ok ? 2 : 1) * g.ncopy;        // copies in Xc (hi, then lo)
   d->Xc = (__nv_bfloat16*)take((size_t)ncp * Tp * Hp * Wp * 2);
   d->G = (float*)take((size_t)d->m * 4);
-  d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * CHUNK);
+  d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * g.nta * 128);
   CUtensorMap* tm = (CUtensorMap*)take(4 * sizeof(CUtensorMap));
   if (off > total) return cudaErrorInvalidValue;
   EncodeTiledFn enc = encoder();

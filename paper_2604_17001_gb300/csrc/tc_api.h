@@ -19,7 +19,10 @@ struct TcGeom {
   int stage_bytes;  // one halo stage (the k2 copies used + 16 zero rows), 1024-aligned
   int nct;          // channel tiles of 128
   // adjoint pass G = U (D V^T) (M = 128 voxels, N = 128 taps, K = channels)
-  int ntt;          // tap tiles of 128 columns (4 groups of rpg tap rows)
+  int gpt;          // 32-column groups per adjoint tap tile: 4 (N = 128) or 8 (N = 256,
+                    // when the wider tile's V D image fits in shared memory)
+  int nta;          // tap-tile width 32 * gpt: the adjoint MMA's N
+  int ntt;          // tap tiles (gpt groups of rpg tap rows each)
   int kcp;          // channels rounded up to 64
   int nch_a;        // 64-wide SW128 chunks of the adjoint A image
   int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*nsl
@@ -48,8 +51,9 @@ struct TcVData {
 
 bool tc_supported(int k1, int k2, int k3, std::string* why);
 // Geometry of the tensor-core passes for these kernel dims (kc: the channel stride).
-TcGeom tc_geom(int k1, int k2, int k3, int kc);
-cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out);
+TcGeom tc_geom(int k1, int k2, int k3, int kc, int gpt_max = 8);
+// gpt_max: widest adjoint tap tile to consider, in 32-column groups (4 or 8)
+cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out, int gpt_max = 8);
 void tc_free_vdata(TcVData* v);
 size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g);
 // Carve the tensor-core buffers of a job from its allocation and encode its TMA maps;
