@@ -57,12 +57,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learn", action="store_true")
     ap.add_argument("--workload", default="serving",
-                    choices=["serving", "prediction", "completion", "interpolation", "batch", "image", "cnnm"],
+                    choices=["serving", "prediction", "completion", "interpolation", "batch", "image", "cnnm",
+                             "autotune"],
                     help="serving (the default line); the others print their own line")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--latency-requests", type=int, default=400, help="serving: requests of the Poisson run")
     ap.add_argument("--fp32-requests", type=int, default=12, help="serving: requests solved in plain FP32")
     ap.add_argument("--no-prediction", action="store_true", help="serving: skip the prediction sub-run")
+    ap.add_argument("--write-table", default=None,
+                    help="autotune: write the tile table (JSON) to this path")
     ap.add_argument("--kdims", default=None,
                     help="prediction: k1,k2,k3 of a resized case (7,7,3 takes the serving family's stored V)")
     ap.add_argument("--dims", default=None,
@@ -516,11 +519,18 @@ def run_batch(args, local):
     stream = torch.cuda.current_stream(dev)
     ctx = icnnm.Context(local, stream=stream.cuda_stream)
     V = _learn_V_gpu(ctx, refs, kd, dev)
+    # the same batch with the built-in tile defaults (no table), for comparison
+    ctx0 = icnnm.Context(local, stream=stream.cuda_stream, tile_table=None)
     Ms = [torch.from_numpy(j["M"]).to(dev) for j in jobs]
     Ks = [torch.from_numpy(j["mask"]).to(dev) for j in jobs]
     Vd = torch.from_numpy(np.ascontiguousarray(V)).to(dev)
     Ls = [torch.zeros_like(m) for m in Ms]
     vox = sum(int(np.prod(j["dims"])) for j in jobs)
+    f0 = lambda: ctx0.icnnm_solve_batch(Ms, Ks, Vd, kd, L_outs=Ls, max_iters=it, prec="bf16")
+    for _ in range(args.warmup):
+        f0()
+    sec0 = _timed(stream, f0, args.steps)
+    ctx0.close()
     f = lambda: ctx.icnnm_solve_batch(Ms, Ks, Vd, kd, L_outs=Ls, max_iters=it, prec="bf16")
     for _ in range(args.warmup):
         f()
@@ -543,6 +553,8 @@ def run_batch(args, local):
                       "ms_per_batch": 1e3 * sec / args.steps,
                       "voxel_iters_per_s": vox * it * args.steps / sec, "gpu_launches_per_batch": int(nl.value) // args.steps,
                       "observed_entries_exact": obs_ok,
+                      "default_tiles_solves_per_s": n * args.steps / sec0,
+                      "tile_table": os.path.exists(os.path.join(ROOT, "paper_2604_17001_gb300", "tile_table.json")),
                       "fp32_plain": {"value": n / fsec, "unit": "solves/s", "ms_per_pass": 1e3 * fsec,
                                      "mode": "one job at a time"}}))
 
@@ -953,6 +965,39 @@ def run_serving_bench(args, ws, rank, local):
     print(json.dumps(out))
 
 
+def run_autotune(args, local):
+    """Tile autotuner over the workload families: for each kernel size, every distinct tile
+    geometry (adjoint tap-tile width, forward channel-tile width, forward U stages) is timed
+    on synthetic jobs of the family's shapes stepped together (10 BF16 iterations), and the
+    fastest is recorded. Prints the table; --write-table saves it in the form Context reads."""
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    torch.cuda.set_device(local)
+    fams = [
+        ("serving / batching", (7, 7, 3), [tuple(s_) for s_ in synth.serving_shapes(16)]),
+        ("video prediction", (9, 9, 5), [(128, 128, 32)]),
+        ("frame interpolation", (7, 7, 5), [(256, 256, 64)]),
+        ("completion", (5, 5, 3), [(32, 32, 8)] * 8),
+        ("image", (13, 13, 1), [(200, 200)] * 24),
+    ]
+    rng = np.random.default_rng(5)
+    entries = []
+    with icnnm.Context(local, tile_table=None) as ctx:
+        for name, kd, dims in fams:
+            k = int(np.prod(kd))
+            V = np.linalg.qr(rng.standard_normal((k, k)))[0]
+            dl = [(d[0], d[1]) if len(d) == 2 else d for d in dims]
+            best, res = ctx.icnnm_autotune(dl, kd if len(dl[0]) == 3 else kd[:2], V, iters=10)
+            entries.append({"family": name, "kdims": list(kd), **best, "candidates": res,
+                            "jobs": len(dims), "voxels": int(sum(np.prod(d) for d in dims))})
+    table = {"about": "tile configurations per kernel size chosen by the autotuner (icnnm_autotune) on one "
+                      "GB300: the fastest of every distinct geometry on synthetic jobs of the family's shapes",
+             "entries": entries}
+    if args.write_table:
+        json.dump(table, open(args.write_table, "w"), indent=1)
+    print(json.dumps({"workload": "autotune", **table}))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -970,6 +1015,8 @@ def main():
         run_image(args, local)
     elif args.workload == "cnnm":
         run_cnnm(args, local)
+    elif args.workload == "autotune":
+        run_autotune(args, local)
     else:
         run_serving_bench(args, ws, rank, local)
     if ws > 1:

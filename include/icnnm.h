@@ -258,6 +258,51 @@ icnnm_status icnnm_profile_read(icnnm_ctx* ctx, int32_t pass, double* ms_total, 
 icnnm_status icnnm_profile_voxels(icnnm_ctx* ctx, int32_t pass, int64_t* voxels);
 
 /*
+ * Tile configuration of the tensor-core passes for one kernel size (no counterpart in the
+ * paper; a performance choice that leaves every result unchanged up to the order of FP32
+ * additions). Each field is an upper bound; 0 keeps the default (the widest that fits):
+ *   adj_tap_width     : columns of an adjoint tap tile, 128 or 256 (256 where the V D image
+ *                       of the wider tile fits in shared memory)
+ *   fwd_channel_width : channels of a forward channel tile, 128 or 256 (256: one tile of all
+ *                       channels when k <= 256 and it fits)
+ *   fwd_u_stages      : shared-memory stages of the forward's U tiles, 1 or 2
+ */
+typedef struct {
+  int32_t adj_tap_width;
+  int32_t fwd_channel_width;
+  int32_t fwd_u_stages;
+} icnnm_tile_config;
+
+typedef struct {
+  icnnm_tile_config cfg;  /* the candidate (upper bounds as passed to the geometry) */
+  int32_t adj_tap_width;  /* what the geometry took: tap-tile columns */
+  int32_t fwd_channel_width; /* channel-tile width taken */
+  int32_t fwd_u_stages;   /* U stages taken */
+  double ms_per_iter;     /* measured device time of one iteration of all the jobs */
+} icnnm_tile_result;
+
+/*
+ * Use cfg for BF16 work with these kernel dims from now on in this context (V data built
+ * before the call keep their tiles). EINVAL for widths other than 0/128/256 or stages
+ * other than 0/1/2.
+ */
+icnnm_status icnnm_set_tile_config(icnnm_ctx* ctx, const int64_t kdims[3], const icnnm_tile_config* cfg);
+
+/*
+ * Autotuner of the tile configuration: for every distinct tile geometry the candidates
+ * give, builds the tensor-core data of V, creates n synthetic jobs of the given shapes
+ * (smooth values, about half the voxels observed), runs `iters` BF16 iterations of all of
+ * them stepped together, and times them with CUDA events on the context's stream. The
+ * fastest becomes the context's configuration for these kernel dims (as by
+ * icnnm_set_tile_config) and is returned in *best; results (capacity max_results, may be
+ * NULL) receive every measured candidate and *n_results their count. Blocking; needs the
+ * device memory of the n jobs within the budget.
+ */
+icnnm_status icnnm_autotune(icnnm_ctx* ctx, const double* V, int32_t n, const icnnm_shape* shapes,
+                            int32_t iters, icnnm_tile_config* best, icnnm_tile_result* results,
+                            int32_t max_results, int32_t* n_results);
+
+/*
  * Device bytes of the state of one job of this shape in this precision (the amount the
  * HBM budget is charged at admission; a BF16 job with a tolerance may take more for its
  * FP32 finish). For callers that size a context's budget. V is not needed: kdims decide.

@@ -148,6 +148,7 @@ struct icnnm_ctx {
   std::string last_err;
   std::map<std::string, std::unique_ptr<VData>> vcache;   // inserted under mu and vmu
   std::mutex vmu;                  // lookups of vcache without mu (the submitting side)
+  std::map<std::string, TcTiles> tiles;   // tile configuration per kernel dims ("k1_k2_k3")
   // serving
   std::mutex qmu;
   std::condition_variable qcv;
@@ -399,12 +400,23 @@ VData* get_vdata(icnnm_ctx* c, const double* V, int k1, int k2, int k3, int prec
   return vd;
 }
 
-void ensure_tc(VData* vd, int prec) {
+std::string kdims_key(int k1, int k2, int k3) {
+  char buf[48];
+  snprintf(buf, sizeof buf, "%d_%d_%d", k1, k2, k3);
+  return buf;
+}
+
+TcTiles tiles_for(icnnm_ctx* c, int k1, int k2, int k3) {
+  auto it = c->tiles.find(kdims_key(k1, k2, k3));
+  return it == c->tiles.end() ? TcTiles() : it->second;
+}
+
+void ensure_tc(icnnm_ctx* c, VData* vd, int prec) {
   const int k1 = vd->k1, k2 = vd->k2, k3 = vd->k3;
   if (prec != ICNNM_FP32 && !vd->tc_ready) {
     std::string why;
     if (!tc_supported(k1, k2, k3, &why)) fail(ICNNM_EUNSUPPORTED, "BF16 path: " + why);
-    CK(tc_build_vdata(vd->V64.data(), k1, k2, k3, vd->kc, &vd->tc));
+    CK(tc_build_vdata(vd->V64.data(), k1, k2, k3, vd->kc, &vd->tc, tiles_for(c, k1, k2, k3)));
     vd->tc_ready = true;
   }
   if (prec == ICNNM_BF16X3 && !vd->tc.g.split_ok)
@@ -577,6 +589,7 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js, int slot = 0) {
   sh.nrp = js[0]->run_prec == ICNNM_FP32 ? fwd_fp32_nrp(vd->k) : tc_nrp(vd->k);
   sh.Vf = vd->dVf;
   sh.VtImg = vd->tc_ready ? vd->tc.VtImg : nullptr;
+  sh.VtImgS = vd->tc_ready ? vd->tc.VtImgS : nullptr;
   sh.njobs = n;
   sh.jobs = c->dlist[slot];
   sh.job_tile0 = c->dtile0[slot];
@@ -599,7 +612,7 @@ void run_fwd(icnnm_ctx* c, const Shared& sh, int prec, int mode, const TcVData* 
 
 // Row groups of the column partials written by the update pass (0 = one per tile).
 int fwd_slots(const Shared& sh, int prec, const TcVData* tcv) {
-  return prec != ICNNM_FP32 ? tc_fwd_slots(sh, *tcv) : 0;
+  return prec != ICNNM_FP32 ? tc_fwd_slots(sh, *tcv, prec == ICNNM_BF16X3) : 0;
 }
 
 // Column norms ||A_k(L) v_c||^2 of each job's current L into its colseg through the
@@ -907,7 +920,7 @@ void prepare_job(icnnm_ctx* c, Job& j, const icnnm_shape* shape, const float* M,
   CK(cudaStreamSynchronize(c->stream));
   if (h2[1]) fail(ICNNM_EINVAL, "mask entries must be 0/1 and M must be finite on Omega");
   if (h2[0] == 0) fail(ICNNM_EINVAL, "Omega is empty");
-  ensure_tc(j.vd, p.prec);
+  ensure_tc(c, j.vd, p.prec);
   j.srcM = M;
   j.srcmask = mask;
 }
@@ -1541,7 +1554,7 @@ icnnm_status icnnm_submit(icnnm_ctx* c, const icnnm_shape* shape, const float* M
       if (!vd) {
         std::lock_guard<std::recursive_mutex> g(c->mu);
         vd = get_vdata(c, hv.data(), k1, k2, k3, p.prec);
-        ensure_tc(vd, p.prec);
+        ensure_tc(c, vd, p.prec);
       }
       const int nrp = std::max(fwd_fp32_nrp(vd->k), tc_nrp(vd->k));
       if (job_bytes(H, W, T, vd->k, vd->kc, p.prec, nrp, &vd->tc.g) > c->budget)
@@ -1635,6 +1648,148 @@ icnnm_status icnnm_profile_read(icnnm_ctx* c, int32_t pass, double* ms_total, in
   return ICNNM_OK;
 }
 
+static bool tile_cfg_ok(const icnnm_tile_config& t) {
+  return (t.adj_tap_width == 0 || t.adj_tap_width == 128 || t.adj_tap_width == 256) &&
+         (t.fwd_channel_width == 0 || t.fwd_channel_width == 128 || t.fwd_channel_width == 256) &&
+         (t.fwd_u_stages >= 0 && t.fwd_u_stages <= 2);
+}
+
+static TcTiles tiles_of(const icnnm_tile_config& t) {
+  TcTiles r;
+  if (t.adj_tap_width) r.gpt_max = t.adj_tap_width / 32;
+  if (t.fwd_channel_width) r.ctw_max = t.fwd_channel_width;
+  if (t.fwd_u_stages) r.nus_max = t.fwd_u_stages;
+  return r;
+}
+
+icnnm_status icnnm_set_tile_config(icnnm_ctx* c, const int64_t kdims[3], const icnnm_tile_config* cfg) {
+  if (!c || !kdims || !cfg) return ICNNM_EINVAL;
+  if (!tile_cfg_ok(*cfg) || kdims[0] < 1 || kdims[1] < 1 || kdims[2] < 1) {
+    set_err(c, "tile widths must be 0, 128 or 256 and stages 0, 1 or 2");
+    return ICNNM_EINVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  c->tiles[kdims_key((int)kdims[0], (int)kdims[1], (int)kdims[2])] = tiles_of(*cfg);
+  return ICNNM_OK;
+}
+
+icnnm_status icnnm_autotune(icnnm_ctx* c, const double* V, int32_t n, const icnnm_shape* shapes, int32_t iters,
+                            icnnm_tile_config* best, icnnm_tile_result* results, int32_t max_results,
+                            int32_t* n_results) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  std::vector<std::unique_ptr<Job>> jobs;
+  std::vector<void*> inputs;
+  TcVData tmp;
+  bool tmp_built = false;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    for (auto& j : jobs) free_job(c, *j);
+    for (void* p : inputs) dfree_async(p, c->stream);
+    if (tmp_built) tc_free_vdata(&tmp);
+    cudaStreamSynchronize(c->stream);
+  };
+  try {
+    CK(cudaSetDevice(c->device));
+    if (n < 1 || !shapes || iters < 1 || !best) fail(ICNNM_EINVAL, "NULL argument, n < 1 or iters < 1");
+    int H, W, T, k1, k2, k3;
+    validate_shape(&shapes[0], H, W, T, k1, k2, k3);
+    VData* vd = get_vdata(c, V, k1, k2, k3, ICNNM_BF16);     // validates V
+    std::string why;
+    if (!tc_supported(k1, k2, k3, &why)) fail(ICNNM_EUNSUPPORTED, "BF16 path: " + why);
+    icnnm_params p = defaults();
+    p.prec = ICNNM_BF16;
+    p.max_iters = iters + 2;
+    // the synthetic jobs (inputs filled on the device)
+    for (int i = 0; i < n; ++i) {
+      int h, w, t, a, b, e;
+      validate_shape(&shapes[i], h, w, t, a, b, e);
+      if (a != k1 || b != k2 || e != k3) fail(ICNNM_EINVAL, "all shapes share kernel dims");
+      auto j = std::make_unique<Job>();
+      j->H = h; j->W = w; j->T = t; j->m = (long long)h * w * t;
+      j->p = p;
+      float* dM = (float*)dalloc_async(c, (size_t)j->m * 4, c->stream);
+      uint8_t* dK = (uint8_t*)dalloc_async(c, (size_t)j->m, c->stream);
+      inputs.push_back(dM);
+      inputs.push_back(dK);
+      CK(launch_tune_fill(dM, dK, h, w, t, c->stream));
+      j->srcM = dM;
+      j->srcmask = dK;
+      jobs.push_back(std::move(j));
+    }
+    // candidates: every combination of the three bounds; equal geometries are measured once
+    std::vector<icnnm_tile_result> res;
+    double best_ms = INFINITY;
+    icnnm_tile_config best_cfg{};
+    for (int aw : {256, 128})
+      for (int fw : {256, 128})
+        for (int us : {2, 1}) {
+          const icnnm_tile_config cfg{aw, fw, us};
+          const TcGeom gg = tc_geom(k1, k2, k3, vd->kc, tiles_of(cfg));
+          bool seen = false;
+          for (const auto& r : res)
+            if (r.adj_tap_width == gg.nta && r.fwd_channel_width == gg.ctw && r.fwd_u_stages == gg.nus) seen = true;
+          if (seen) continue;
+          // V data of this candidate, not cached: the jobs point at a private VData
+          VData cand;
+          cand.k1 = k1; cand.k2 = k2; cand.k3 = k3; cand.k = vd->k; cand.kc = vd->kc;
+          cand.dVf = vd->dVf;
+          cand.dV64 = vd->dV64;
+          CK(tc_build_vdata(vd->V64.data(), k1, k2, k3, vd->kc, &tmp, tiles_of(cfg)));
+          tmp_built = true;
+          cand.tc = tmp;
+          cand.tc_ready = true;
+          std::vector<Job*> js;
+          for (auto& j : jobs) {
+            j->vd = &cand;
+            alloc_job(c, *j);
+            js.push_back(j.get());
+          }
+          engine_init(c, js);
+          const Shared sh = upload_list(c, js);
+          for (int w0 = 0; w0 < 2; ++w0) engine_step(c, sh, ICNNM_BF16, &cand.tc, false);
+          cudaEvent_t e0, e1;
+          CK(cudaEventCreate(&e0));
+          CK(cudaEventCreate(&e1));
+          CK(cudaEventRecord(e0, c->stream));
+          for (int it = 0; it < iters; ++it) engine_step(c, sh, ICNNM_BF16, &cand.tc, false);
+          CK(cudaEventRecord(e1, c->stream));
+          CK(cudaStreamSynchronize(c->stream));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          enqueue_scals(c, js);
+          CK(cudaStreamSynchronize(c->stream));
+          for (size_t i = 0; i < js.size(); ++i)
+            if (c->hscal[i].status) fail(ICNNM_ETIMEOUT, "a bounded device-side wait expired while tuning");
+          for (auto& j : jobs) free_job(c, *j);
+          CK(cudaStreamSynchronize(c->stream));
+          tc_free_vdata(&tmp);
+          tmp_built = false;
+          icnnm_tile_result r{cfg, gg.nta, gg.ctw, gg.nus, ms / iters};
+          res.push_back(r);
+          if (r.ms_per_iter < best_ms) {
+            best_ms = r.ms_per_iter;
+            best_cfg = cfg;
+          }
+        }
+    for (auto& j : jobs) j->vd = nullptr;
+    c->tiles[kdims_key(k1, k2, k3)] = tiles_of(best_cfg);
+    *best = best_cfg;
+    if (n_results) *n_results = (int32_t)res.size();
+    for (int i = 0; results && i < (int)res.size() && i < max_results; ++i) results[i] = res[i];
+    cleanup();
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    cleanup();
+    return report(c, f);
+  } catch (CudaFail& f) {
+    cleanup();
+    return report(c, f);
+  }
+}
+
 icnnm_status icnnm_job_bytes(icnnm_ctx* c, const icnnm_shape* shape, int32_t prec, size_t* bytes) {
   if (!c || !bytes) return ICNNM_EINVAL;
   try {
@@ -1646,7 +1801,7 @@ icnnm_status icnnm_job_bytes(icnnm_ctx* c, const icnnm_shape* shape, int32_t pre
     if (prec != ICNNM_FP32) {
       std::string why;
       if (!tc_supported(k1, k2, k3, &why)) fail(ICNNM_EUNSUPPORTED, "BF16 path: " + why);
-      g = tc_geom(k1, k2, k3, kc);
+      g = tc_geom(k1, k2, k3, kc, tiles_for(c, k1, k2, k3));
       if (prec == ICNNM_BF16X3 && !g.split_ok) fail(ICNNM_EUNSUPPORTED, "BF16X3 is not built for these kernel dims");
     }
     const int nrp = std::max(fwd_fp32_nrp(k), tc_nrp(k));

@@ -80,7 +80,8 @@ struct Shared {
   int kc;                // channel stride of U (k rounded up to 16)
   int nrp;               // residual partials per tile
   const float* Vf;       // [k taps][kc] FP32, V[s][c] (column c = eigenvector c)
-  const __nv_bfloat16* VtImg;  // BF16 forward-pass A-operand images (see k_tc.cu)
+  const __nv_bfloat16* VtImg;  // BF16 forward-pass B images (see k_tc.cu)
+  const __nv_bfloat16* VtImgS; // the same for the split forward (hi, then lo), or null
   int njobs;
   const JobDev* jobs;    // device array of njobs
   const int* job_tile0;  // device, njobs + 1 prefix sums of ntiles
@@ -129,6 +130,8 @@ __device__ __forceinline__ float l_update(const JobDev& J, int k, long long v, f
 // ---------------------------------------------------------------------------------
 // k_common.cu
 cudaError_t launch_init_L(const Shared& sh, cudaStream_t st);
+// synthetic input of the tile autotuner (smooth values, about half observed)
+cudaError_t launch_tune_fill(float* M, uint8_t* mask, int H, int W, int T, cudaStream_t st);
 // slots = 0: the partials have one row group per tile; slots > 0: per forward CTA slot,
 // min(slots, ntiles) row groups per job.
 cudaError_t launch_reduce_cols(const Shared& sh, int advance, int slots, cudaStream_t st);

@@ -220,7 +220,27 @@ __global__ void check_observed_kernel(const float* M, const uint8_t* mask, long 
   if (bad) atomicExch(out + 1, 1);
 }
 
+// Synthetic input of the tile autotuner: a smooth pattern with about half of the voxels
+// observed (a hash of the index decides), deterministic.
+__global__ void tune_fill_kernel(float* M, uint8_t* mask, int H, int W, int T) {
+  const long long m = (long long)H * W * T;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(i % W), h = (int)((i / W) % H), t = (int)(i / ((long long)W * H));
+    M[i] = 0.5f + 0.25f * __sinf(0.37f * w + 0.11f * t) * __cosf(0.23f * h - 0.07f * t);
+    unsigned x = (unsigned)i * 2654435761u;
+    x ^= x >> 15;
+    x *= 2246822519u;
+    x ^= x >> 13;
+    mask[i] = (x & 1u) ? 1 : 0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tune_fill(float* M, uint8_t* mask, int H, int W, int T, cudaStream_t st) {
+  tune_fill_kernel<<<512, 256, 0, st>>>(M, mask, H, W, T);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init_L(const Shared& sh, cudaStream_t st) {
   init_L_kernel<<<sh.total_tiles, TILE_VOX, 0, st>>>(sh);

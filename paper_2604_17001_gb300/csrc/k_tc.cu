@@ -62,7 +62,7 @@ size_t fwd_smem_n(const TcGeom& g, int nus, bool split = false);
 
 size_t adj_smem(const TcGeom& g);
 
-TcGeom make_geom(int k1, int k2, int k3, int gpt_max) {
+TcGeom make_geom(int k1, int k2, int k3, int gpt_max, int ctw_max = 256, int nus_max = FWD_USTAGES) {
   TcGeom g{};
   g.k1 = k1; g.k2 = k2; g.k3 = k3; g.k = k1 * k2 * k3; g.kc = rup(g.k, 16);
   // each w-run of taps is padded to a multiple of 16 (two 8-row K-groups): every MMA then
@@ -78,7 +78,9 @@ TcGeom make_geom(int k1, int k2, int k3, int gpt_max) {
   g.Hh = TH + k1 - 1;
   g.region_bytes = g.Hh * k3 * 16;
   g.stage_bytes = rup(k2 * g.region_bytes + 16 * 16, 1024);  // k2 copies + 16 zero rows
+  g.ctw = 128;
   g.nct = (g.k + 127) / 128;
+  g.nct_s = g.nct;
   // adjoint tap columns: whole tap rows per 32-column group for the kernel widths with a
   // compile-time col2im (3, 5, 7, 9), taps in order otherwise
   g.rpg = (k2 == 3 || k2 == 5 || k2 == 7 || k2 == 9) ? 32 / k2 : 0;
@@ -123,8 +125,26 @@ TcGeom make_geom(int k1, int k2, int k3, int gpt_max) {
     g.nsl = std::max(g.nsl, hi - lo + 1);
   }
   g.HB = g.Hb * g.Wb * g.nsl;
-  g.nus = FWD_USTAGES;
+  g.nus = std::max(1, std::min(FWD_USTAGES, nus_max));
   while (g.nus > 1 && fwd_smem_n(g, g.nus) > SMEM_LIMIT) --g.nus;
+  // one channel tile of all channels (N = kc rounded up to 32) when 128 < that <= 256 and
+  // it fits in shared memory with two U stages: one CTA per voxel tile, so the halo is
+  // loaded and the MMAs issued once instead of twice
+  {
+    const int w = rup(g.kc, 32);
+    if (ctw_max >= 256 && w > 128 && w <= 256) {
+      TcGeom h = g;
+      h.ctw = w;
+      h.nct = 1;
+      int nu = std::max(1, std::min(FWD_USTAGES, nus_max));
+      while (nu > 1 && fwd_smem_n(h, nu) > SMEM_LIMIT) --nu;
+      if (fwd_smem_n(h, nu) <= SMEM_LIMIT) {
+        g.ctw = w;
+        g.nct = 1;
+        g.nus = nu;
+      }
+    }
+  }
   // the lo copies start on a 128-byte boundary (tiled TMA destinations must)
   g.lo_off = rup(k2 * g.region_bytes + 16 * 16, 128);
   g.stage_bytes_s = rup(g.lo_off + k2 * g.region_bytes + 16 * 16, 1024);
@@ -134,11 +154,17 @@ TcGeom make_geom(int k1, int k2, int k3, int gpt_max) {
   return g;
 }
 
+// Shared memory of the forward pass: B image(s), two halo stages, nus U stages (ubox boxes
+// of 64 channels, twice for split), the per-warp scales (two tasks per warp) and the
+// shared column-sum accumulators of second tasks (wide channel tiles), descriptors, barriers.
 size_t fwd_smem_n(const TcGeom& g, int nus, bool split) {
   const int img = split ? 2 : 1;
+  const int ctw = split ? 128 : g.ctw;
   const size_t stage = split ? (size_t)g.stage_bytes_s : (size_t)g.stage_bytes;
-  return 1024 + (size_t)img * g.nch_f * CHUNK + 2 * stage + (size_t)nus * img * USTAGE + EPI_WARPS * 32 * 4 +
-         64 * 16 + 256;
+  const int ubox = (ctw + 63) / 64;
+  const int ng2 = std::max(0, ctw / 32 - 4);          // column groups beyond the first four
+  return 1024 + (size_t)img * g.nch_f * (ctw * 128) + 2 * stage + (size_t)nus * img * ubox * CHUNK +
+         EPI_WARPS * (ng2 ? 64 : 32) * 4 + (size_t)ng2 * 4 * 32 * 32 * 4 + 64 * 16 + 256;
 }
 size_t fwd_smem(const TcGeom& g, bool split = false) {
   return split ? fwd_smem_n(g, g.nus_s, true) : fwd_smem_n(g, g.nus);
@@ -233,14 +259,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   const TcGeom& g = a.g;
   const Shared& sh = a.sh;
   constexpr int NIMG = SPLIT ? 2 : 1;
+  const int ctw = SPLIT ? 128 : g.ctw;                          // channels per tile (the MMA's N)
+  const int nct = SPLIT ? g.nct_s : g.nct;
+  const int chunkF = ctw * 128;                                  // one K chunk (64 taps) of the B image
+  const int ubox = (ctw + 63) / 64;                              // 64-channel U boxes per tile
+  const int ng = ctw / 32;                                       // 32-channel epilogue groups
+  const uint32_t tcols = 2 * ctw > 256 ? 512u : TMEM_COLS;
   const int stage_bytes = SPLIT ? g.stage_bytes_s : g.stage_bytes;
   const int nus = SPLIT ? g.nus_s : g.nus;
-  const int ustage = NIMG * USTAGE;
+  const int uhalf = ubox * CHUNK;                                // one U tile (hi or lo) in a stage
+  const int ustage = NIMG * uhalf;
   uint8_t* sA = sm;                                              // V^T image(s) of this channel tile
-  uint8_t* sH = sA + (size_t)NIMG * g.nch_f * CHUNK;             // [2] halo stages
+  uint8_t* sH = sA + (size_t)NIMG * g.nch_f * chunkF;            // [2] halo stages
   uint8_t* sU = sH + 2 * (size_t)stage_bytes;                    // [nus] U tiles
-  float* sD = reinterpret_cast<float*>(sU + (size_t)nus * ustage);   // [EPI_WARPS][32]
-  ulonglong2* sDesc = reinterpret_cast<ulonglong2*>(sD + EPI_WARPS * 32);  // [64] MMA descriptors
+  const int sdw = ng > 4 ? 64 : 32;                              // scale slots per warp (one per group)
+  float* sD = reinterpret_cast<float*>(sU + (size_t)nus * ustage);   // [EPI_WARPS][sdw] channel scales
+  float* sAcc2 = sD + EPI_WARPS * sdw;                           // [ng - 4 groups][4][32][32] second-group sums
+  ulonglong2* sDesc = reinterpret_cast<ulonglong2*>(sAcc2 + (size_t)max(0, ng - 4) * 4 * 32 * 32);  // [64]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sDesc + 64);
   uint64_t* full = bars;                   // [2] halo landed
   uint64_t* empty = bars + 2;              // [2] halo consumed by the MMAs
@@ -253,12 +288,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   uint32_t* tslot = reinterpret_cast<uint32_t*>(dbar + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ct = blockIdx.x % g.nct;
-  const int slot = blockIdx.x / g.nct, nslot = gridDim.x / g.nct;
+  const int ct = blockIdx.x % nct;
+  const int slot = blockIdx.x / nct, nslot = gridDim.x / nct;
   const int mode = a.mode;
   const bool rdU = (mode == 1 || mode == 3);   // U is read (TMA) in these modes
   const bool wrU = (mode == 1 || mode == 2);   // U' is written (TMA store) in these modes
-  const int nbox = (ct * 128 + 64 < sh.kc) ? 2 : 1;   // 64-channel boxes of U inside kc
+  const int nbox = min(ubox, (sh.kc - ct * ctw + 63) / 64);     // 64-channel boxes of U inside kc
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -277,9 +312,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(tslot, TMEM_COLS);
+    ptx::tmem_alloc(tslot, tcols);
     ptx::tmem_relinquish();
   }
+  for (int i = threadIdx.x; i < max(0, ng - 4) * 4 * 32 * 32; i += blockDim.x) sAcc2[i] = 0.f;
   // zero rows after the copies of each stage (read by the padded taps, times zero)
   for (int i = threadIdx.x; i < 2 * NIMG * 64; i += blockDim.x) {
     const int st = i / (NIMG * 64), half = (i / 64) % NIMG;
@@ -295,12 +331,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 
   if (warp == 0) {
     if (lane == 0) {
-      ptx::mbar_arrive_expect_tx(abar, (uint32_t)(NIMG * g.nch_f * CHUNK));
+      ptx::mbar_arrive_expect_tx(abar, (uint32_t)(NIMG * g.nch_f * chunkF));
       for (int im = 0; im < NIMG; ++im) {
-        // image im of channel tile ct: the lo images follow the nct hi images
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(sh.VtImg) + ((size_t)im * g.nct + ct) * g.nch_f * CHUNK;
+        // image im of channel tile ct (split: the lo images follow the nct hi images)
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(SPLIT ? sh.VtImgS : sh.VtImg) +
+                             ((size_t)im * nct + ct) * g.nch_f * chunkF;
         for (int c = 0; c < g.nch_f; ++c)
-          ptx::bulk_g2s(sA + ((size_t)im * g.nch_f + c) * CHUNK, src + (size_t)c * CHUNK, CHUNK, abar);
+          ptx::bulk_g2s(sA + ((size_t)im * g.nch_f + c) * chunkF, src + (size_t)c * chunkF, (uint32_t)chunkF, abar);
       }
       const uint32_t hbytes = (uint32_t)(NIMG * g.k2 * g.region_bytes);
       int it = 0;
@@ -328,8 +365,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
           ptx::mbar_arrive_expect_tx(&ufull[us], (uint32_t)(NIMG * nbox * CHUNK));
           for (int half = 0; half < NIMG; ++half)
             for (int bx = 0; bx < nbox; ++bx)
-              ptx::tma_load_4d(sU + (size_t)us * ustage + (size_t)half * USTAGE + (size_t)bx * CHUNK,
-                               half ? J.tmapUlo : J.tmapU, ct * 128 + bx * 64, tw * TW, th * TH, t, &ufull[us]);
+              ptx::tma_load_4d(sU + (size_t)us * ustage + (size_t)half * uhalf + (size_t)bx * CHUNK,
+                               half ? J.tmapUlo : J.tmapU, ct * ctw + bx * 64, tw * TW, th * TH, t, &ufull[us]);
         }
       }
       // every issued load has landed before the CTA can exit
@@ -351,14 +388,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       for (int i = lane; i < g.nmma; i += 32) {
         ulonglong2 dd;
         dd.x = ptx::sdesc(hB + a.tab.boff[i], a.tab.kstr[i], nstride, 0);
-        dd.y = ptx::sdesc(aB + (uint32_t)(i >> 2) * CHUNK + (uint32_t)(i & 3) * 32, 16, 1024, 2);
+        dd.y = ptx::sdesc(aB + (uint32_t)(i >> 2) * (uint32_t)chunkF + (uint32_t)(i & 3) * 32, 16, 1024, 2);
         sDesc[i] = dd;
       }
       __syncwarp();
     }
     if (lane == 0) {
       if (!ptx::mbar_wait_abortable(abar, 0, abort)) failed = true;
-      const uint32_t idesc = ptx::idesc_bf16(128, 128, 1, 0);
+      const uint32_t idesc = ptx::idesc_bf16(128, (uint32_t)ctw, 1, 0);
       int it = 0;
       for (int tg = slot; !failed && tg < sh.total_tiles; tg += nslot, ++it) {
         const int s = it & 1, b = it & 1;
@@ -366,12 +403,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         if (!ptx::mbar_wait_abortable(&full[s], ph, abort)) { failed = true; break; }
         if (!ptx::mbar_wait_abortable(&tempty[b], ph ^ 1, abort)) { failed = true; break; }
         ptx::tc_fence_after();
-        const uint32_t d = tbase + (uint32_t)b * 128;
+        const uint32_t d = tbase + (uint32_t)(b * ctw);
         const uint64_t sadd = (uint64_t)(((uint32_t)s * (uint32_t)stage_bytes) >> 4);   // start-address field
         // chains: (hi, hi); SPLIT adds (lo halo, hi V^T) and (hi halo, lo V^T)
         for (int chn = 0; chn < (SPLIT ? 3 : 1); ++chn) {
           const uint64_t aoff = chn == 1 ? (uint64_t)(g.lo_off >> 4) : 0;
-          const uint64_t boff = chn == 2 ? (uint64_t)((g.nch_f * CHUNK) >> 4) : 0;
+          const uint64_t boff = chn == 2 ? (uint64_t)((g.nch_f * chunkF) >> 4) : 0;
           if (a.tab.reg) {
             // regular tap layout: both descriptors advance by register adds (no table
             // loads, so the issue rate is the tensor core's): A by 256 bytes inside a
@@ -383,7 +420,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
             for (int i = 0; i < g.nmma; ++i) {
               ptx::mma_bf16(d, ad, bd, idesc, (chn > 0 || i > 0) ? 1u : 0u);
               if (++jj == a.tab.hp) { jj = 0; ad += a_run; } else { ad += 16; }
-              if (++bq == 4) { bq = 0; bd += (CHUNK >> 4) - 6; } else { bd += 2; }
+              if (++bq == 4) { bq = 0; bd += (uint64_t)((chunkF >> 4) - 6); } else { bd += 2; }
             }
           } else {
 #pragma unroll 4
@@ -402,22 +439,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     }
   } else {
     // Epilogue: 16 warps. Warp w reads TMEM lanes 32q..32q+31 (q = w % 4), i.e. voxels
-    // 32q + lane of the tile, and columns 32g..32g+31 (g = (w - 2) / 4), i.e. 32 channels.
-    // U of the tile sits in a shared-memory stage (two SW128 boxes of 64 channels, row =
-    // voxel), loaded by TMA ahead of time; U' is written back into the stage and stored
-    // by TMA. Column sums of U'^2 stay in registers (per voxel lane, per channel) across
-    // all tiles of a job that this CTA processes, and are reduced over the warp once per
-    // job into one partial row per (CTA, voxel quarter).
+    // 32q + lane of the tile, and column groups cg = (w - 2) / 4 and, in a channel tile
+    // wider than 128, cg + 4 (32 channels each). U of the tile sits in a shared-memory
+    // stage (SW128 boxes of 64 channels, row = voxel), loaded by TMA ahead of time; U' is
+    // written back into the stage and stored by TMA. Column sums of U'^2 stay, per voxel
+    // lane and channel, in registers (first group) or in a shared-memory slot of the warp
+    // (second group) across all tiles of a job that this CTA processes, and are reduced
+    // over the warp once per job into one partial row per (CTA, voxel quarter).
     // A failed wait marks the thread failed; it still passes every named barrier (the
     // other warps may be waiting there) but does no more waiting.
     const int q = warp & 3;
-    const int cg = (warp - 2) >> 2;
     const int ew = warp - 2;
+    const int cgs[2] = {ew >> 2, (ew >> 2) + 4};
+    const int ntask = cgs[1] < ng ? 2 : 1;
     const int vox = q * 32 + lane;
-    const int c0 = ct * 128 + cg * 32;                          // first channel of this warp
-    const int nun = max(0, min(4, (sh.kc - c0) / 8));           // 8-channel units inside kc
     const uint32_t usw = (uint32_t)(lane & 7);                  // SW128 row phase (vox % 8)
-    float* sDw = sD + ew * 32;
+    float* acc2 = sAcc2 + (size_t)((cgs[1] - 4) * 4 + q) * 32 * 32;   // second group's sums [j][lane]
     float acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
@@ -431,16 +468,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
         if (cur >= 0 && wrU) {
           // flush the previous job's column sums
           const JobDev& P = sh.jobs[cur];
-          warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+          for (int ti = 0; ti < ntask; ++ti) {
+            const int c0 = ct * ctw + cgs[ti] * 32;
+            if (ti == 1) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+              for (int j = 0; j < 32; ++j) { acc[j] = acc2[j * 32 + lane]; acc2[j * 32 + lane] = 0.f; }
+            }
+            warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+          }
         }
         cur = jb;
         row0 = tile;
         if (rdU) {
           const float* src = mode == 1 ? J.D : J.s;
           const float sc = mode == 1 ? 1.f : (float)(1.0 / J.sc->theta);
-          sDw[lane] = (c0 + lane < sh.kc) ? src[c0 + lane] * sc : 0.f;
+          for (int ti = 0; ti < ntask; ++ti) {
+            const int c0 = ct * ctw + cgs[ti] * 32;
+            sD[ew * sdw + ti * 32 + lane] = (c0 + lane < sh.kc) ? src[c0 + lane] * sc : 0.f;
+          }
           __syncwarp();
         }
       }
@@ -451,104 +498,126 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       const uint32_t ph = (it >> 1) & 1;
       const int us = it % nus;
       const uint32_t uph = (it / nus) & 1;
-      uint8_t* urow = sU + (size_t)us * ustage + (size_t)(cg >> 1) * CHUNK + (size_t)vox * 128;
-      uint8_t* urow_lo = urow + USTAGE;                          // SPLIT: the lo tile
-      const uint32_t u0 = (uint32_t)(cg & 1) * 4;
       if (!failed)
         failed = !ptx::mbar_wait_abortable(rdU ? &ufull[us] : &uempty[us], rdU ? uph : (uph ^ 1), abort);
       if (!failed) failed = !ptx::mbar_wait_abortable(&tfull[b], ph, abort);
       ptx::tc_fence_after();
+      // the groups' accumulator columns are read one after the other into e (the second
+      // after the first has been used); the accumulator is released after the last read
       float e[32];
-      ptx::tmem_ld32(tbase + (uint32_t)b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)cg * 32, e);
-      ptx::tmem_ld_wait();
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&tempty[b]);     // the accumulator is in registers
-      if (mode == 3) {
-        float rsum = 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (u < nun) {
-            const uint4 x = *reinterpret_cast<const uint4*>(urow + (((u0 + u) ^ usw) << 4));
-            uint4 xl = make_uint4(0u, 0u, 0u, 0u);
-            if (SPLIT) xl = *reinterpret_cast<const uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
-            const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
-            const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
-            const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-            const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
-            const uint32_t xlw[4] = {xl.x, xl.y, xl.z, xl.w};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float uf = __uint_as_float((j & 1) ? (xw[j >> 1] & 0xffff0000u) : (xw[j >> 1] << 16));
-              if (SPLIT) uf += __uint_as_float((j & 1) ? (xlw[j >> 1] & 0xffff0000u) : (xlw[j >> 1] << 16));
-              const float r = fmaf(uf, dv[j], e[8 * u + j]);
-              rsum = fmaf(r, r, rsum);
-            }
-          }
+      const uint32_t tl = tbase + (uint32_t)(b * ctw) + ((uint32_t)(q * 32) << 16);
+      float rsum = 0.f;
+#pragma unroll 1
+      for (int ti = 0; ti < ntask; ++ti) {
+        ptx::tmem_ld32(tl + (uint32_t)cgs[ti] * 32, e);
+        ptx::tmem_ld_wait();
+        if (ti == ntask - 1) {
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&tempty[b]);     // the accumulator is in registers
         }
-        if (!valid) rsum = 0.f;
+        const int cg = cgs[ti];
+        const int c0 = ct * ctw + cg * 32;                        // first channel of this group
+        const int nun = max(0, min(4, (sh.kc - c0) / 8));         // 8-channel units inside kc
+        const float* sDw = sD + ew * sdw + ti * 32;
+        uint8_t* urow = sU + (size_t)us * ustage + (size_t)(cg >> 1) * CHUNK + (size_t)vox * 128;
+        uint8_t* urow_lo = urow + uhalf;                          // SPLIT: the lo tile
+        const uint32_t u0 = (uint32_t)(cg & 1) * 4;
+        if (mode == 3) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
-        if (lane == 0) J.rpart[(size_t)tile * sh.nrp + ct * 16 + cg * 4 + q] = rsum;
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (u < nun) {
-            uint4* p = reinterpret_cast<uint4*>(urow + (((u0 + u) ^ usw) << 4));
-            uint4* pl = reinterpret_cast<uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
-            float dv[8];
-            uint32_t xw[4] = {0u, 0u, 0u, 0u}, xlw[4] = {0u, 0u, 0u, 0u};
-            if (mode == 1) {
-              const uint4 x = *p;
-              xw[0] = x.x; xw[1] = x.y; xw[2] = x.z; xw[3] = x.w;
-              if (SPLIT) {
-                const uint4 y = *pl;
-                xlw[0] = y.x; xlw[1] = y.y; xlw[2] = y.z; xlw[3] = y.w;
-              }
+          for (int u = 0; u < 4; ++u) {
+            if (u < nun) {
+              const uint4 x = *reinterpret_cast<const uint4*>(urow + (((u0 + u) ^ usw) << 4));
+              uint4 xl = make_uint4(0u, 0u, 0u, 0u);
+              if (SPLIT) xl = *reinterpret_cast<const uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
               const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
               const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
-              dv[0] = d0.x; dv[1] = d0.y; dv[2] = d0.z; dv[3] = d0.w;
-              dv[4] = d1.x; dv[5] = d1.y; dv[6] = d1.z; dv[7] = d1.w;
-            } else {
+              const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+              const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+              const uint32_t xlw[4] = {xl.x, xl.y, xl.z, xl.w};
 #pragma unroll
-              for (int j = 0; j < 8; ++j) dv[j] = 0.f;
+              for (int j = 0; j < 8; ++j) {
+                float uf = __uint_as_float((j & 1) ? (xw[j >> 1] & 0xffff0000u) : (xw[j >> 1] << 16));
+                if (SPLIT) uf += __uint_as_float((j & 1) ? (xlw[j >> 1] & 0xffff0000u) : (xlw[j >> 1] << 16));
+                const float r = fmaf(uf, dv[j], e[8 * u + j]);
+                rsum = fmaf(r, r, rsum);
+              }
             }
-            uint32_t ow[4], olw[4];
+          }
+        } else {
 #pragma unroll
-            for (int j2 = 0; j2 < 4; ++j2) {
-              // the two channels of word j2 (its low and high halves)
-              float ua = __uint_as_float(xw[j2] << 16), ub = __uint_as_float(xw[j2] & 0xffff0000u);
-              if (SPLIT) {
-                ua += __uint_as_float(xlw[j2] << 16);
-                ub += __uint_as_float(xlw[j2] & 0xffff0000u);
+          for (int u = 0; u < 4; ++u) {
+            if (u < nun) {
+              uint4* p = reinterpret_cast<uint4*>(urow + (((u0 + u) ^ usw) << 4));
+              uint4* pl = reinterpret_cast<uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
+              float dv[8];
+              uint32_t xw[4] = {0u, 0u, 0u, 0u}, xlw[4] = {0u, 0u, 0u, 0u};
+              if (mode == 1) {
+                const uint4 x = *p;
+                xw[0] = x.x; xw[1] = x.y; xw[2] = x.z; xw[3] = x.w;
+                if (SPLIT) {
+                  const uint4 y = *pl;
+                  xlw[0] = y.x; xlw[1] = y.y; xlw[2] = y.z; xlw[3] = y.w;
+                }
+                const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
+                const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
+                dv[0] = d0.x; dv[1] = d0.y; dv[2] = d0.z; dv[3] = d0.w;
+                dv[4] = d1.x; dv[5] = d1.y; dv[6] = d1.z; dv[7] = d1.w;
+              } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) dv[j] = 0.f;
               }
-              const float na = fmaf(ua, dv[2 * j2], -e[8 * u + 2 * j2]);
-              const float nb = fmaf(ub, dv[2 * j2 + 1], -e[8 * u + 2 * j2 + 1]);
-              const __nv_bfloat162 pr = __floats2bfloat162_rn(na, nb);
-              ow[j2] = *reinterpret_cast<const uint32_t*>(&pr);
-              float ra = __uint_as_float(ow[j2] << 16), rb = __uint_as_float(ow[j2] & 0xffff0000u);
-              if (SPLIT) {
-                const __nv_bfloat162 pl2 = __floats2bfloat162_rn(na - ra, nb - rb);
-                olw[j2] = *reinterpret_cast<const uint32_t*>(&pl2);
-                ra += __uint_as_float(olw[j2] << 16);
-                rb += __uint_as_float(olw[j2] & 0xffff0000u);
+              uint32_t ow[4], olw[4];
+#pragma unroll
+              for (int j2 = 0; j2 < 4; ++j2) {
+                // the two channels of word j2 (its low and high halves)
+                float ua = __uint_as_float(xw[j2] << 16), ub = __uint_as_float(xw[j2] & 0xffff0000u);
+                if (SPLIT) {
+                  ua += __uint_as_float(xlw[j2] << 16);
+                  ub += __uint_as_float(xlw[j2] & 0xffff0000u);
+                }
+                const float na = fmaf(ua, dv[2 * j2], -e[8 * u + 2 * j2]);
+                const float nb = fmaf(ub, dv[2 * j2 + 1], -e[8 * u + 2 * j2 + 1]);
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(na, nb);
+                ow[j2] = *reinterpret_cast<const uint32_t*>(&pr);
+                float ra = __uint_as_float(ow[j2] << 16), rb = __uint_as_float(ow[j2] & 0xffff0000u);
+                if (SPLIT) {
+                  const __nv_bfloat162 pl2 = __floats2bfloat162_rn(na - ra, nb - rb);
+                  olw[j2] = *reinterpret_cast<const uint32_t*>(&pl2);
+                  ra += __uint_as_float(olw[j2] << 16);
+                  rb += __uint_as_float(olw[j2] & 0xffff0000u);
+                }
+                const int ja = 8 * u + 2 * j2;
+                if (ti == 0) {
+                  acc[ja] = valid ? fmaf(ra, ra, acc[ja]) : acc[ja];
+                  acc[ja + 1] = valid ? fmaf(rb, rb, acc[ja + 1]) : acc[ja + 1];
+                } else if (valid) {
+                  acc2[ja * 32 + lane] = fmaf(ra, ra, acc2[ja * 32 + lane]);
+                  acc2[(ja + 1) * 32 + lane] = fmaf(rb, rb, acc2[(ja + 1) * 32 + lane]);
+                }
               }
-              acc[8 * u + 2 * j2] = valid ? fmaf(ra, ra, acc[8 * u + 2 * j2]) : acc[8 * u + 2 * j2];
-              acc[8 * u + 2 * j2 + 1] = valid ? fmaf(rb, rb, acc[8 * u + 2 * j2 + 1]) : acc[8 * u + 2 * j2 + 1];
+              *p = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+              if (SPLIT) *pl = make_uint4(olw[0], olw[1], olw[2], olw[3]);
             }
-            *p = make_uint4(ow[0], ow[1], ow[2], ow[3]);
-            if (SPLIT) *pl = make_uint4(olw[0], olw[1], olw[2], olw[3]);
           }
         }
-        ptx::fence_proxy_async_smem();    // U' in shared memory -> the TMA store
+        if (mode == 3) {
+          // residual partial of this group (one per (channel group, voxel quarter))
+          float r = valid ? rsum : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+          if (lane == 0) J.rpart[(size_t)tile * sh.nrp + (ct * ng + cg) * 4 + q] = r;
+          rsum = 0.f;
+        }
       }
+      if (mode != 3) ptx::fence_proxy_async_smem();    // U' in shared memory -> the TMA store
       ptx::named_bar_sync(1, 32 * EPI_WARPS);
       if (ew == 0 && lane == 0) {
         if (wrU) {
           for (int half = 0; half < NIMG; ++half)
             for (int bx = 0; bx < nbox; ++bx)
-              ptx::tma_store_4d(half ? J.tmapUlo : J.tmapU, sU + (size_t)us * ustage + (size_t)half * USTAGE +
-                                (size_t)bx * CHUNK, ct * 128 + bx * 64, tw * TW, th * TH, t);
+              ptx::tma_store_4d(half ? J.tmapUlo : J.tmapU, sU + (size_t)us * ustage + (size_t)half * uhalf +
+                                (size_t)bx * CHUNK, ct * ctw + bx * 64, tw * TW, th * TH, t);
           ptx::bulk_commit_group();
           ptx::bulk_wait_group_read0();   // the stage may be refilled once the store has read it
         }
@@ -557,7 +626,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     }
     if (cur >= 0 && wrU) {
       const JobDev& P = sh.jobs[cur];
-      warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+      for (int ti = 0; ti < ntask; ++ti) {
+        const int c0 = ct * ctw + cgs[ti] * 32;
+        if (ti == 1) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) { acc[j] = acc2[j * 32 + lane]; acc2[j * 32 + lane] = 0.f; }
+        }
+        warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+      }
     }
     if (ew == 0 && lane == 0 && wrU) ptx::bulk_wait_group0();   // U' stores complete
   }
@@ -566,7 +642,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tbase, TMEM_COLS);
+    ptx::tmem_dealloc(tbase, tcols);
   }
 }
 
@@ -1028,8 +1104,8 @@ EncodeTiledFn encoder() {
 // ---------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------
-TcGeom tc_geom(int k1, int k2, int k3, int kc, int gpt_max) {
-  TcGeom g = make_geom(k1, k2, k3, gpt_max);
+TcGeom tc_geom(int k1, int k2, int k3, int kc, const TcTiles& t) {
+  TcGeom g = make_geom(k1, k2, k3, t.gpt_max, t.ctw_max, t.nus_max);
   g.kc = kc;
   return g;
 }
@@ -1048,18 +1124,19 @@ bool tc_supported(int k1, int k2, int k3, std::string* why) {
   return true;
 }
 
-cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out, int gpt_max) {
-  TcGeom g = make_geom(k1, k2, k3, gpt_max);
-  g.kc = kc;
-  out->g = g;
-  const int k = g.k;
-  const size_t per = (size_t)g.nch_f * CHUNK;
-  const int nimg = g.split_ok ? 2 : 1;                // hi images, then lo images
-  std::vector<uint8_t> img((size_t)nimg * g.nct * per, 0);
+// B image of the forward pass for channel tiles of `ctw` channels: tile ct, K chunk c (64
+// taps), row r (channel ct*ctw + r), SW128 K-major (16-byte unit j of row r at unit
+// j ^ (r % 8) of its 128-byte row, 8-row groups 1024 bytes apart); the taps in the
+// forward K order (w-runs of k1*k3 taps padded to R8). `part` 0: bf16(V), 1: the
+// remainder bf16(V - bf16(V)).
+static std::vector<uint8_t> fwd_images(const TcGeom& g, const double* V64, int ctw, int nct, int part) {
+  const int k = g.k, k1 = g.k1, k3 = g.k3;
+  const size_t chunk = (size_t)ctw * 128, per = (size_t)g.nch_f * chunk;
+  std::vector<uint8_t> img((size_t)nct * per, 0);
   const int per8 = g.R8 / 8;
-  for (int ct = 0; ct < g.nct; ++ct)
-    for (int r = 0; r < 128; ++r) {
-      const int ch = ct * 128 + r;
+  for (int ct = 0; ct < nct; ++ct)
+    for (int r = 0; r < ctw; ++r) {
+      const int ch = ct * ctw + r;
       if (ch >= k) continue;
       for (int kap = 0; kap < g.kpad; ++kap) {
         const int grp = kap / 8, rin = kap % 8;
@@ -1067,20 +1144,24 @@ cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, Tc
         const int sw = grp / per8, rr = (grp % per8) * 8 + rin;
         if (rr >= g.R) continue;
         const int u = g.R - 1 - rr, sh = u / k3, st = u % k3;
-        const int s = (st * k1 + sh) * k2 + sw;
-        const float vf = (float)V64[(size_t)ch * k + s];
-        const __nv_bfloat16 b = __float2bfloat16(vf);
-        const int chunk = kap / 64, col = kap % 64;
-        const size_t off = (size_t)ct * per + (size_t)chunk * CHUNK + (r / 8) * 1024 + (r % 8) * 128 +
+        const int s = (st * k1 + sh) * g.k2 + sw;
+        const double vd = V64[(size_t)ch * k + s];
+        const __nv_bfloat16 hi = __float2bfloat16((float)vd);
+        const __nv_bfloat16 b = part == 0 ? hi : __float2bfloat16((float)(vd - (double)__bfloat162float(hi)));
+        const int c = kap / 64, col = kap % 64;
+        const size_t off = (size_t)ct * per + (size_t)c * chunk + (r / 8) * 1024 + (r % 8) * 128 +
                            (((col / 8) ^ (r % 8)) * 16) + (col % 8) * 2;
         memcpy(&img[off], &b, 2);
-        if (nimg == 2) {
-          // lo part of V^T: the remainder of the FP64 value after the hi part
-          const __nv_bfloat16 bl = __float2bfloat16((float)(V64[(size_t)ch * k + s] - (double)__bfloat162float(b)));
-          memcpy(&img[(size_t)g.nct * per + off], &bl, 2);
-        }
       }
     }
+  return img;
+}
+
+cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out, const TcTiles& t) {
+  TcGeom g = make_geom(k1, k2, k3, t.gpt_max, t.ctw_max, t.nus_max);
+  g.kc = kc;
+  out->g = g;
+  std::vector<uint8_t> img = fwd_images(g, V64, g.ctw, g.nct, 0);
   for (int i = 0; i < 64; ++i) { out->boff[i] = 0; out->kstr[i] = 0; }
   for (int i = 0; i < g.nmma; ++i) {
     out->boff[i] = group_off(g, 2 * i);
@@ -1088,15 +1169,29 @@ cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, Tc
   }
   cudaError_t e = cudaMalloc(&out->VtImg, img.size());
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(out->VtImg, img.data(), img.size(), cudaMemcpyHostToDevice);
+  if ((e = cudaMemcpy(out->VtImg, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if (g.split_ok) {
+    std::vector<uint8_t> hi = fwd_images(g, V64, 128, g.nct_s, 0), lo = fwd_images(g, V64, 128, g.nct_s, 1);
+    hi.insert(hi.end(), lo.begin(), lo.end());
+    if ((e = cudaMalloc(&out->VtImgS, hi.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(out->VtImgS, hi.data(), hi.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 void tc_free_vdata(TcVData* v) {
   if (v->VtImg) cudaFree(v->VtImg);
+  if (v->VtImgS) cudaFree(v->VtImgS);
   v->VtImg = nullptr;
+  v->VtImgS = nullptr;
 }
 
-int tc_nrp(int k) { return 16 * ((k + 127) / 128); }
+// residual partials per tile: 4 per 32-channel group of every channel tile (an upper bound
+// for both channel-tile widths)
+int tc_nrp(int k) {
+  const int kc = (k + 15) / 16 * 16;
+  return std::max(16 * ((k + 127) / 128), 4 * ((kc + 31) / 32));
+}
 
 static void xc_dims(const TcGeom& g, int H, int W, int T, int& Tp, int& Hp, int& Wp) {
   const int nth = (H + TH - 1) / TH, ntw = (W + TW - 1) / TW;
@@ -1274,14 +1369,14 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
       a.tab.reg = 0;
   a.mode = mode;
   const size_t smem = fwd_smem(v.g, split);
-  const int per = tc_fwd_slots(sh, v);
-  if (split) fwd_tc_kernel<true><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  const int per = tc_fwd_slots(sh, v, split);
+  if (split) fwd_tc_kernel<true><<<per * v.g.nct_s, TC_THREADS, smem, st>>>(a);
   else fwd_tc_kernel<false><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-int tc_fwd_slots(const Shared& sh, const TcVData& v) {
-  return std::max(1, std::min(dev_sms() / v.g.nct, sh.total_tiles));
+int tc_fwd_slots(const Shared& sh, const TcVData& v, bool split) {
+  return std::max(1, std::min(dev_sms() / (split ? v.g.nct_s : v.g.nct), sh.total_tiles));
 }
 
 cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st) {

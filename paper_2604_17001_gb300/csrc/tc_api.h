@@ -17,7 +17,10 @@ struct TcGeom {
   int Hh;           // halo height TH + k1 - 1
   int region_bytes; // one copy's halo: Hh * k3 rows of 16 bytes
   int stage_bytes;  // one halo stage (the k2 copies used + 16 zero rows), 1024-aligned
-  int nct;          // channel tiles of 128
+  int ctw;          // channel-tile width of the plain forward: 128, or kc rounded up to 32
+                    // (128 < that <= 256) when one tile of all channels fits shared memory
+  int nct;          // channel tiles of the plain forward (of ctw channels)
+  int nct_s;        // channel tiles of the split forward (of 128 channels)
   // adjoint pass G = U (D V^T) (M = 128 voxels, N = 128 taps, K = channels)
   int gpt;          // 32-column groups per adjoint tap tile: 4 (N = 128) or 8 (N = 256,
                     // when the wider tile's V D image fits in shared memory)
@@ -43,17 +46,29 @@ struct TcGeom {
 // Per-V device data of the tensor-core path.
 struct TcVData {
   TcGeom g{};
-  __nv_bfloat16* VtImg = nullptr;   // nct forward A images of V^T, nch_f * 16 KiB each; when
-                                    // g.split_ok, nct more of V^T - bf16(V^T) (the lo part)
+  __nv_bfloat16* VtImg = nullptr;   // plain forward: nct B images of V^T (ctw channels each,
+                                    // nch_f chunks of ctw x 128 bytes)
+  __nv_bfloat16* VtImgS = nullptr;  // split forward (when g.split_ok): nct_s images of V^T (128
+                                    // channels each), then nct_s of V^T - bf16(V^T) (the lo part)
   uint32_t boff[64];                // forward: byte offset of each MMA's first K-group
   uint32_t kstr[64];                // forward: byte distance to its second K-group
 };
 
+// Tile choices of the tensor-core passes (upper bounds; a choice that does not fit in
+// shared memory falls back to the narrower one): adjoint tap tiles of 32 * gpt_max columns
+// (4 or 8), forward channel tiles of up to ctw_max channels (128 or 256), forward U stages
+// up to nus_max (1 or 2).
+struct TcTiles {
+  int gpt_max = 8;
+  int ctw_max = 256;
+  int nus_max = 2;
+};
+
 bool tc_supported(int k1, int k2, int k3, std::string* why);
 // Geometry of the tensor-core passes for these kernel dims (kc: the channel stride).
-TcGeom tc_geom(int k1, int k2, int k3, int kc, int gpt_max = 8);
-// gpt_max: widest adjoint tap tile to consider, in 32-column groups (4 or 8)
-cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out, int gpt_max = 8);
+TcGeom tc_geom(int k1, int k2, int k3, int kc, const TcTiles& tiles = TcTiles());
+cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out,
+                           const TcTiles& tiles = TcTiles());
 void tc_free_vdata(TcVData* v);
 size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g);
 // Carve the tensor-core buffers of a job from its allocation and encode its TMA maps;
@@ -71,7 +86,7 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
 cudaError_t tc_attach_ulo(JobDev* d, const TcVData& v, void* ulo, void* host_tmp, cudaStream_t st);
 // CTA slots per channel tile of the forward launch: the update modes write one
 // column-partial row group per (slot, job), min(slots, ntiles) groups per job.
-int tc_fwd_slots(const Shared& sh, const TcVData& v);
+int tc_fwd_slots(const Shared& sh, const TcVData& v, bool split = false);
 // B = V D image per job (bf16, SW128), then the adjoint GEMM + col2im into halo partials.
 cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st);
 cudaError_t tc_launch_adj(const Shared& sh, const TcVData& v, cudaStream_t st);

@@ -39,6 +39,18 @@ class icnnm_stats(C.Structure):
                     theta=self.theta, seconds=self.seconds, latency=self.latency)
 
 
+class icnnm_tile_config(C.Structure):
+    _fields_ = [("adj_tap_width", C.c_int32), ("fwd_channel_width", C.c_int32), ("fwd_u_stages", C.c_int32)]
+
+
+class icnnm_tile_result(C.Structure):
+    _fields_ = [("cfg", icnnm_tile_config), ("adj_tap_width", C.c_int32), ("fwd_channel_width", C.c_int32),
+                ("fwd_u_stages", C.c_int32), ("ms_per_iter", C.c_double)]
+
+
+TILE_TABLE = os.path.join(HERE, "tile_table.json")
+
+
 class ICNNMError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"icnnm status {status}: {msg}")
@@ -76,6 +88,9 @@ def load(path: str = LIB_PATH):
         "icnnm_profile_read": ([P, I32, C.POINTER(D), C.POINTER(I64)], I32),
         "icnnm_profile_voxels": ([P, I32, C.POINTER(I64)], I32),
         "icnnm_job_bytes": ([P, C.POINTER(icnnm_shape), I32, C.POINTER(C.c_size_t)], I32),
+        "icnnm_set_tile_config": ([P, C.POINTER(I64), C.POINTER(icnnm_tile_config)], I32),
+        "icnnm_autotune": ([P, P, I32, C.POINTER(icnnm_shape), I32, C.POINTER(icnnm_tile_config),
+                            C.POINTER(icnnm_tile_result), I32, C.POINTER(I32)], I32),
         "icnnm_check_bounded_wait": ([P, I64], I32),
         "icnnm_cnnm_solve": ([P, C.POINTER(icnnm_shape), P, P, C.POINTER(icnnm_params), P,
                               C.POINTER(icnnm_stats)], I32),
@@ -162,13 +177,20 @@ def icnnm_learn_V_noalloc(refs, kdims, V_out=None, eig_out=None, stream=None):
 class Context:
     """An icnnm_ctx on one CUDA device."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None, tile_table=TILE_TABLE):
+        """tile_table: JSON file of tile configurations per kernel size (written by the
+        autotuner; the package's table by default, None for the built-in defaults)."""
         self.lib = load()
         self.h = C.c_void_p()
         st = self.lib.icnnm_create(C.byref(self.h), device, hbm_budget_bytes,
                                    C.c_void_p(stream) if stream else None)
         if st != OK:
             raise ICNNMError(st, self.lib.icnnm_strerror(st).decode())
+        if tile_table and os.path.exists(tile_table):
+            import json
+            for ent in json.load(open(tile_table)).get("entries", []):
+                self.icnnm_set_tile_config(ent["kdims"], ent["adj_tap_width"], ent["fwd_channel_width"],
+                                           ent["fwd_u_stages"])
 
     def close(self):
         if self.h:
@@ -316,6 +338,29 @@ class Context:
 
     def icnnm_cancel(self, job_id: int):
         self._check(self.lib.icnnm_cancel(self.h, job_id))
+
+    def icnnm_set_tile_config(self, kdims, adj_tap_width=0, fwd_channel_width=0, fwd_u_stages=0):
+        kd = list(kdims) + [1] * (3 - len(kdims))
+        cfg = icnnm_tile_config(int(adj_tap_width), int(fwd_channel_width), int(fwd_u_stages))
+        self._check(self.lib.icnnm_set_tile_config(self.h, (C.c_int64 * 3)(*kd), C.byref(cfg)))
+
+    def icnnm_autotune(self, dims_list, kdims, V, iters=10):
+        """Time every distinct tile geometry on synthetic jobs of the given dims (all
+        stepped together) and adopt the fastest. Returns (best dict, list of results)."""
+        n = len(dims_list)
+        shapes = (icnnm_shape * n)()
+        for i, d in enumerate(dims_list):
+            shapes[i] = make_shape(d, kdims)
+        best = icnnm_tile_config()
+        res = (icnnm_tile_result * 16)()
+        nres = C.c_int32()
+        Vc = self._v_colmajor(V)
+        self._check(self.lib.icnnm_autotune(self.h, _ptr(Vc), n, shapes, int(iters), C.byref(best), res, 16,
+                                            C.byref(nres)))
+        out = [dict(adj_tap_width=r.adj_tap_width, fwd_channel_width=r.fwd_channel_width,
+                    fwd_u_stages=r.fwd_u_stages, ms_per_iter=r.ms_per_iter) for r in res[:nres.value]]
+        return dict(adj_tap_width=best.adj_tap_width, fwd_channel_width=best.fwd_channel_width,
+                    fwd_u_stages=best.fwd_u_stages), out
 
     def icnnm_job_bytes(self, dims, kdims, prec="bf16") -> int:
         s = make_shape(dims, kdims)
