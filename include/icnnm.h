@@ -260,7 +260,8 @@ icnnm_status icnnm_profile_voxels(icnnm_ctx* ctx, int32_t pass, int64_t* voxels)
 /*
  * Tile configuration of the tensor-core passes for one kernel size (no counterpart in the
  * paper; a performance choice that leaves every result unchanged up to the order of FP32
- * additions). Each field is an upper bound; 0 keeps the default (the widest that fits):
+ * additions). Each field is an upper bound (the widest tile that fits in shared memory
+ * below it is taken); 0 keeps the default, the narrow tile (128 / 128 / 2):
  *   adj_tap_width     : columns of an adjoint tap tile, 128 or 256 (256 where the V D image
  *                       of the wider tile fits in shared memory)
  *   fwd_channel_width : channels of a forward channel tile, 128 or 256 (256: one tile of all

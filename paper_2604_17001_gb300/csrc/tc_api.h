@@ -57,10 +57,11 @@ struct TcVData {
 // Tile choices of the tensor-core passes (upper bounds; a choice that does not fit in
 // shared memory falls back to the narrower one): adjoint tap tiles of 32 * gpt_max columns
 // (4 or 8), forward channel tiles of up to ctw_max channels (128 or 256), forward U stages
-// up to nus_max (1 or 2).
+// up to nus_max (1 or 2). The defaults are the narrow tiles; the autotuner (or a table of
+// its results) picks wider ones per kernel size.
 struct TcTiles {
-  int gpt_max = 8;
-  int ctw_max = 256;
+  int gpt_max = 4;
+  int ctw_max = 128;
   int nus_max = 2;
 };
 

@@ -13,6 +13,7 @@ from tests.gpu_util import need_gpu, rel
 pytestmark = pytest.mark.gpu
 
 KD = (7, 7, 3)
+ITERS = 40
 
 
 @pytest.fixture(scope="module")
@@ -23,29 +24,34 @@ def problem():
     L0 = synth.video(H, W, T, seed=81)
     mask = synth.mask_uniform(H, W, T, 0.5, seed=82)
     M = np.where(mask.astype(bool), L0, 0).astype(np.float32)
-    Lo, _ = O.icnnm_solve(M, mask, V, KD, max_iters=60)
-    return V, M, mask, Lo
+    Lo, _ = O.icnnm_solve(M, mask, V, KD, max_iters=ITERS)
+    with icnnm.Context(0, tile_table=None) as ctx:
+        Ld, _ = ctx.icnnm_solve(M, mask, V, KD, max_iters=ITERS, prec="bf16")      # narrow tiles
+    return V, M, mask, Lo, Ld
 
 
 @pytest.mark.parametrize("adj,fwd,stages", [(128, 128, 2), (256, 128, 2), (128, 256, 2), (256, 256, 1), (0, 0, 0)])
 def test_every_tile_geometry_matches_oracle(problem, adj, fwd, stages):
-    V, M, mask, Lo = problem
+    # within the BF16 bar of the oracle, and close to the narrow tiles' result (the
+    # geometries differ only in the order of FP32 additions)
+    V, M, mask, Lo, Ld = problem
     with icnnm.Context(0, tile_table=None) as ctx:
         ctx.icnnm_set_tile_config(KD, adj, fwd, stages)
-        L, _ = ctx.icnnm_solve(M, mask, V, KD, max_iters=60, prec="bf16")
+        L, _ = ctx.icnnm_solve(M, mask, V, KD, max_iters=ITERS, prec="bf16")
     assert rel(L, Lo) <= 1e-3
+    assert rel(L, Ld) <= 2e-4
     assert np.array_equal(L[mask.astype(bool)], M[mask.astype(bool)])
 
 
 def test_autotune_adopts_a_measured_candidate(problem):
-    V, M, mask, Lo = problem
+    V, M, mask, Lo, _ = problem
     with icnnm.Context(0, tile_table=None) as ctx:
         best, res = ctx.icnnm_autotune([(40, 32, 8), (32, 48, 10)], KD, V, iters=4)
         assert len(res) >= 2 and all(r["ms_per_iter"] > 0 for r in res)
         fastest = min(res, key=lambda r: r["ms_per_iter"])
         assert best["adj_tap_width"] in (128, 256) and best["fwd_u_stages"] in (1, 2)
         # the adopted configuration is used from now on, and still solves correctly
-        L, _ = ctx.icnnm_solve(M, mask, V, KD, max_iters=60, prec="bf16")
+        L, _ = ctx.icnnm_solve(M, mask, V, KD, max_iters=ITERS, prec="bf16")
         assert rel(L, Lo) <= 1e-3
         assert fastest["ms_per_iter"] <= min(r["ms_per_iter"] for r in res)
         with pytest.raises(icnnm.ICNNMError) as e:
