@@ -332,6 +332,18 @@ def run_ours(args, ws, rank, local, sub=False):
                  "hbm_gbs_alg": gbs, "tensor_tflops_alg": tfs,
                  "share_of_step": {k_: prof[k_][0] / sum(v[0] for v in prof.values()) for k_ in prof}})
 
+    # the same solves without deterministic reductions (float atomics in the col2im)
+    ctx_nd = icnnm.Context(local, stream=stream.cuda_stream)
+    ctx_nd.icnnm_set_deterministic(False)
+    Ln = torch.zeros_like(Md)
+    fnd = lambda: ctx_nd.icnnm_solve(Md, Kd, Vd, KDIMS, L_out=Ln, max_iters=args.iters, prec="bf16")
+    fnd()
+    nd_sec = _timed(stream, fnd, args.steps)
+    ctx_nd.close()
+    nondet = {"solves_per_s": args.steps / nd_sec, "ms_per_solve": 1e3 * nd_sec / args.steps,
+              "rel_diff_vs_deterministic": float(torch.linalg.norm((Ln - Ld).double()) /
+                                                 torch.linalg.norm(Ld.double()))}
+
     # end to end through the C ABI with host buffers
     Mh, Kh, Vh = w["M"], w["mask"], np.ascontiguousarray(V)
     Lh = np.zeros_like(Mh)
@@ -391,6 +403,7 @@ def run_ours(args, ws, rank, local, sub=False):
         "clocks": clk,
         "gpu_launches": int(nall.value),
         "learn_V": learn,
+        "nondeterministic": nondet,
     }
     if sub:
         return out

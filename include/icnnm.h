@@ -283,6 +283,17 @@ typedef struct {
 } icnnm_tile_result;
 
 /*
+ * Deterministic reductions of the BF16 path (on by default; no counterpart in the paper).
+ * On: the col2im sums of the adjoint pass are 64-bit fixed point (2^-40 units, whose
+ * additions are associative) and the forward pass keeps its column partials per fixed chunk
+ * of each job's tiles, so a job's result is the same, bit for bit, alone, in any batch or
+ * serving mix, and from run to run. Off: float atomics and a round-robin tile order, faster
+ * on large kernels (k = 405: about 20%) but reproducible only to rounding. Applies to V data
+ * built after the call (set it before the first BF16 solve of a V).
+ */
+icnnm_status icnnm_set_deterministic(icnnm_ctx* ctx, int32_t on);
+
+/*
  * Use cfg for BF16 work with these kernel dims from now on in this context (V data built
  * before the call keep their tiles). EINVAL for widths other than 0/128/256 or stages
  * other than 0/1/2.

@@ -149,6 +149,7 @@ struct icnnm_ctx {
   std::map<std::string, std::unique_ptr<VData>> vcache;   // inserted under mu and vmu
   std::mutex vmu;                  // lookups of vcache without mu (the submitting side)
   std::map<std::string, TcTiles> tiles;   // tile configuration per kernel dims ("k1_k2_k3")
+  int det = 1;                     // deterministic reductions of the BF16 path
   // serving
   std::mutex qmu;
   std::condition_variable qcv;
@@ -408,7 +409,9 @@ std::string kdims_key(int k1, int k2, int k3) {
 
 TcTiles tiles_for(icnnm_ctx* c, int k1, int k2, int k3) {
   auto it = c->tiles.find(kdims_key(k1, k2, k3));
-  return it == c->tiles.end() ? TcTiles() : it->second;
+  TcTiles t = it == c->tiles.end() ? TcTiles() : it->second;
+  t.det = c->det;
+  return t;
 }
 
 void ensure_tc(icnnm_ctx* c, VData* vd, int prec) {
@@ -442,6 +445,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   d.H = j.H; d.W = j.W; d.T = j.T;
   d.nth = (j.H + TH - 1) / TH; d.ntw = (j.W + TW - 1) / TW;
   d.ntiles = d.nth * d.ntw * j.T;
+  d.fchunk = fwd_chunk_of(d.ntiles);
   d.m = m;
   d.lam = j.p.lambda; d.rho = j.p.rho; d.theta_max = j.p.theta_max;
   d.sc = (JobScal*)take(sizeof(JobScal));
@@ -476,7 +480,7 @@ void alloc_job(icnnm_ctx* c, Job& j) {
   CK(cudaMemsetAsync(d.U, 0, (size_t)m * kc * (j.p.prec == ICNNM_FP32 ? 4 : 2), c->stream));
   CK(cudaMemsetAsync(d.part, 0, (size_t)d.ntiles * PROW * kc * 4, c->stream));
   CK(cudaMemsetAsync(d.rpart, 0, (size_t)d.ntiles * nrp * 4, c->stream));
-  if (j.p.prec != ICNNM_FP32) CK(cudaMemsetAsync(d.G, 0, (size_t)m * 4, c->stream));
+  if (j.p.prec != ICNNM_FP32) CK(cudaMemsetAsync(d.G, 0, (size_t)m * 8, c->stream));   // fixed-point Delta
   // inputs: staged on the device at submit (serving), else the caller's buffers
   if (j.dstage) {
     CK(cudaMemcpyAsync((void*)d.M, j.dstage, m * 4, cudaMemcpyDeviceToDevice, c->stream));
@@ -567,18 +571,21 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js, int slot = 0) {
     c->dtile0[slot] = nullptr;
     const int cap = std::max(n, 2 * c->list_cap[slot]);
     c->dlist[slot] = (JobDev*)dalloc_async(c, sizeof(JobDev) * std::max(cap, 64), c->stream);
-    c->dtile0[slot] = (int*)dalloc_async(c, sizeof(int) * (std::max(cap, 64) + 1), c->stream);
+    c->dtile0[slot] = (int*)dalloc_async(c, sizeof(int) * 2 * (std::max(cap, 64) + 1), c->stream);
     c->list_cap[slot] = std::max(cap, 64);
   }
-  // one pinned staging buffer: the job table, then the tile prefix sums
-  const size_t tb = sizeof(JobDev) * n, pb = sizeof(int) * (n + 1);
+  // one pinned staging buffer: the job table, then the tile and the chunk prefix sums
+  const size_t tb = sizeof(JobDev) * n, pb = sizeof(int) * 2 * (n + 1);
   icnnm_ctx::Pinned& e = pinned_take(c, tb + pb);
   JobDev* hd = reinterpret_cast<JobDev*>(e.p);
   int* t0 = reinterpret_cast<int*>(e.p + tb);
+  int* c0 = t0 + (n + 1);
   t0[0] = 0;
+  c0[0] = 0;
   for (int i = 0; i < n; ++i) {
     hd[i] = js[i]->dev;
     t0[i + 1] = t0[i] + js[i]->dev.ntiles;
+    c0[i + 1] = c0[i] + (js[i]->dev.ntiles + js[i]->dev.fchunk - 1) / js[i]->dev.fchunk;
   }
   CK(cudaMemcpyAsync(c->dlist[slot], hd, tb, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->dtile0[slot], t0, pb, cudaMemcpyHostToDevice, c->stream));
@@ -593,7 +600,9 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js, int slot = 0) {
   sh.njobs = n;
   sh.jobs = c->dlist[slot];
   sh.job_tile0 = c->dtile0[slot];
+  sh.job_chunk0 = c->dtile0[slot] + (n + 1);
   sh.total_tiles = t0[n];
+  sh.total_chunks = c0[n];
   sh.max_vblk = 1;
   sh.nvox = 0;
   for (int i = 0; i < n; ++i) {
@@ -610,9 +619,10 @@ void run_fwd(icnnm_ctx* c, const Shared& sh, int prec, int mode, const TcVData* 
   else CK(tc_launch_fwd(sh, *tcv, mode, c->stream, prec == ICNNM_BF16X3));
 }
 
-// Row groups of the column partials written by the update pass (0 = one per tile).
+// Tiles per column-partial row group of the update pass.
 int fwd_slots(const Shared& sh, int prec, const TcVData* tcv) {
-  return prec != ICNNM_FP32 ? tc_fwd_slots(sh, *tcv, prec == ICNNM_BF16X3) : 0;
+  if (prec == ICNNM_FP32) return 1;
+  return tcv->g.det ? 0 : -tc_fwd_slots(sh, *tcv, prec == ICNNM_BF16X3);
 }
 
 // Column norms ||A_k(L) v_c||^2 of each job's current L into its colseg through the
@@ -650,7 +660,7 @@ bool gram_colnorms(icnnm_ctx* c, const std::vector<Job*>& js) {
 // same route alone and in a batch.
 void launch_reduce_cols_counted(icnnm_ctx* c, const Shared& sh) {
   PassScope ps(c, 3, 1);
-  CK(launch_reduce_cols(sh, 0, 0, c->stream));
+  CK(launch_reduce_cols(sh, 0, 1, c->stream));
 }
 
 bool gram_route(const Job* j) { return (double)j->m * j->vd->k * j->vd->k >= 2147483648.0; }
@@ -1662,6 +1672,13 @@ static TcTiles tiles_of(const icnnm_tile_config& t) {
   return r;
 }
 
+icnnm_status icnnm_set_deterministic(icnnm_ctx* c, int32_t on) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  c->det = on ? 1 : 0;
+  return ICNNM_OK;
+}
+
 icnnm_status icnnm_set_tile_config(icnnm_ctx* c, const int64_t kdims[3], const icnnm_tile_config* cfg) {
   if (!c || !kdims || !cfg) return ICNNM_EINVAL;
   if (!tile_cfg_ok(*cfg) || kdims[0] < 1 || kdims[1] < 1 || kdims[2] < 1) {
@@ -1725,7 +1742,9 @@ icnnm_status icnnm_autotune(icnnm_ctx* c, const double* V, int32_t n, const icnn
       for (int fw : {256, 128})
         for (int us : {2, 1}) {
           const icnnm_tile_config cfg{aw, fw, us};
-          const TcGeom gg = tc_geom(k1, k2, k3, vd->kc, tiles_of(cfg));
+          TcTiles tl = tiles_of(cfg);
+          tl.det = c->det;
+          const TcGeom gg = tc_geom(k1, k2, k3, vd->kc, tl);
           bool seen = false;
           for (const auto& r : res)
             if (r.adj_tap_width == gg.nta && r.fwd_channel_width == gg.ctw && r.fwd_u_stages == gg.nus) seen = true;
@@ -1735,7 +1754,7 @@ icnnm_status icnnm_autotune(icnnm_ctx* c, const double* V, int32_t n, const icnn
           cand.k1 = k1; cand.k2 = k2; cand.k3 = k3; cand.k = vd->k; cand.kc = vd->kc;
           cand.dVf = vd->dVf;
           cand.dV64 = vd->dV64;
-          CK(tc_build_vdata(vd->V64.data(), k1, k2, k3, vd->kc, &tmp, tiles_of(cfg)));
+          CK(tc_build_vdata(vd->V64.data(), k1, k2, k3, vd->kc, &tmp, tl));
           tmp_built = true;
           cand.tc = tmp;
           cand.tc_ready = true;

@@ -24,6 +24,14 @@ constexpr int TW = 8;
 constexpr int TH = 16;
 constexpr int TILE_VOX = TW * TH;
 constexpr int NSEG = 128;         // row segments of the first column-reduction stage
+// Tiles of a job per column-partial row group of the deterministic BF16 forward pass:
+// decided by the job alone (1 for jobs of fewer than 2048 tiles, up to 4 for large ones),
+// so that the column sums are grouped the same way whatever other jobs share a launch; small
+// chunks keep the CTAs evenly loaded.
+__host__ __device__ inline int fwd_chunk_of(int ntiles) {
+  const int c = ntiles / 1024;
+  return c < 1 ? 1 : (c > 4 ? 4 : c);
+}
 constexpr int PROW = 4;           // column-partial rows per tile (one per group of 32 voxels)
 
 // Mutable per-job scalars (device memory). Kept apart from JobDev so that a job can
@@ -43,6 +51,7 @@ struct JobDev {
   int H, W, T;          // dims
   int nth, ntw;         // voxel tiles along h and w (ceil(H/TH), ceil(W/TW))
   int ntiles;           // nth * ntw * T
+  int fchunk;           // fwd_chunk_of(ntiles)
   long long m;          // H*W*T
   double lam;           // INFINITY for the exact projection
   double rho, theta_max;
@@ -63,8 +72,9 @@ struct JobDev {
   double* colseg;       // first-stage column sums: [NSEG][kc]
   float* s;             // kc, shrink factors of this iteration
   float* D;             // kc, 1 - s
-  float* G;             // FP32 path: G^T = (V D) U^T, [k][m]; BF16 path: col2im sums Delta [m],
-                        //   zero between passes (the gather clears what it reads)
+  float* G;             // FP32 path: G^T = (V D) U^T, [k][m]; BF16 path: col2im sums Delta [m]
+                        //   as 64-bit fixed point (2^-40 units), zero between passes (the
+                        //   gather clears what it reads)
   __nv_bfloat16* B2img; // BF16 path: A-operand images of the adjoint pass (V D)
   const void* tmapX;    // BF16 path: TMA map (CUtensorMap, device memory) of Xc, 8 copies
   const void* tmapX2;   // BF16 path: the same with k2 - 8 copies (kernels wider than 8)
@@ -85,7 +95,9 @@ struct Shared {
   int njobs;
   const JobDev* jobs;    // device array of njobs
   const int* job_tile0;  // device, njobs + 1 prefix sums of ntiles
+  const int* job_chunk0; // device, njobs + 1 prefix sums of ceil(ntiles / fchunk)
   int total_tiles;
+  int total_chunks;
   int max_vblk;          // most 1024-voxel blocks of one job in the list
   long long nvox;        // voxels of all jobs in the list (host-side bookkeeping)
 };
@@ -132,9 +144,11 @@ __device__ __forceinline__ float l_update(const JobDev& J, int k, long long v, f
 cudaError_t launch_init_L(const Shared& sh, cudaStream_t st);
 // synthetic input of the tile autotuner (smooth values, about half observed)
 cudaError_t launch_tune_fill(float* M, uint8_t* mask, int H, int W, int T, cudaStream_t st);
-// slots = 0: the partials have one row group per tile; slots > 0: per forward CTA slot,
-// min(slots, ntiles) row groups per job.
-cudaError_t launch_reduce_cols(const Shared& sh, int advance, int slots, cudaStream_t st);
+// tpr: tiles per column-partial row group (1: one per tile, the FP32 passes; 0: the job's
+// fchunk, the deterministic BF16 forward pass), ceil(ntiles / tpr) row groups per job; tpr
+// < 0: one row group per forward CTA slot (-tpr slots, the BF16 forward without
+// deterministic reductions), min(-tpr, ntiles) per job.
+cudaError_t launch_reduce_cols(const Shared& sh, int advance, int tpr, cudaStream_t st);
 cudaError_t launch_theta0(const Shared& sh, double theta0_user, cudaStream_t st);
 cudaError_t launch_scale_X(const Shared& sh, cudaStream_t st);
 // dst[i] = float(src[i]) (BF16 to FP32 state, for the FP32 finish of a BF16 job)

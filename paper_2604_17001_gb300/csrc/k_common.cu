@@ -46,12 +46,15 @@ __global__ void init_L_kernel(Shared sh) {
 // order and the 8 warp sums are combined in warp order. Block = (job, 32 channels, segment).
 // With `advance`, one block per job moves theta to theta_next and counts the
 // iteration (every kernel of the iteration that reads theta has run by then).
-__global__ void reduce_cols_kernel(Shared sh, int advance, int slots) {
+__global__ void reduce_cols_kernel(Shared sh, int advance, int tpr) {
   const JobDev& J = sh.jobs[blockIdx.x];
   const int c = blockIdx.y * 32 + (threadIdx.x & 31);
   const int warp = threadIdx.x >> 5;
   const int seg = blockIdx.z;
-  const int nrows = (slots > 0 ? min(slots, J.ntiles) : J.ntiles) * PROW;
+  // row groups: tpr > 0 tiles each; tpr == 0: the job's fchunk tiles each; tpr < 0: one per
+  // forward CTA slot (-tpr slots), at most one per tile
+  const int tp = tpr > 0 ? tpr : J.fchunk;
+  const int nrows = (tpr < 0 ? min(-tpr, J.ntiles) : (J.ntiles + tp - 1) / tp) * PROW;
   const int lo = (int)((long long)nrows * seg / NSEG);
   const int hi = (int)((long long)nrows * (seg + 1) / NSEG);
   double acc = 0.0;
@@ -252,9 +255,9 @@ cudaError_t launch_widen_bf16(const __nv_bfloat16* src, float* dst, long long n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_cols(const Shared& sh, int advance, int slots, cudaStream_t st) {
+cudaError_t launch_reduce_cols(const Shared& sh, int advance, int tpr, cudaStream_t st) {
   dim3 grid(sh.njobs, (sh.kc + 31) / 32, NSEG);
-  reduce_cols_kernel<<<grid, 256, 0, st>>>(sh, advance, slots);
+  reduce_cols_kernel<<<grid, 256, 0, st>>>(sh, advance, tpr);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 #include <vector>
 
@@ -56,14 +57,30 @@ constexpr int USTAGE = 2 * 16384;    // one U tile: 128 voxels x 128 channels bf
 constexpr int CHUNK = 16384;         // one SW128 K-chunk: 128 rows x 128 bytes
 constexpr uint32_t TMEM_COLS = 256;
 constexpr int SMEM_LIMIT = 227 * 1024;
+// The col2im sums (the halo buffers and the per-job Delta) are 64-bit fixed point with 40
+// fractional bits: integer additions are associative, so the sums do not depend on the
+// order in which CTAs and warps add them (results are the same alone and in any batch).
+// Range: every column of U D has norm <= 1 (D_c = 1/||U_c|| when ||U_c|| > 1), so each
+// entry of G = U D V^T is at most sqrt(k) and |Delta| <= k sqrt(k) < 2^14 for k <= 512,
+// well inside 2^63 / 2^40 = 2^23; resolution 2^-40.
+constexpr float FX_ONE = 1099511627776.0f;          // 2^40
+constexpr double FX_INV = 1.0 / 1099511627776.0;
+
+__device__ __forceinline__ void fx_add(unsigned long long* p, float v) {
+  atomicAdd(p, (unsigned long long)__float2ll_rn(v * FX_ONE));
+}
+// the col2im accumulation: fixed point (deterministic) or float
+__device__ __forceinline__ void col_add(unsigned long long* p, float v) { fx_add(p, v); }
+__device__ __forceinline__ void col_add(float* p, float v) { atomicAdd(p, v); }
 
 int rup(int x, int a) { return (x + a - 1) / a * a; }
 size_t fwd_smem_n(const TcGeom& g, int nus, bool split = false);
 
 size_t adj_smem(const TcGeom& g);
 
-TcGeom make_geom(int k1, int k2, int k3, int gpt_max, int ctw_max = 256, int nus_max = FWD_USTAGES) {
+TcGeom make_geom(int k1, int k2, int k3, int gpt_max, int ctw_max = 256, int nus_max = FWD_USTAGES, int det = 1) {
   TcGeom g{};
+  g.det = det;
   g.k1 = k1; g.k2 = k2; g.k3 = k3; g.k = k1 * k2 * k3; g.kc = rup(g.k, 16);
   // each w-run of taps is padded to a multiple of 16 (two 8-row K-groups): every MMA then
   // stays inside one run, its K stride is one group and the issuer advances descriptors
@@ -170,7 +187,8 @@ size_t fwd_smem(const TcGeom& g, bool split = false) {
   return split ? fwd_smem_n(g, g.nus_s, true) : fwd_smem_n(g, g.nus);
 }
 size_t adj_smem(const TcGeom& g) {
-  return 1024 + (size_t)g.nch_a * (g.nta * 128) + ADJ_STAGES * (size_t)CHUNK + 2 * (size_t)g.HBp * 4 + 128 * 4 + 256;
+  return 1024 + (size_t)g.nch_a * (g.nta * 128) + ADJ_STAGES * (size_t)CHUNK + 2 * (size_t)g.HBp * (g.det ? 8 : 4) +
+         128 * 4 + 256;
 }
 
 // Byte offset of forward K-group `grp` (8 taps) inside a halo stage.
@@ -246,20 +264,53 @@ __device__ __forceinline__ void warp_colsum_store(float (&a)[32], int lane, floa
 // ---------------------------------------------------------------------------------
 // Forward pass
 // ---------------------------------------------------------------------------------
+// Tile order of a forward CTA: the chunks (fchunk consecutive tiles of one job) of the
+// launch list, every nslot-th from `slot`, each chunk's tiles in order. Column partials
+// are kept per chunk (row group = chunk index within its job), so the sums are grouped the
+// same way whatever other jobs share the launch.
+// Without deterministic reductions the CTA takes every nslot-th tile of the list instead,
+// with one partial row group per (job, CTA): the round-robin order spreads neighbouring
+// tiles over the CTAs, but a job's sums are then grouped by its position in the list.
+struct TileSeq {
+  const Shared& sh;
+  int nslot, det, chg, jb = 0, tile = 0, thi = 0;
+  __device__ TileSeq(const Shared& s, int slot, int ns, int d) : sh(s), nslot(ns), det(d), chg(slot - ns) {}
+  // key of the column-partial group of the current tile
+  __device__ int group() const { return det ? chg : jb; }
+  __device__ bool next() {
+    if (!det) {
+      chg += nslot;                                   // chg is the global tile index here
+      if (chg >= sh.total_tiles) return false;
+      jb = job_of_tile(sh.job_tile0, sh.njobs, chg);
+      tile = chg - sh.job_tile0[jb];
+      return true;
+    }
+    if (++tile < thi) return true;
+    chg += nslot;
+    if (chg >= sh.total_chunks) return false;
+    jb = job_of_tile(sh.job_chunk0, sh.njobs, chg);
+    const int fc = sh.jobs[jb].fchunk;
+    tile = (chg - sh.job_chunk0[jb]) * fc;
+    thi = min(sh.jobs[jb].ntiles, tile + fc);
+    return true;
+  }
+};
 // SPLIT: the operand copies, V^T and U come as hi + lo BF16 pairs (lo = bf16(x - hi)),
 // and each tile takes three products into one accumulator, A_k(X_hi)V_hi + A_k(X_lo)V_hi
 // + A_k(X_hi)V_lo, i.e. A_k(X)V to about 2^-16 relative instead of 2^-8; U' is stored as
 // hi = bf16(U'), lo = bf16(U' - hi). The halo stage holds the hi copies (and 16 zero
 // rows) and then the lo copies (and 16 zero rows); a U stage holds the hi tile and then
 // the lo tile; shared memory holds both V^T images.
-template <bool SPLIT>
+// WIDE: channel tiles of g.ctw > 128 channels (some epilogue warps take two 32-channel
+// groups); otherwise the tile width is the compile-time 128 and each warp one group.
+template <bool SPLIT, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_constant__ FwdArgs a) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1k(smraw);
   const TcGeom& g = a.g;
   const Shared& sh = a.sh;
   constexpr int NIMG = SPLIT ? 2 : 1;
-  const int ctw = SPLIT ? 128 : g.ctw;                          // channels per tile (the MMA's N)
+  const int ctw = (SPLIT || !WIDE) ? 128 : g.ctw;               // channels per tile (the MMA's N)
   const int nct = SPLIT ? g.nct_s : g.nct;
   const int chunkF = ctw * 128;                                  // one K chunk (64 taps) of the B image
   const int ubox = (ctw + 63) / 64;                              // 64-channel U boxes per tile
@@ -341,13 +392,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       }
       const uint32_t hbytes = (uint32_t)(NIMG * g.k2 * g.region_bytes);
       int it = 0;
-      for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
+      TileSeq sq(sh, slot, nslot, g.det);
+      for (; sq.next(); ++it) {
         const int s = it & 1;
         const uint32_t ph = (it >> 1) & 1;
         if (!ptx::mbar_wait_abortable(&empty[s], ph ^ 1, abort)) { failed = true; break; }
-        const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
-        const JobDev& J = sh.jobs[jb];
-        const int tile = tg - sh.job_tile0[jb];
+        const JobDev& J = sh.jobs[sq.jb];
+        const int tile = sq.tile;
         const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
         ptx::mbar_arrive_expect_tx(&full[s], hbytes);
         // w-chunk q holds the copies of taps sw = 8q .. min(8q + 7, k2 - 1); the last
@@ -397,7 +448,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       if (!ptx::mbar_wait_abortable(abar, 0, abort)) failed = true;
       const uint32_t idesc = ptx::idesc_bf16(128, (uint32_t)ctw, 1, 0);
       int it = 0;
-      for (int tg = slot; !failed && tg < sh.total_tiles; tg += nslot, ++it) {
+      TileSeq sq(sh, slot, nslot, g.det);
+      for (; !failed && sq.next(); ++it) {
         const int s = it & 1, b = it & 1;
         const uint32_t ph = (it >> 1) & 1;
         if (!ptx::mbar_wait_abortable(&full[s], ph, abort)) { failed = true; break; }
@@ -451,22 +503,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     const int q = warp & 3;
     const int ew = warp - 2;
     const int cgs[2] = {ew >> 2, (ew >> 2) + 4};
-    const int ntask = cgs[1] < ng ? 2 : 1;
+    const int ntask = (WIDE && cgs[1] < ng) ? 2 : 1;
     const int vox = q * 32 + lane;
     const uint32_t usw = (uint32_t)(lane & 7);                  // SW128 row phase (vox % 8)
     float* acc2 = sAcc2 + (size_t)((cgs[1] - 4) * 4 + q) * 32 * 32;   // second group's sums [j][lane]
     float acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    int cur = -1, row0 = 0;
+    int cur = -1, row0 = 0, curchunk = -1;
     int it = 0;
-    for (int tg = slot; tg < sh.total_tiles; tg += nslot, ++it) {
-      const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+    TileSeq sq(sh, slot, nslot, g.det);
+    for (; sq.next(); ++it) {
+      const int jb = sq.jb;
       const JobDev& J = sh.jobs[jb];
-      const int tile = tg - sh.job_tile0[jb];
-      if (jb != cur) {
+      const int tile = sq.tile;
+      if (sq.group() != curchunk) {
         if (cur >= 0 && wrU) {
-          // flush the previous job's column sums
+          // flush the previous chunk's column sums into its row group
           const JobDev& P = sh.jobs[cur];
           for (int ti = 0; ti < ntask; ++ti) {
             const int c0 = ct * ctw + cgs[ti] * 32;
@@ -480,7 +533,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
           }
         }
         cur = jb;
-        row0 = tile;
+        curchunk = sq.group();
+        row0 = g.det ? tile / J.fchunk : tile;
         if (rdU) {
           const float* src = mode == 1 ? J.D : J.s;
           const float sc = mode == 1 ? 1.f : (float)(1.0 / J.sc->theta);
@@ -680,8 +734,8 @@ __device__ __forceinline__ int adj_rowoff(const TcGeom& g, int TR) {
 // the outputs o = w + 8j), then add those sums into the halo buffer: 1 + (k2 - 1) / 8
 // shared-memory reductions per lane and tap row instead of k2. The sum over the 8 lanes
 // runs in a fixed order; the reductions of different warps into one address do not.
-template <int K2>
-__device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, float* hb, int hoff,
+template <int K2, typename HT>
+__device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, HT* hb, int hoff,
                                                 const TcGeom& g, int G) {
   constexpr int RPG = 32 / K2;
   constexpr int NJ = (K2 + 14) / 8;      // halo columns 0 .. K2 + 6 over 8 lanes
@@ -702,7 +756,7 @@ __device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, 
         if (w + d >= 0 && w + d <= 7) T += x;
       }
       const int o = w + 8 * j;
-      if (o <= K2 + 6) atomicAdd(&hb[base + o], T);
+      if (o <= K2 + 6) col_add(&hb[base + o], T);
     }
   }
 }
@@ -712,8 +766,9 @@ __device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, 
 // (Hb x pitch per frame of the k3-frame halo) and flushes the buffer to the tile's halo
 // partial, which the gather pass sums. K2 = 0 selects the per-element reduction path
 // for kernel widths without a compile-time specialisation.
-template <int K2>
+template <int K2, bool DET>
 __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_constant__ AdjArgs a) {
+  using HT = typename std::conditional<DET, unsigned long long, float>::type;   // halo entry
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1k(smraw);
   const TcGeom& g = a.g;
@@ -722,7 +777,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
   const uint32_t tcols = g.nta == 256 ? 512u : TMEM_COLS;   // two accumulators of nta columns
   uint8_t* sA = sm;
   uint8_t* sU = sm + (size_t)g.nch_a * chunkA;
-  float* buf = reinterpret_cast<float*>(sU + (size_t)ADJ_STAGES * CHUNK);   // [2][HBp]
+  HT* buf = reinterpret_cast<HT*>(sU + (size_t)ADJ_STAGES * CHUNK);   // [2][HBp]
   int* toff = reinterpret_cast<int*>(buf + 2 * (size_t)g.HBp);              // [128] (K2 = 0)
   uint64_t* bars = reinterpret_cast<uint64_t*>(toff + 128);
   uint64_t* full = bars;                           // [ADJ_STAGES]
@@ -760,7 +815,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     ptx::tmem_alloc(tslot, tcols);
     ptx::tmem_relinquish();
   }
-  for (int i = threadIdx.x; i < 2 * g.HBp; i += blockDim.x) buf[i] = 0.f;
+  for (int i = threadIdx.x; i < 2 * g.HBp; i += blockDim.x) buf[i] = (HT)0;
   // K2 = 0: halo offset of each tap column (-1 for padding); G[v][j] lands at
   // buf[h_v * pitch + w_v + toff[j]]
   if (K2 == 0 && threadIdx.x < 128) {
@@ -861,7 +916,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     int prev_jb = 0, prev_t = 0, prev_h0 = 0, prev_w0 = 0;   // tile flushed next: job, frame, halo origin
     for (int tg = lo; tg <= hi; ++tg, ++i) {
       const bool have = tg < hi;
-      float* hb = buf + (size_t)(i & 1) * g.HBp;
+      HT* hb = buf + (size_t)(i & 1) * g.HBp;
       if (have) {
         // buffer i % 2 was last used by tile i - 2; wait until it has been flushed
         if (i >= 2 && !ptx::mbar_wait(&zbar[i & 1], ((i - 2) >> 1) & 1)) { failed = true; break; }
@@ -887,7 +942,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const int o = toff[cg * 32 + e];
-            if (o >= 0) atomicAdd(&hb[vbase + o], v[e]);
+            if (o >= 0) col_add(&hb[vbase + o], v[e]);
           }
         }
         __syncwarp();
@@ -897,7 +952,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
       if (i >= 1) {
         const int pb = (i - 1) & 1;
         if (!ptx::mbar_wait(&redbar[pb], ((i - 1) >> 1) & 1)) { failed = true; break; }
-        float* src = buf + (size_t)pb * g.HBp;
+        HT* src = buf + (size_t)pb * g.HBp;
         // halo entry (frame st, row bh, column bw) belongs to voxel ((t - st) mod T,
         // (th*TH - (k1-1) + bh) mod H, (tw*TW - (k2-1) + bw) mod W); only the nsl frames
         // this tap tile reaches (from slo) can be nonzero
@@ -907,14 +962,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
           const int st = g.slo[tt] + j;
           if (st >= g.k3) continue;
           const int si = ((g.k3 - 1 - st) * g.Hb + bh) * g.pitch + col;
-          const float v = src[si];
-          src[si] = 0.f;
+          const HT v = src[si];
+          src[si] = (HT)0;
           const JobDev& P = sh.jobs[prev_jb];
           int tq = prev_t - st, hq = prev_h0 + bh, wq = prev_w0 + col;
           tq += tq < 0 ? P.T : 0;
           hq = hq < 0 ? hq + P.H : (hq >= P.H ? hq - P.H : hq);
           wq = wq < 0 ? wq + P.W : (wq >= P.W ? wq - P.W : wq);
-          atomicAdd(P.G + ((size_t)tq * P.H + hq) * P.W + wq, v);
+          if (v) atomicAdd(reinterpret_cast<HT*>(P.G) + ((size_t)tq * P.H + hq) * P.W + wq, v);
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&zbar[pb]);
@@ -1015,6 +1070,7 @@ __global__ void prepare_X_kernel(Shared sh, TcGeom g, int from_L) {
 // then the same projection as the FP32 path. Flat over the voxels: block (b, job) takes
 // voxels 1024 b .. 1024 b + 1023 of the job, four per thread with 16-byte accesses; the
 // block's ||L'||^2 partial goes to lpart[b].
+template <bool DET>
 __global__ void __launch_bounds__(256) gather_tc_kernel(Shared sh) {
   const JobDev& J = sh.jobs[blockIdx.y];
   const long long v0 = (long long)blockIdx.x * 1024 + 4 * threadIdx.x;
@@ -1023,9 +1079,20 @@ __global__ void __launch_bounds__(256) gather_tc_kernel(Shared sh) {
   const float xa = (float)(th + thn), xb = -(float)th;
   const float inv = (float)(1.0 / (sh.k * th));
   float l2 = 0.f;
+  unsigned long long* Dx = reinterpret_cast<unsigned long long*>(J.G);   // fixed-point Delta (DET)
   if (v0 + 3 < J.m) {
-    const float4 d = *reinterpret_cast<const float4*>(J.G + v0);
-    *reinterpret_cast<float4*>(J.G + v0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 d;
+    if (DET) {
+      const ulonglong2 da = *reinterpret_cast<const ulonglong2*>(Dx + v0);
+      const ulonglong2 db = *reinterpret_cast<const ulonglong2*>(Dx + v0 + 2);
+      *reinterpret_cast<ulonglong2*>(Dx + v0) = make_ulonglong2(0ull, 0ull);
+      *reinterpret_cast<ulonglong2*>(Dx + v0 + 2) = make_ulonglong2(0ull, 0ull);
+      d = make_float4((float)((double)(long long)da.x * FX_INV), (float)((double)(long long)da.y * FX_INV),
+                      (float)((double)(long long)db.x * FX_INV), (float)((double)(long long)db.y * FX_INV));
+    } else {
+      d = *reinterpret_cast<const float4*>(J.G + v0);
+      *reinterpret_cast<float4*>(J.G + v0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const float4 lo = *reinterpret_cast<const float4*>(J.L + v0);
     const float4 mv = *reinterpret_cast<const float4*>(J.M + v0);
     const uchar4 ob = *reinterpret_cast<const uchar4*>(J.mask + v0);
@@ -1047,8 +1114,14 @@ __global__ void __launch_bounds__(256) gather_tc_kernel(Shared sh) {
     *reinterpret_cast<float4*>(J.X + v0) = make_float4(xn[0], xn[1], xn[2], xn[3]);
   } else {
     for (long long v = v0; v < J.m; ++v) {
-      const float d = J.G[v];
-      J.G[v] = 0.f;
+      float d;
+      if (DET) {
+        d = (float)((double)(long long)Dx[v] * FX_INV);
+        Dx[v] = 0ull;
+      } else {
+        d = J.G[v];
+        J.G[v] = 0.f;
+      }
       const float Ln = l_update(J, sh.k, v, d);
       l2 = fmaf(Ln, Ln, l2);
     }
@@ -1105,7 +1178,7 @@ EncodeTiledFn encoder() {
 // Host side
 // ---------------------------------------------------------------------------------
 TcGeom tc_geom(int k1, int k2, int k3, int kc, const TcTiles& t) {
-  TcGeom g = make_geom(k1, k2, k3, t.gpt_max, t.ctw_max, t.nus_max);
+  TcGeom g = make_geom(k1, k2, k3, t.gpt_max, t.ctw_max, t.nus_max, t.det);
   g.kc = kc;
   return g;
 }
@@ -1158,7 +1231,7 @@ static std::vector<uint8_t> fwd_images(const TcGeom& g, const double* V64, int c
 }
 
 cudaError_t tc_build_vdata(const double* V64, int k1, int k2, int k3, int kc, TcVData* out, const TcTiles& t) {
-  TcGeom g = make_geom(k1, k2, k3, t.gpt_max, t.ctw_max, t.nus_max);
+  TcGeom g = make_geom(k1, k2, k3, t.gpt_max, t.ctw_max, t.nus_max, t.det);
   g.kc = kc;
   out->g = g;
   std::vector<uint8_t> img = fwd_images(g, V64, g.ctw, g.nct, 0);
@@ -1207,7 +1280,7 @@ size_t tc_job_extra_bytes(int H, int W, int T, const TcGeom& g) {
   size_t b = 0;
   auto add = [&](size_t n) { b += (n + 255) / 256 * 256; };
   add((size_t)(g.split_ok ? 2 : 1) * g.ncopy * Tp * Hp * Wp * 2);   // Xc (and its lo copies)
-  add((size_t)H * W * T * 4);                          // col2im sums (Delta)
+  add((size_t)H * W * T * 8);                          // col2im sums (Delta, 64-bit fixed point)
   add((size_t)g.ntt * g.nch_a * g.nta * 128);          // V D images
   add(4 * sizeof(CUtensorMap));                        // TMA maps
   return b;
@@ -1224,7 +1297,7 @@ cudaError_t tc_carve_job(JobDev* d, const TcVData& v, char* base, size_t& off, s
   d->xTp = Tp; d->xHp = Hp; d->xWp = Wp;
   const int ncp = (g.split_ok ? 2 : 1) * g.ncopy;        // copies in Xc (hi, then lo)
   d->Xc = (__nv_bfloat16*)take((size_t)ncp * Tp * Hp * Wp * 2);
-  d->G = (float*)take((size_t)d->m * 4);
+  d->G = (float*)take((size_t)d->m * 8);             // fixed-point Delta (see FX_ONE)
   d->B2img = (__nv_bfloat16*)take((size_t)g.ntt * g.nch_a * g.nta * 128);
   CUtensorMap* tm = (CUtensorMap*)take(4 * sizeof(CUtensorMap));
   if (off > total) return cudaErrorInvalidValue;
@@ -1325,16 +1398,18 @@ std::mutex g_dev_mu;
 
 typedef void (*AdjKernel)(AdjArgs);
 // compile-time kernel widths of the adjoint col2im (others take the per-element path)
-AdjKernel adj_kernel_for(const TcGeom& g) {
-  if (g.rpg == 0) return adj_tc_kernel<0>;
+template <bool DET>
+AdjKernel adj_kernel_for_t(const TcGeom& g) {
+  if (g.rpg == 0) return adj_tc_kernel<0, DET>;
   switch (g.k2) {
-    case 3: return adj_tc_kernel<3>;
-    case 5: return adj_tc_kernel<5>;
-    case 7: return adj_tc_kernel<7>;
-    case 9: return adj_tc_kernel<9>;
-    default: return adj_tc_kernel<0>;
+    case 3: return adj_tc_kernel<3, DET>;
+    case 5: return adj_tc_kernel<5, DET>;
+    case 7: return adj_tc_kernel<7, DET>;
+    case 9: return adj_tc_kernel<9, DET>;
+    default: return adj_tc_kernel<0, DET>;
   }
 }
+AdjKernel adj_kernel_for(const TcGeom& g) { return g.det ? adj_kernel_for_t<true>(g) : adj_kernel_for_t<false>(g); }
 
 int dev_sms() {
   std::lock_guard<std::mutex> lk(g_dev_mu);
@@ -1346,9 +1421,12 @@ int dev_sms() {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     f.sms = n > 0 ? n : 1;
-    cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    for (AdjKernel kf : {adj_tc_kernel<0>, adj_tc_kernel<3>, adj_tc_kernel<5>, adj_tc_kernel<7>, adj_tc_kernel<9>})
+    cudaFuncSetAttribute(fwd_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    cudaFuncSetAttribute(fwd_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    cudaFuncSetAttribute(fwd_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    for (AdjKernel kf : {adj_tc_kernel<0, true>, adj_tc_kernel<3, true>, adj_tc_kernel<5, true>, adj_tc_kernel<7, true>,
+                         adj_tc_kernel<9, true>, adj_tc_kernel<0, false>, adj_tc_kernel<3, false>,
+                         adj_tc_kernel<5, false>, adj_tc_kernel<7, false>, adj_tc_kernel<9, false>})
       cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     f.ready = true;
   }
@@ -1370,13 +1448,14 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
   a.mode = mode;
   const size_t smem = fwd_smem(v.g, split);
   const int per = tc_fwd_slots(sh, v, split);
-  if (split) fwd_tc_kernel<true><<<per * v.g.nct_s, TC_THREADS, smem, st>>>(a);
-  else fwd_tc_kernel<false><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  if (split) fwd_tc_kernel<true, false><<<per * v.g.nct_s, TC_THREADS, smem, st>>>(a);
+  else if (v.g.ctw > 128) fwd_tc_kernel<false, true><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  else fwd_tc_kernel<false, false><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 int tc_fwd_slots(const Shared& sh, const TcVData& v, bool split) {
-  return std::max(1, std::min(dev_sms() / (split ? v.g.nct_s : v.g.nct), sh.total_tiles));
+  return std::max(1, std::min(dev_sms() / (split ? v.g.nct_s : v.g.nct), v.g.det ? sh.total_chunks : sh.total_tiles));
 }
 
 cudaError_t tc_launch_build_B2(const Shared& sh, const TcVData& v, cudaStream_t st) {
@@ -1399,8 +1478,8 @@ cudaError_t tc_bounded_wait_check(uint64_t limit_ns, int* dstatus, cudaStream_t 
 }
 
 cudaError_t tc_launch_gather(const Shared& sh, const TcVData& v, cudaStream_t st) {
-  (void)v;
-  gather_tc_kernel<<<dim3(sh.max_vblk, sh.njobs), 256, 0, st>>>(sh);
+  if (v.g.det) gather_tc_kernel<true><<<dim3(sh.max_vblk, sh.njobs), 256, 0, st>>>(sh);
+  else gather_tc_kernel<false><<<dim3(sh.max_vblk, sh.njobs), 256, 0, st>>>(sh);
   return cudaGetLastError();
 }
 

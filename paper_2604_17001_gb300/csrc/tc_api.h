@@ -35,6 +35,7 @@ struct TcGeom {
   int nus;          // forward U tile stages in shared memory (1 or 2)
   // split forward (ICNNM_BF16X3 and the finish of BF16 jobs): the operand and V^T as
   // hi + lo BF16 pairs, three products per tile, U stored as a hi + lo pair
+  int det;          // deterministic reductions (TcTiles::det)
   int split_ok;     // 1: the split forward fits in shared memory for these kernel dims
   int lo_off;       // byte offset of the lo copies in a split halo stage (after hi + 16 zero rows)
   int stage_bytes_s;// one split halo stage: hi copies, 16 zero rows, lo copies, 16 zero rows
@@ -63,6 +64,8 @@ struct TcTiles {
   int gpt_max = 4;
   int ctw_max = 128;
   int nus_max = 2;
+  int det = 1;      // 1: deterministic reductions (fixed-point col2im, forward partials per
+                    // fixed chunk of a job's tiles); 0: float atomics, strided tiles
 };
 
 bool tc_supported(int k1, int k2, int k3, std::string* why);

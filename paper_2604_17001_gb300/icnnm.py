@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "icnnm_profile_voxels": ([P, I32, C.POINTER(I64)], I32),
         "icnnm_job_bytes": ([P, C.POINTER(icnnm_shape), I32, C.POINTER(C.c_size_t)], I32),
         "icnnm_set_tile_config": ([P, C.POINTER(I64), C.POINTER(icnnm_tile_config)], I32),
+        "icnnm_set_deterministic": ([P, I32], I32),
         "icnnm_autotune": ([P, P, I32, C.POINTER(icnnm_shape), I32, C.POINTER(icnnm_tile_config),
                             C.POINTER(icnnm_tile_result), I32, C.POINTER(I32)], I32),
         "icnnm_check_bounded_wait": ([P, I64], I32),
@@ -338,6 +339,9 @@ class Context:
 
     def icnnm_cancel(self, job_id: int):
         self._check(self.lib.icnnm_cancel(self.h, job_id))
+
+    def icnnm_set_deterministic(self, on: bool):
+        self._check(self.lib.icnnm_set_deterministic(self.h, 1 if on else 0))
 
     def icnnm_set_tile_config(self, kdims, adj_tap_width=0, fwd_channel_width=0, fwd_u_stages=0):
         kd = list(kdims) + [1] * (3 - len(kdims))
