@@ -766,15 +766,19 @@ __device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, 
 // (Hb x pitch per frame of the k3-frame halo) and flushes the buffer to the tile's halo
 // partial, which the gather pass sums. K2 = 0 selects the per-element reduction path
 // for kernel widths without a compile-time specialisation.
-template <int K2, bool DET>
+// WIDE: tap tiles of 256 columns (g.gpt == 8; each epilogue warp takes two column groups);
+// otherwise 128 columns as compile-time constants.
+template <int K2, bool DET, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_constant__ AdjArgs a) {
   using HT = typename std::conditional<DET, unsigned long long, float>::type;   // halo entry
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1k(smraw);
   const TcGeom& g = a.g;
   const Shared& sh = a.sh;
-  const int chunkA = g.nta * 128;                // one 64-channel chunk of the V D image
-  const uint32_t tcols = g.nta == 256 ? 512u : TMEM_COLS;   // two accumulators of nta columns
+  const int nta = WIDE ? 256 : 128;              // tap-tile columns (the MMA's N)
+  const int gpt = WIDE ? 8 : 4;
+  const int chunkA = nta * 128;                  // one 64-channel chunk of the V D image
+  const uint32_t tcols = WIDE ? 512u : TMEM_COLS;   // two accumulators of nta columns
   uint8_t* sA = sm;
   uint8_t* sU = sm + (size_t)g.nch_a * chunkA;
   HT* buf = reinterpret_cast<HT*>(sU + (size_t)ADJ_STAGES * CHUNK);   // [2][HBp]
@@ -856,7 +860,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     if (lane == 0) {
       // A = U tile (voxels x channels), B = V D image (tap columns x channels), both
       // K-major SW128: G[voxel][tap column] in TMEM.
-      const uint32_t idesc = ptx::idesc_bf16(128, (uint32_t)g.nta, 0, 0);
+      const uint32_t idesc = ptx::idesc_bf16(128, (uint32_t)nta, 0, 0);
       // descriptors of U stage 0 and image chunk 0; others differ only in the start address
       const uint64_t ubase = ptx::sdesc(ptx::smem_u32(sU), 16, 1024, 2);
       const uint64_t bbase = ptx::sdesc(ptx::smem_u32(sA), 16, 1024, 2);
@@ -883,7 +887,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         const uint32_t bph = (i >> 1) & 1;
         if (!ptx::mbar_wait(&tempty[b], bph ^ 1)) { failed = true; break; }
         ptx::tc_fence_after();
-        const uint32_t d = tbase + (uint32_t)(b * g.nta);
+        const uint32_t d = tbase + (uint32_t)(b * nta);
         for (int c = 0; c < g.nch_a; ++c, ++cnt) {
           const int s = cnt % ADJ_STAGES;
           const uint32_t ph = (cnt / ADJ_STAGES) & 1;
@@ -924,20 +928,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         const uint32_t bph = (i >> 1) & 1;
         if (!ptx::mbar_wait(&tfull[b], bph)) { failed = true; break; }
         ptx::tc_fence_after();
-        // the warp's column groups: cg, and cg + 4 in a 256-column tap tile (K2 = 0
-        // keeps 128-column tiles)
-        float v[32], v2[32];
-        const uint32_t tl = tbase + (uint32_t)(b * g.nta) + ((uint32_t)(q * 32) << 16);
-        ptx::tmem_ld32(tl + (uint32_t)cg * 32, v);
-        if (g.gpt == 8) ptx::tmem_ld32(tl + (uint32_t)(cg + 4) * 32, v2);
-        ptx::tmem_ld_wait();
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&tempty[b]);
+        // the warp's column groups: cg, and cg + 4 in a 256-column tap tile, read from
+        // TMEM one after the other into v; the accumulator is released after the last read
+        float v[32];
+        const uint32_t tl = tbase + (uint32_t)(b * nta) + ((uint32_t)(q * 32) << 16);
         if constexpr (K2 > 0) {
-          adj_col2im_rows<K2>(v, lane, hb, hoff, g, tt * g.gpt + cg);
-          if (g.gpt == 8) adj_col2im_rows<K2>(v2, lane, hb, hoff, g, tt * g.gpt + cg + 4);
+#pragma unroll 1
+          for (int gi = 0; gi < (WIDE ? 2 : 1); ++gi) {
+            ptx::tmem_ld32(tl + (uint32_t)(cg + 4 * gi) * 32, v);
+            ptx::tmem_ld_wait();
+            if (gi == (WIDE ? 1 : 0)) {
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&tempty[b]);
+            }
+            adj_col2im_rows<K2>(v, lane, hb, hoff, g, tt * gpt + cg + 4 * gi);
+          }
         } else {
+          ptx::tmem_ld32(tl + (uint32_t)cg * 32, v);
+          ptx::tmem_ld_wait();
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&tempty[b]);
           const int vbase = hoff + (vox & 7);
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
@@ -1398,18 +1410,22 @@ std::mutex g_dev_mu;
 
 typedef void (*AdjKernel)(AdjArgs);
 // compile-time kernel widths of the adjoint col2im (others take the per-element path)
-template <bool DET>
+template <bool DET, bool WIDE>
 AdjKernel adj_kernel_for_t(const TcGeom& g) {
-  if (g.rpg == 0) return adj_tc_kernel<0, DET>;
+  if (g.rpg == 0) return adj_tc_kernel<0, DET, false>;
   switch (g.k2) {
-    case 3: return adj_tc_kernel<3, DET>;
-    case 5: return adj_tc_kernel<5, DET>;
-    case 7: return adj_tc_kernel<7, DET>;
-    case 9: return adj_tc_kernel<9, DET>;
-    default: return adj_tc_kernel<0, DET>;
+    case 3: return adj_tc_kernel<3, DET, WIDE>;
+    case 5: return adj_tc_kernel<5, DET, WIDE>;
+    case 7: return adj_tc_kernel<7, DET, WIDE>;
+    case 9: return adj_tc_kernel<9, DET, WIDE>;
+    default: return adj_tc_kernel<0, DET, false>;
   }
 }
-AdjKernel adj_kernel_for(const TcGeom& g) { return g.det ? adj_kernel_for_t<true>(g) : adj_kernel_for_t<false>(g); }
+AdjKernel adj_kernel_for(const TcGeom& g) {
+  const bool wide = g.gpt == 8;
+  if (g.det) return wide ? adj_kernel_for_t<true, true>(g) : adj_kernel_for_t<true, false>(g);
+  return wide ? adj_kernel_for_t<false, true>(g) : adj_kernel_for_t<false, false>(g);
+}
 
 int dev_sms() {
   std::lock_guard<std::mutex> lk(g_dev_mu);
@@ -1424,9 +1440,13 @@ int dev_sms() {
     cudaFuncSetAttribute(fwd_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     cudaFuncSetAttribute(fwd_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     cudaFuncSetAttribute(fwd_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    for (AdjKernel kf : {adj_tc_kernel<0, true>, adj_tc_kernel<3, true>, adj_tc_kernel<5, true>, adj_tc_kernel<7, true>,
-                         adj_tc_kernel<9, true>, adj_tc_kernel<0, false>, adj_tc_kernel<3, false>,
-                         adj_tc_kernel<5, false>, adj_tc_kernel<7, false>, adj_tc_kernel<9, false>})
+    for (AdjKernel kf : {adj_tc_kernel<0, true, false>, adj_tc_kernel<0, false, false>,
+                         adj_tc_kernel<3, true, false>, adj_tc_kernel<5, true, false>, adj_tc_kernel<7, true, false>,
+                         adj_tc_kernel<9, true, false>, adj_tc_kernel<3, false, false>, adj_tc_kernel<5, false, false>,
+                         adj_tc_kernel<7, false, false>, adj_tc_kernel<9, false, false>, adj_tc_kernel<3, true, true>,
+                         adj_tc_kernel<5, true, true>, adj_tc_kernel<7, true, true>, adj_tc_kernel<9, true, true>,
+                         adj_tc_kernel<3, false, true>, adj_tc_kernel<5, false, true>, adj_tc_kernel<7, false, true>,
+                         adj_tc_kernel<9, false, true>})
       cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     f.ready = true;
   }
