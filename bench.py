@@ -19,7 +19,7 @@ iteration count; "prediction" the video-prediction workload (128x128x32, k = 405
 iterations) as blocking solves.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--requests R]
-    python bench.py --workload prediction|completion|interpolation|batch|image|cnnm
+    python bench.py --workload prediction|completion|interpolation|batch|image|cnnm|fft
 """
 from __future__ import annotations
 
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-learn", action="store_true")
     ap.add_argument("--workload", default="serving",
                     choices=["serving", "prediction", "completion", "interpolation", "batch", "image", "cnnm",
-                             "autotune"],
+                             "autotune", "fft"],
                     help="serving (the default line); the others print their own line")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--latency-requests", type=int, default=400, help="serving: requests of the Poisson run")
@@ -461,6 +461,137 @@ def run_completion(args, local):
                       "fp32_plain": out["fp32"], "note": "fits in L2; launch- and latency-bound"}))
 
 
+def run_fft(args, local):
+    """The frequency-domain solve (icnnm_solve_fft, FP32 complex spectra) on the prediction
+    workload (128x128x32, kernel 9x9x5, frames 24..31 missing, 500 iterations) or, with
+    --dims 256,256,64 --kdims 7,7,5, the interpolation workload (100 iterations): solves/s,
+    the error against the stored FP64 oracle run, per-pass device times, and the HBM
+    roofline of the dominant spectral pass, beside the BF16 tensor-core and plain FP32
+    solves of the same problem."""
+    import ctypes as C
+
+    import torch
+    from paper_2604_17001_gb300 import icnnm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    dims = tuple(int(x) for x in args.dims.split(",")) if args.dims else (128, 128, 32)
+    interp = dims == (256, 256, 64)
+    gpath = os.path.join(ROOT, "tests", "golden",
+                         "interpolation_256x256x64_k7x7x5.npz" if interp else "prediction_128x128x32_k9x9x5.npz")
+    g = np.load(gpath) if os.path.exists(gpath) else None
+    if interp or dims == (128, 128, 32):
+        w = synth.workload(3 if interp else 2, n_ref=0 if g is not None else 4)
+    else:                       # a resized prediction case (profiling): no stored run to compare
+        w = synth.workload(2, dims=dims, n_ref=0 if g is not None else 4)
+    kd = tuple(w["kdims"])
+    stream = torch.cuda.current_stream(dev)
+    ctx = icnnm.Context(local, stream=stream.cuda_stream)
+    V = g["V"] if g is not None else _learn_V_gpu(ctx, w["refs"], kd, dev)
+    it = int(g["iters"]) if g is not None else args.iters
+    if not (interp or dims == (128, 128, 32)):
+        g, it = None, args.iters
+    H, W, T = w["dims"]
+    m, k = H * W * T, int(np.prod(kd))
+    mh = T * H * (W // 2 + 1)
+    Md, Kd = torch.from_numpy(w["M"]).to(dev), torch.from_numpy(w["mask"]).to(dev)
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(dev)
+    Ld = torch.zeros_like(Md)
+    f = lambda: ctx.icnnm_solve_fft(Md, Kd, Vd, kd, L_out=Ld, max_iters=it)
+    for _ in range(args.warmup):
+        f()
+    ctx.lib.icnnm_profile_enable(ctx.h, 0)
+    clocks = Clocks(local)
+    sec = _timed(stream, f, args.steps)
+    clk = clocks.stop()
+    nall = C.c_int64()
+    ctx.lib.icnnm_profile_read(ctx.h, -1, None, C.byref(nall))
+
+    def err(L):
+        if g is None:
+            return None
+        L = L.astype(np.float64)
+        if interp:
+            got = L.reshape(-1)[g["sample_idx"]]
+            return float(np.linalg.norm(got - g["L_sample"]) / np.linalg.norm(g["L_sample"]))
+        Lo = L.copy()
+        Lo[g["frames"]] = g["L_missing"]
+        return float(np.linalg.norm(L - Lo) / np.linalg.norm(Lo))
+
+    e_fft = err(Ld.cpu().numpy())
+    # per-pass device times (CUDA events around every pass)
+    ctx.lib.icnnm_profile_enable(ctx.h, 1)
+    f()
+    torch.cuda.synchronize()
+    prof = {}
+    for p_, name in ((0, "update"), (1, "adjoint"), (2, "gather"), (3, "transforms")):
+        ms, n = C.c_double(), C.c_int64()
+        ctx.lib.icnnm_profile_read(ctx.h, p_, C.byref(ms), C.byref(n))
+        prof[name] = (ms.value, n.value)
+    ctx.lib.icnnm_profile_enable(ctx.h, 0)
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if peaks else "fallback"
+    # algorithmic bytes of one launch over k*mh (frequency, eigenvector) pairs: the update
+    # reads y (complex FP32) and q (FP32) and writes y; the adjoint reads y
+    alg = {"update": 20 * k * mh, "adjoint": 8 * k * mh}
+    dom = max(("update", "adjoint"), key=lambda n_: prof[n_][0])
+    per_ms = prof[dom][0] / max(1, prof[dom][1] if dom == "adjoint" else prof[dom][1] // 2)
+    gbs = alg[dom] / (per_ms * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC):
+        ent = json.load(open(TRAFFIC)).get(f"fft_{dom}")
+        if ent and ent.get("source_hash") == fft_source_hash():
+            traffic = ent.get("bytes_per_launch_per_kmh", 0) * k * mh or None
+    roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
+            "kernel": "fft_spectral_kernel" if dom == "update" else "fft_adjoint_kernel", "peak_source": src,
+            "ms_per_launch": per_ms, "alg_bytes_per_launch": alg[dom],
+            "share_of_step": {n_: prof[n_][0] / sum(v[0] for v in prof.values()) for n_ in prof},
+            "ms_per_pass": {n_: prof[n_][0] for n_ in prof}}
+    # the same problem on the implicit-GEMM paths
+    other = {}
+    for prec in ("bf16", "fp32"):
+        if prec == "fp32" and args.fp32_steps <= 0:
+            continue
+        L2 = torch.zeros_like(Md)
+        f2 = lambda: ctx.icnnm_solve(Md, Kd, Vd, kd, L_out=L2, max_iters=it, prec=prec)
+        f2()
+        n2 = args.steps if prec == "bf16" else args.fp32_steps
+        s2 = _timed(stream, f2, n2)
+        other[prec] = {"solves_per_s": n2 / s2, "ms_per_solve": 1e3 * s2 / n2, "rel_err_vs_oracle": err(L2.cpu().numpy())}
+    # end to end with host buffers
+    Lh = np.zeros_like(w["M"])
+    Vh = np.ascontiguousarray(V)
+    ctx.icnnm_solve_fft(w["M"], w["mask"], Vh, kd, L_out=Lh, max_iters=it)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.icnnm_solve_fft(w["M"], w["mask"], Vh, kd, L_out=Lh, max_iters=it)
+    e2e_s = time.perf_counter() - t0
+    ctx.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        ts = oracle_iteration_seconds(w, V, 1)
+        cpu = {"value": 1.0 / (ts[0] * it), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"1 of {it} ADMM iterations (FP64 numpy, explicit A_k rows) of the same solve, scaled"}
+    name = f"{'interpolation' if interp else 'prediction'}_{H}x{W}x{T}_k{kd[0]}x{kd[1]}x{kd[2]}_fft"
+    print(json.dumps({
+        "metric": "ICNNM solves/s, frequency-domain FP32 path", "value": args.steps / sec, "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (complex spectra)",
+        "data": "synthetic",
+        "config": {"workload": name, "dims_HWT": [H, W, T], "kdims": list(kd), "iters": it,
+                   "l2": f"inputs larger than L2 (the spectral state y, q is {12 * k * mh / 1e9:.2f} GB)"},
+        "rel_err_vs_oracle": e_fft, "roofline": roof, "implicit_gemm": other,
+        "e2e": {"value": args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": m * 5 + k * k * 8,
+                "d2h_bytes_per_step": m * 4},
+        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(nall.value)}))
+
+
+def fft_source_hash():
+    h = hashlib.sha256()
+    h.update(open(os.path.join(ROOT, "paper_2604_17001_gb300", "csrc", "k_fft.cu"), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def run_interpolation(args, local):
     """256x256x64, kernel 7x7x5, every other frame dropped plus 20% of the rest, noise,
     100 iterations: BF16 and FP32 solves/s (and BF16 with lambda = 1000), the BF16 result
@@ -736,6 +867,47 @@ def serving_cpu_baseline(V, budget_s=12.0):
                     f"(32x32x8, k=147), {sec:.3f} s each, scaled per voxel-iteration to the stream"
 
 
+def fp32_sample(ctx, Md, Kd, Ld, Vd, kd, vox, iters, R, S, t32, x32, it32, rng, arr, P):
+    """Plain FP32, one request at a time, on the first S requests; its time per request
+    is modelled as a + b * voxels * iterations (least squares over the sample) for the
+    whole stream, and FCFS latencies follow from that model."""
+    import torch
+    ctx.icnnm_solve(Md[0], Kd[0], Vd, kd, L_out=Ld[0], prec="fp32", **SERVING_KW)
+    for i in range(S):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = ctx.icnnm_solve(Md[i], Kd[i], Vd, kd, L_out=Ld[i], prec="fp32", **SERVING_KW)
+        torch.cuda.synchronize()
+        t32.append(time.perf_counter() - t0)
+        x32.append(vox[i] * st["iters"])
+        it32.append(st["iters"])
+    A = np.stack([np.ones(S), np.array(x32, dtype=np.float64)], axis=1)
+    coef = np.linalg.lstsq(A, np.array(t32), rcond=None)[0]
+    model32 = np.maximum(coef[0] + coef[1] * vox[:R] * np.maximum(iters, 1), 1e-4)
+    cap32 = R / float(model32.sum())
+
+    def fcfs(arrivals, svc):
+        done, out = 0.0, []
+        for a, s_ in zip(arrivals, svc):
+            start = max(a, done)
+            done = start + s_
+            out.append(done - a)
+        return np.array(out) * 1e3
+    fp32 = {"value": cap32, "unit": "solves/s", "measured_requests": S, "measured_s": float(sum(t32)),
+            "measured_solves_per_s": S / float(sum(t32)), "mean_iters_sample": float(np.mean(it32)),
+            "model": "t = a + b * voxels * iterations fitted on the sample, applied to every request with its "
+                     "served iteration count", "a_s": float(coef[0]), "b_s_per_voxel_iter": float(coef[1])}
+    if P > 0:
+        lat32_same = fcfs(arr, model32[:P])
+        arr32 = np.cumsum(rng.exponential(1.0 / (0.8 * cap32), size=P))
+        lat32_own = fcfs(arr32, model32[:P])
+        fp32["latency_ms_same_arrivals"] = {"p50": float(np.percentile(lat32_same, 50)),
+                                            "p99": float(np.percentile(lat32_same, 99))}
+        fp32["latency_ms_at_0.8x_own_capacity"] = {"p50": float(np.percentile(lat32_own, 50)),
+                                                   "p99": float(np.percentile(lat32_own, 99))}
+    return fp32
+
+
 def run_serving_bench(args, ws, rank, local):
     R = args.requests
     reqs = serving_inputs(R)                  # host inputs; no CUDA call before this
@@ -836,16 +1008,17 @@ def run_serving_bench(args, ws, rank, local):
             if dt > 0:
                 time.sleep(dt)
             jid_lat[i] = ctx.icnnm_submit(Md[i], Kd[i], Vd, kd, prec="bf16", **SERVING_KW)
-    th_ = threading.Thread(target=submitter)
-    th_.start()
     lat = []
-    for i in range(P):
-        while jid_lat[i] is None:
-            time.sleep(0.0005)
-        _, st = ctx.icnnm_wait(jid_lat[i], L_out=Ld[i], timeout_ms=-1)
-        lat.append(st["latency"])
-    th_.join()
-    lat_ms = np.array(lat) * 1e3
+    if P > 0:
+        th_ = threading.Thread(target=submitter)
+        th_.start()
+        for i in range(P):
+            while jid_lat[i] is None:
+                time.sleep(0.0005)
+            _, st = ctx.icnnm_wait(jid_lat[i], L_out=Ld[i], timeout_ms=-1)
+            lat.append(st["latency"])
+        th_.join()
+    lat_ms = np.array(lat if lat else [float("nan")]) * 1e3
 
     # roofline of the dominant pass over one profiled wave
     ctx.lib.icnnm_profile_enable(ctx.h, 1)
@@ -897,38 +1070,9 @@ def run_serving_bench(args, ws, rank, local):
     # a + b * voxels * iterations (least squares over the sample) for the whole stream
     S = min(R, args.fp32_requests)
     t32, x32, it32 = [], [], []
-    ctx.icnnm_solve(Md[0], Kd[0], Vd, kd, L_out=Ld[0], prec="fp32", **SERVING_KW)
-    for i in range(S):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, st = ctx.icnnm_solve(Md[i], Kd[i], Vd, kd, L_out=Ld[i], prec="fp32", **SERVING_KW)
-        torch.cuda.synchronize()
-        t32.append(time.perf_counter() - t0)
-        x32.append(vox[i] * st["iters"])
-        it32.append(st["iters"])
-    A = np.stack([np.ones(S), np.array(x32, dtype=np.float64)], axis=1)
-    coef = np.linalg.lstsq(A, np.array(t32), rcond=None)[0]
-    model32 = np.maximum(coef[0] + coef[1] * vox[:R] * np.maximum(iters, 1), 1e-4)
-    cap32 = R / float(model32.sum())
-
-    def fcfs(arrivals, svc):
-        done, out = 0.0, []
-        for a, s_ in zip(arrivals, svc):
-            start = max(a, done)
-            done = start + s_
-            out.append(done - a)
-        return np.array(out) * 1e3
-    lat32_same = fcfs(arr, model32[:P])
-    arr32 = np.cumsum(rng.exponential(1.0 / (0.8 * cap32), size=P))
-    lat32_own = fcfs(arr32, model32[:P])
-    fp32 = {"value": cap32, "unit": "solves/s", "measured_requests": S, "measured_s": float(sum(t32)),
-            "measured_solves_per_s": S / float(sum(t32)), "mean_iters_sample": float(np.mean(it32)),
-            "model": "t = a + b * voxels * iterations fitted on the sample, applied to every request with its "
-                     "served iteration count", "a_s": float(coef[0]), "b_s_per_voxel_iter": float(coef[1]),
-            "latency_ms_same_arrivals": {"p50": float(np.percentile(lat32_same, 50)),
-                                         "p99": float(np.percentile(lat32_same, 99))},
-            "latency_ms_at_0.8x_own_capacity": {"p50": float(np.percentile(lat32_own, 50)),
-                                                "p99": float(np.percentile(lat32_own, 99))}}
+    fp32 = None
+    if S > 0:
+        fp32 = fp32_sample(ctx, Md, Kd, Ld, Vd, kd, vox, iters, R, S, t32, x32, it32, rng, arr, P)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1028,6 +1172,8 @@ def main():
         run_image(args, local)
     elif args.workload == "cnnm":
         run_cnnm(args, local)
+    elif args.workload == "fft":
+        run_fft(args, local)
     elif args.workload == "autotune":
         run_autotune(args, local)
     else:

@@ -190,6 +190,29 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* ctx, const icnnm_shape* shape, const fl
                               icnnm_stats* stats);
 
 /*
+ * Solve one completion problem as icnnm_solve does (Sec. III-D, the same ADMM iteration,
+ * initial state and stopping rule), computing in the frequency domain. The convolution
+ * of Sec. II-B is circular, so A_k(X)V has the 3-D DFT X^ kappa_c^ in column c (kappa_c:
+ * eigenvector c laid out as a k1 x k2 x k3 kernel), A_k^*(U D V^T) has the DFT
+ * sum_c D_c U_c^ conj(kappa_c^), and column norms follow from Parseval. Each U_c^ stays a
+ * multiple of kappa_c^, so the state is y_c = U_c^ conj(kappa_c^) (FP32 complex) and
+ * q_c = |kappa_c^|^2 (FP32) over the H*T*(W/2+1) frequencies of a real transform; an
+ * iteration streams y once and y and q once more (about 14*k*m bytes) and transforms one
+ * tensor each way, in place of the two m x k x k products.
+ *   shape, M, mask, V, L_out : as for icnnm_solve
+ *   params : as for icnnm_solve; prec is ignored (the spectra are FP32 complex, the
+ *            norms FP64)
+ *   stats  : as for icnnm_solve; seconds = device time of the solve including the
+ *            transforms of the k kernels
+ * EINVAL as for icnnm_solve. EUNSUPPORTED unless H, W, T are powers of two with
+ * 2 <= W <= 1024, H <= 1024, T <= 1024 and H*T >= 2. ENOMEM if the state (12 bytes per
+ * frequency and eigenvector, k*H*T*(W/2+1) of them, plus O(16 m)) exceeds the budget.
+ */
+icnnm_status icnnm_solve_fft(icnnm_ctx* ctx, const icnnm_shape* shape, const float* M,
+                             const uint8_t* mask, const double* V, const icnnm_params* params,
+                             float* L_out, icnnm_stats* stats);
+
+/*
  * Relative convolution diagnostics of a tensor L0 with respect to V (Sec. III-A,
  * Definition 2, Eqs. rkL0 and alphaK; the coherence of Eq. coherence):
  *   sigma_i = ||L0 * kappa_i||_F = ||A_k(L0) v_i||_2   (relative convolution eigenvalues)

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libicnnm.so")
-SOURCES = ["api.cu", "k_cnnm.cu", "k_common.cu", "k_fp32.cu", "k_learn.cu", "k_tc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "k_cnnm.cu", "k_common.cu", "k_fft.cu", "k_fp32.cu", "k_learn.cu", "k_tc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr", "-Xptxas", "-v"]

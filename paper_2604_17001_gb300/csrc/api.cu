@@ -167,6 +167,7 @@ struct icnnm_ctx {
   double pass_ms[4] = {0, 0, 0, 0};
   long long pass_n[5] = {0, 0, 0, 0, 0};
   long long pass_vox[5] = {0, 0, 0, 0, 0};
+  size_t hook_idx = 0;                           // start event of the open hook pass
   // engine scratch
   // device job tables: slot 0 for the main list, slot 1 for a list stepped beside it
   // (the BF16 jobs finishing in FP32), so that both can be live at once. Uploads are
@@ -1493,6 +1494,102 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* c, const icnnm_shape* shape, const floa
     return report(c, f);
   } catch (CudaFail& f) {
     for (void* q : tmp) cudaFree(q);
+    return report(c, f);
+  }
+}
+
+// PassHook callbacks on a context: the same counters and events as PassScope, without
+// throwing (a failed event record only loses that pass's time).
+static void fft_hook_begin(void* u, int pass, int nk, long long nvox) {
+  icnnm_ctx* c = (icnnm_ctx*)u;
+  c->pass_n[pass] += nk;
+  c->pass_n[4] += nk;
+  c->pass_vox[pass] += nvox;
+  c->pass_vox[4] += nvox;
+  if (c->prof) {
+    try {
+      c->hook_idx = c->evnext;
+      cudaEventRecord(pool_event(c), c->stream);
+    } catch (...) {
+      c->hook_idx = (size_t)-1;
+    }
+  }
+}
+static void fft_hook_end(void* u, int pass) {
+  icnnm_ctx* c = (icnnm_ctx*)u;
+  if (c->prof && c->hook_idx != (size_t)-1) {
+    try {
+      cudaEventRecord(pool_event(c), c->stream);
+      c->pending.emplace_back(pass, c->hook_idx);
+    } catch (...) {
+    }
+  }
+}
+
+icnnm_status icnnm_solve_fft(icnnm_ctx* c, const icnnm_shape* shape, const float* M, const uint8_t* mask,
+                             const double* V, const icnnm_params* params, float* L_out, icnnm_stats* stats) {
+  if (!c) return ICNNM_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  std::vector<void*> tmp;
+  auto release = [&] {
+    for (void* q : tmp) cudaFree(q);
+    tmp.clear();
+  };
+  try {
+    CK(cudaSetDevice(c->device));
+    int H, W, T, k1, k2, k3;
+    validate_shape(shape, H, W, T, k1, k2, k3);
+    const icnnm_params p = params ? *params : defaults();
+    validate_params(p);
+    if (!M || !mask || !L_out) fail(ICNNM_EINVAL, "M, mask and L_out must not be NULL");
+    std::string why;
+    if (!fft_supported(H, W, T, &why)) fail(ICNNM_EUNSUPPORTED, why);
+    VData* vd = get_vdata(c, V, k1, k2, k3, ICNNM_FP32);       // validates V (orthonormal, finite)
+    const long long m = (long long)H * W * T;
+    if (fft_state_bytes(H, W, T, vd->k) + (size_t)m * 9 + c->used > c->budget)
+      fail(ICNNM_ENOMEM, "the spectra of U and of the kernels exceed the HBM budget");
+    auto dalloc = [&](size_t bytes) {
+      void* q;
+      CK(cudaMalloc(&q, bytes));
+      tmp.push_back(q);
+      return q;
+    };
+    float* dM = (float*)dalloc(m * 4);
+    uint8_t* dK = (uint8_t*)dalloc(m);
+    float* dL = (float*)dalloc(m * 4);
+    CK(cudaMemcpyAsync(dM, M, m * 4, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(dK, mask, m, cudaMemcpyDefault, c->stream));
+    int* d2 = (int*)dalloc(8);
+    CK(cudaMemsetAsync(d2, 0, 8, c->stream));
+    CK(check_observed(dM, dK, m, d2, c->stream));
+    int h2[2];
+    CK(cudaMemcpyAsync(h2, d2, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h2[1]) fail(ICNNM_EINVAL, "mask entries must be 0/1 and M must be finite on Omega");
+    if (h2[0] == 0) fail(ICNNM_EINVAL, "Omega is empty");
+    FftProblem P{c->device, H, W, T, k1, k2, k3, dM, dK, dL, vd->dV64, p.max_iters, p.check_every,
+                 p.theta0, p.rho, p.theta_max, p.lambda, p.tol, PassHook{c, fft_hook_begin, fft_hook_end}};
+    FftResult r{};
+    const cudaError_t fe = fft_run(P, c->stream, &r);
+    flush_prof(c);
+    CK(fe);
+    CK(cudaMemcpyAsync(L_out, dL, m * 4, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (stats) {
+      stats->iters = r.iters;
+      stats->residual = r.residual;
+      stats->objective = r.objective;
+      stats->theta = r.theta;
+      stats->seconds = r.seconds;
+      stats->latency = r.seconds;
+    }
+    release();
+    return ICNNM_OK;
+  } catch (StatusFail& f) {
+    release();
+    return report(c, f);
+  } catch (CudaFail& f) {
+    release();
     return report(c, f);
   }
 }

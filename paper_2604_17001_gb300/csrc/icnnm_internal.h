@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace icnnm {
 
 // Voxel tile of the forward/adjoint passes: TW (w) x TH (h) x 1 (t) = 128 voxels.
@@ -208,6 +210,34 @@ struct CnnmResult {
   int timed_out;
   int unconverged;   // the eigensolver hit its sweep cap unconverged in some iteration
 };
+// Pass bracketing for diagnostics: begin(user, pass, kernels, voxels) before the kernels
+// of a pass are enqueued, end(user, pass) after. Neither may throw.
+struct PassHook {
+  void* user = nullptr;
+  void (*begin)(void* user, int pass, int nkernels, long long nvox) = nullptr;
+  void (*end)(void* user, int pass) = nullptr;
+};
+
+// Frequency-domain ICNNM (power-of-two dims; FP32 complex spectra of U and kappa).
+// Passes for the hook: 0 = the spectral U update (U' = U D - X^ kappa^), 1 = the spectral
+// adjoint sum, 2 = the L-update, 3 = transforms and everything else.
+struct FftProblem {
+  int device, H, W, T, k1, k2, k3;
+  const float* dM;          // device, m
+  const uint8_t* dmask;     // device, m
+  float* dL;                // device output, m (also the iterate)
+  const double* dV;         // device, k*k, eigenvector c at dV[c*k ...]
+  int max_iters, check_every;
+  double theta0, rho, theta_max, lambda, tol;
+  PassHook hook;
+};
+struct FftResult {
+  int iters;
+  double residual, objective, theta, seconds;
+};
+bool fft_supported(int H, int W, int T, std::string* why);
+size_t fft_state_bytes(int H, int W, int T, int k);
+cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res);
 size_t cnnm_state_bytes(int H, int W, int T, int k1, int k2, int k3);
 cudaError_t cnnm_run(const CnnmProblem& P, cudaStream_t st, CnnmResult* res);
 cudaError_t learn_gram_streamed(int b, const float* const* dptrs, const int* ddims, int k1, int k2, int k3,

@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
         "icnnm_check_bounded_wait": ([P, I64], I32),
         "icnnm_cnnm_solve": ([P, C.POINTER(icnnm_shape), P, P, C.POINTER(icnnm_params), P,
                               C.POINTER(icnnm_stats)], I32),
+        "icnnm_solve_fft": ([P, C.POINTER(icnnm_shape), P, P, P, C.POINTER(icnnm_params), P,
+                             C.POINTER(icnnm_stats)], I32),
         "icnnm_spectral_diagnostics": ([P, C.POINTER(icnnm_shape), P, P, D, P, C.POINTER(I32), C.POINTER(D),
                                         C.POINTER(D)], I32),
         "icnnm_learn_V_noalloc": ([C.POINTER(I64), I32, C.POINTER(icnnm_shape), C.POINTER(P), P, P, P], I32),
@@ -288,6 +290,22 @@ class Context:
         st = icnnm_stats()
         self._check(self.lib.icnnm_solve(self.h, C.byref(s), _ptr(M), _ptr(mask), _ptr(Vc), C.byref(p),
                                          _ptr(L_out), C.byref(st)))
+        return L_out, st.as_dict()
+
+    def icnnm_solve_fft(self, M, mask, V, kdims, dims=None, L_out=None, **kw):
+        """As icnnm_solve, computed in the frequency domain (power-of-two dims; FP32
+        complex spectra whatever ``prec`` says). Returns (L, stats dict)."""
+        shp = tuple(M.shape)
+        if dims is None:
+            dims = (shp[1], shp[2], shp[0]) if len(shp) == 3 else (shp[0], shp[1])
+        s = make_shape(dims, kdims)
+        p = params(**kw)
+        Vc = self._v_colmajor(V)
+        if L_out is None:
+            L_out = np.zeros(shp, dtype=np.float32) if isinstance(M, np.ndarray) else M.new_zeros(shp)
+        st = icnnm_stats()
+        self._check(self.lib.icnnm_solve_fft(self.h, C.byref(s), _ptr(M), _ptr(mask), _ptr(Vc), C.byref(p),
+                                             _ptr(L_out), C.byref(st)))
         return L_out, st.as_dict()
 
     def icnnm_solve_batch(self, Ms, masks, V, kdims, L_outs=None, **kw):
