@@ -540,6 +540,11 @@ bool switch_to_finish(icnnm_ctx* c, Job& j) {
   c->used += need;
   j.block2 = b;
   j.bytes2 = need;
+  // the finishing kernel writes its residual partials into its own slots of rpart, which
+  // need not be the slots the BF16 kernel wrote: clear them all so that no stale BF16
+  // partial is summed into a later residual
+  const int nrp = std::max(fwd_fp32_nrp((int)k), tc_nrp((int)k));
+  CK(cudaMemsetAsync(j.dev.rpart, 0, (size_t)j.dev.ntiles * nrp * 4, c->stream));
   if (split) {
     CK(cudaMemsetAsync(b, 0, m * kc * 2, c->stream));
     icnnm_ctx::Pinned& e = pinned_take(c, tc_tmap_bytes());

@@ -212,6 +212,18 @@ struct FwdArgs {
   int mode;
 };
 
+// TMA store of one tile's U' (hi, and lo for the split form) from a U stage.
+template <int NIMG>
+__device__ __forceinline__ void fwd_store_u(const Shared& sh, uint8_t* stage, size_t uhalf, int jb, int tile, int c0,
+                                            int nbox) {
+  const JobDev& J = sh.jobs[jb];
+  const int tw = tile % J.ntw, th = (tile / J.ntw) % J.nth, t = tile / (J.ntw * J.nth);
+  for (int half = 0; half < NIMG; ++half)
+    for (int bx = 0; bx < nbox; ++bx)
+      ptx::tma_store_4d(half ? J.tmapUlo : J.tmapU, stage + (size_t)half * uhalf + (size_t)bx * CHUNK, c0 + bx * 64,
+                        tw * TW, th * TH, t);
+}
+
 struct AdjArgs {
   Shared sh;
   TcGeom g;
@@ -228,6 +240,24 @@ __device__ __forceinline__ void set_fail(const Shared& sh) {
 // Sum a[j] (j = 0..31) over the 32 lanes of the warp in a fixed order and store the sum
 // for j = lane at dst[lane] (if `ok`): a transpose-reduce in five halving steps, after
 // which lane l holds the total of value l.
+// n (8, 16, 24 or 32; warp-uniform) consecutive accumulator columns from TMEM into e[0..n).
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&e)[32], int n) {
+  if (n == 32) {
+    ptx::tmem_ld32(taddr, e);
+  } else if (n == 8) {
+    ptx::tmem_ld8(taddr, *reinterpret_cast<float(*)[8]>(&e[0]));
+  } else {
+    ptx::tmem_ld16(taddr, *reinterpret_cast<float(*)[16]>(&e[0]));
+    if (n == 24) ptx::tmem_ld8(taddr + 16, *reinterpret_cast<float(*)[8]>(&e[16]));
+  }
+}
+
+// Address of 8-channel unit cu (channel 8 cu of the tile) in a voxel's row of a U stage:
+// 64-channel SW128 boxes of CHUNK bytes, the unit's 16 bytes XOR-swizzled by the row phase.
+__device__ __forceinline__ uint8_t* uunit(uint8_t* rowb, int cu, uint32_t usw) {
+  return rowb + (size_t)(cu >> 3) * CHUNK + ((((uint32_t)cu & 7u) ^ usw) << 4);
+}
+
 __device__ __forceinline__ void warp_colsum_store(float (&a)[32], int lane, float* dst, bool ok) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -333,8 +363,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   uint64_t* tfull = bars + 4;              // [2] accumulator ready
   uint64_t* tempty = bars + 6;             // [2] accumulator read out
   uint64_t* ufull = bars + 8;              // [nus] U tile landed
-  uint64_t* uempty = bars + 8 + nus;       // [nus] U stage free again
-  uint64_t* abar = bars + 8 + 2 * nus;
+  uint64_t* uempty = bars + 8 + nus;       // [nus] U stage free again (mode 2: the epilogue may write it)
+  uint64_t* sready = bars + 8 + 2 * nus;   // [nus] the epilogue is done with the stage (U' written)
+  uint64_t* abar = bars + 8 + 3 * nus;
   uint64_t* dbar = abar + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(dbar + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
@@ -356,6 +387,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     for (int i = 0; i < nus; ++i) {
       ptx::mbar_init(&ufull[i], 1);
       ptx::mbar_init(&uempty[i], 1);
+      ptx::mbar_init(&sready[i], EPI_WARPS);
     }
     ptx::mbar_init(abar, 1);
     ptx::mbar_init(dbar, 1);
@@ -391,6 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
           ptx::bulk_g2s(sA + ((size_t)im * g.nch_f + c) * chunkF, src + (size_t)c * chunkF, (uint32_t)chunkF, abar);
       }
       const uint32_t hbytes = (uint32_t)(NIMG * g.k2 * g.region_bytes);
+      int rjb[FWD_USTAGES] = {0}, rtile[FWD_USTAGES] = {0};   // job and tile held by each U stage
       int it = 0;
       TileSeq sq(sh, slot, nslot, g.det);
       for (; sq.next(); ++it) {
@@ -409,17 +442,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
             ptx::tma_load_4d(sH + (size_t)s * stage_bytes + (size_t)half * g.lo_off + (size_t)q * g.ncopy * g.region_bytes,
                              (q > 0) ? J.tmapX2 : J.tmapX, t * 8, th * TH, tw + (g.nwc - 1) - q, half * g.ncopy,
                              &full[s]);
-        if (rdU) {
+        {
+          // U stage us: once the epilogue is done with tile it - nus there, store that tile's
+          // U' (this thread issues every store, so that no epilogue warp waits for one) and
+          // wait until the store has read the stage; then load tile it's U into it (modes 1
+          // and 3) or hand it to the epilogue (mode 2)
           const int us = it % nus;
-          const uint32_t uph = (it / nus) & 1;
-          if (!ptx::mbar_wait_abortable(&uempty[us], uph ^ 1, abort)) { failed = true; ++it; break; }
-          ptx::mbar_arrive_expect_tx(&ufull[us], (uint32_t)(NIMG * nbox * CHUNK));
-          for (int half = 0; half < NIMG; ++half)
-            for (int bx = 0; bx < nbox; ++bx)
-              ptx::tma_load_4d(sU + (size_t)us * ustage + (size_t)half * uhalf + (size_t)bx * CHUNK,
-                               half ? J.tmapUlo : J.tmapU, ct * ctw + bx * 64, tw * TW, th * TH, t, &ufull[us]);
+          if (it >= nus) {
+            if (!ptx::mbar_wait_abortable(&sready[us], ((it - nus) / nus) & 1, abort)) { failed = true; ++it; break; }
+            if (wrU) {
+              fwd_store_u<NIMG>(sh, sU + (size_t)us * ustage, uhalf, rjb[us], rtile[us], ct * ctw, nbox);
+              ptx::bulk_commit_group();
+              ptx::bulk_wait_group_read0();
+            }
+          }
+          rjb[us] = sq.jb;
+          rtile[us] = tile;
+          if (rdU) {
+            ptx::mbar_arrive_expect_tx(&ufull[us], (uint32_t)(NIMG * nbox * CHUNK));
+            for (int half = 0; half < NIMG; ++half)
+              for (int bx = 0; bx < nbox; ++bx)
+                ptx::tma_load_4d(sU + (size_t)us * ustage + (size_t)half * uhalf + (size_t)bx * CHUNK,
+                                 half ? J.tmapUlo : J.tmapU, ct * ctw + bx * 64, tw * TW, th * TH, t, &ufull[us]);
+          } else if (it >= nus) {
+            ptx::mbar_arrive(&uempty[us]);
+          }
         }
       }
+      // the U' of the last tiles, once the epilogue is done with them
+      if (!failed)
+        for (int i = (it > nus ? it - nus : 0); i < it; ++i) {
+          const int us = i % nus;
+          if (!ptx::mbar_wait_abortable(&sready[us], (i / nus) & 1, abort)) { failed = true; break; }
+          if (wrU) {
+            fwd_store_u<NIMG>(sh, sU + (size_t)us * ustage, uhalf, rjb[us], rtile[us], ct * ctw, nbox);
+            ptx::bulk_commit_group();
+          }
+        }
+      if (wrU) ptx::bulk_wait_group0();   // every U' store is complete before the CTA exits
       // every issued load has landed before the CTA can exit
       for (int i = (it > 2 ? it - 2 : 0); i < it; ++i)
         if (!ptx::mbar_wait(&full[i & 1], (i >> 1) & 1)) failed = true;
@@ -491,22 +551,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     }
   } else {
     // Epilogue: 16 warps. Warp w reads TMEM lanes 32q..32q+31 (q = w % 4), i.e. voxels
-    // 32q + lane of the tile, and column groups cg = (w - 2) / 4 and, in a channel tile
-    // wider than 128, cg + 4 (32 channels each). U of the tile sits in a shared-memory
+    // 32q + lane of the tile. Task 0 of the warp is column group jq = (w - 2) / 4 (32
+    // channels); in a channel tile wider than 128, task 1 is the warp's equal share of the
+    // channels past 128 (E = (ctw - 128) / 4 of them, a multiple of 8), so that the four
+    // warps of a voxel quarter carry the same load. U of the tile sits in a shared-memory
     // stage (SW128 boxes of 64 channels, row = voxel), loaded by TMA ahead of time; U' is
     // written back into the stage and stored by TMA. Column sums of U'^2 stay, per voxel
-    // lane and channel, in registers (first group) or in a shared-memory slot of the warp
-    // (second group) across all tiles of a job that this CTA processes, and are reduced
-    // over the warp once per job into one partial row per (CTA, voxel quarter).
+    // lane and channel, in registers (task 0) or in a shared-memory slot of the warp
+    // (task 1) across the tiles of a chunk, and are reduced over the warp once per chunk
+    // into its partial row group.
     // A failed wait marks the thread failed; it still passes every named barrier (the
     // other warps may be waiting there) but does no more waiting.
     const int q = warp & 3;
     const int ew = warp - 2;
-    const int cgs[2] = {ew >> 2, (ew >> 2) + 4};
-    const int ntask = (WIDE && cgs[1] < ng) ? 2 : 1;
+    const int jq = ew >> 2;
+    const int E = WIDE ? (ctw - 128) / 4 : 0;
+    // first channel (in the tile) and width of task ti
+#define TCS(ti) ((ti) == 0 ? 32 * jq : 128 + E * jq)
+#define TCW(ti) ((ti) == 0 ? 32 : E)
+    const int ntask = E > 0 ? 2 : 1;
     const int vox = q * 32 + lane;
     const uint32_t usw = (uint32_t)(lane & 7);                  // SW128 row phase (vox % 8)
-    float* acc2 = sAcc2 + (size_t)((cgs[1] - 4) * 4 + q) * 32 * 32;   // second group's sums [j][lane]
+    float* acc2 = sAcc2 + (size_t)ew * E * 32;                 // task 1's sums [j < E][lane]
     float acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
@@ -522,12 +588,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
           // flush the previous chunk's column sums into its row group
           const JobDev& P = sh.jobs[cur];
           for (int ti = 0; ti < ntask; ++ti) {
-            const int c0 = ct * ctw + cgs[ti] * 32;
+            const int c0 = ct * ctw + TCS(ti);
             if (ti == 1) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) { acc[j] = acc2[j * 32 + lane]; acc2[j * 32 + lane] = 0.f; }
+              for (int j = 0; j < 32; ++j) {
+                acc[j] = j < E ? acc2[j * 32 + lane] : 0.f;
+                if (j < E) acc2[j * 32 + lane] = 0.f;
+              }
             }
-            warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+            warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0,
+                              c0 + lane < sh.kc && lane < TCW(ti));
 #pragma unroll
             for (int j = 0; j < 32; ++j) acc[j] = 0.f;
           }
@@ -539,8 +609,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
           const float* src = mode == 1 ? J.D : J.s;
           const float sc = mode == 1 ? 1.f : (float)(1.0 / J.sc->theta);
           for (int ti = 0; ti < ntask; ++ti) {
-            const int c0 = ct * ctw + cgs[ti] * 32;
-            sD[ew * sdw + ti * 32 + lane] = (c0 + lane < sh.kc) ? src[c0 + lane] * sc : 0.f;
+            const int c0 = ct * ctw + TCS(ti);
+            sD[ew * sdw + ti * 32 + lane] = (c0 + lane < sh.kc && lane < TCW(ti)) ? src[c0 + lane] * sc : 0.f;
           }
           __syncwarp();
         }
@@ -563,27 +633,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
       float rsum = 0.f;
 #pragma unroll 1
       for (int ti = 0; ti < ntask; ++ti) {
-        ptx::tmem_ld32(tl + (uint32_t)cgs[ti] * 32, e);
+        tmem_ld_cols(tl + (uint32_t)TCS(ti), e, TCW(ti));
         ptx::tmem_ld_wait();
         if (ti == ntask - 1) {
           ptx::tc_fence_before();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&tempty[b]);     // the accumulator is in registers
         }
-        const int cg = cgs[ti];
-        const int c0 = ct * ctw + cg * 32;                        // first channel of this group
-        const int nun = max(0, min(4, (sh.kc - c0) / 8));         // 8-channel units inside kc
+        const int c0 = ct * ctw + TCS(ti);                        // first channel of this task
+        const int nun = max(0, min(TCW(ti) / 8, (sh.kc - c0) / 8));   // 8-channel units inside kc
         const float* sDw = sD + ew * sdw + ti * 32;
-        uint8_t* urow = sU + (size_t)us * ustage + (size_t)(cg >> 1) * CHUNK + (size_t)vox * 128;
-        uint8_t* urow_lo = urow + uhalf;                          // SPLIT: the lo tile
-        const uint32_t u0 = (uint32_t)(cg & 1) * 4;
+        uint8_t* rowb = sU + (size_t)us * ustage + (size_t)vox * 128;   // this voxel's row of the stage
+        const int cu0 = TCS(ti) >> 3;                             // first 8-channel unit of the task
         if (mode == 3) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             if (u < nun) {
-              const uint4 x = *reinterpret_cast<const uint4*>(urow + (((u0 + u) ^ usw) << 4));
+              const uint4 x = *reinterpret_cast<const uint4*>(uunit(rowb, cu0 + u, usw));
               uint4 xl = make_uint4(0u, 0u, 0u, 0u);
-              if (SPLIT) xl = *reinterpret_cast<const uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
+              if (SPLIT) xl = *reinterpret_cast<const uint4*>(uunit(rowb, cu0 + u, usw) + uhalf);
               const float4 d0 = *reinterpret_cast<const float4*>(sDw + 8 * u);
               const float4 d1 = *reinterpret_cast<const float4*>(sDw + 8 * u + 4);
               const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
@@ -602,8 +670,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             if (u < nun) {
-              uint4* p = reinterpret_cast<uint4*>(urow + (((u0 + u) ^ usw) << 4));
-              uint4* pl = reinterpret_cast<uint4*>(urow_lo + (((u0 + u) ^ usw) << 4));
+              uint4* p = reinterpret_cast<uint4*>(uunit(rowb, cu0 + u, usw));
+              uint4* pl = reinterpret_cast<uint4*>(uunit(rowb, cu0 + u, usw) + uhalf);
               float dv[8];
               uint32_t xw[4] = {0u, 0u, 0u, 0u}, xlw[4] = {0u, 0u, 0u, 0u};
               if (mode == 1) {
@@ -660,36 +728,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
           float r = valid ? rsum : 0.f;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-          if (lane == 0) J.rpart[(size_t)tile * sh.nrp + (ct * ng + cg) * 4 + q] = r;
+          if (lane == 0) J.rpart[(size_t)tile * sh.nrp + (ct * 8 + (ti == 0 ? jq : 4 + jq)) * 4 + q] = r;
           rsum = 0.f;
         }
       }
-      if (mode != 3) ptx::fence_proxy_async_smem();    // U' in shared memory -> the TMA store
-      ptx::named_bar_sync(1, 32 * EPI_WARPS);
-      if (ew == 0 && lane == 0) {
-        if (wrU) {
-          for (int half = 0; half < NIMG; ++half)
-            for (int bx = 0; bx < nbox; ++bx)
-              ptx::tma_store_4d(half ? J.tmapUlo : J.tmapU, sU + (size_t)us * ustage + (size_t)half * uhalf +
-                                (size_t)bx * CHUNK, ct * ctw + bx * 64, tw * TW, th * TH, t);
-          ptx::bulk_commit_group();
-          ptx::bulk_wait_group_read0();   // the stage may be refilled once the store has read it
-        }
-        ptx::mbar_arrive(&uempty[us]);
-      }
+      // done with the stage: the producer thread stores U' from it (the writes are made
+      // visible to the async proxy first) and refills it
+      if (wrU) ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&sready[us]);
     }
     if (cur >= 0 && wrU) {
       const JobDev& P = sh.jobs[cur];
       for (int ti = 0; ti < ntask; ++ti) {
-        const int c0 = ct * ctw + cgs[ti] * 32;
+        const int c0 = ct * ctw + TCS(ti);
         if (ti == 1) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) { acc[j] = acc2[j * 32 + lane]; acc2[j * 32 + lane] = 0.f; }
+          for (int j = 0; j < 32; ++j) {
+            acc[j] = j < E ? acc2[j * 32 + lane] : 0.f;
+            if (j < E) acc2[j * 32 + lane] = 0.f;
+          }
         }
-        warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0, c0 + lane < sh.kc);
+        warp_colsum_store(acc, lane, P.part + ((size_t)row0 * PROW + q) * sh.kc + c0,
+                          c0 + lane < sh.kc && lane < TCW(ti));
       }
     }
-    if (ew == 0 && lane == 0 && wrU) ptx::bulk_wait_group0();   // U' stores complete
   }
   if (failed) set_fail(sh);
   ptx::tc_fence_before();
@@ -699,6 +762,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     ptx::tmem_dealloc(tbase, tcols);
   }
 }
+
+#undef TCS
+#undef TCW
 
 // ---------------------------------------------------------------------------------
 // Adjoint pass
@@ -1271,11 +1337,11 @@ void tc_free_vdata(TcVData* v) {
   v->VtImgS = nullptr;
 }
 
-// residual partials per tile: 4 per 32-channel group of every channel tile (an upper bound
-// for both channel-tile widths)
+// residual partials per tile: 8 task slots (4 column groups and 4 shares of the channels
+// past 128) x 4 voxel quarters per channel tile (an upper bound for every channel-tile width)
 int tc_nrp(int k) {
   const int kc = (k + 15) / 16 * 16;
-  return std::max(16 * ((k + 127) / 128), 4 * ((kc + 31) / 32));
+  return std::max(32 * ((k + 127) / 128), 4 * ((kc + 31) / 32));
 }
 
 static void xc_dims(const TcGeom& g, int H, int W, int T, int& Tp, int& Hp, int& Wp) {

@@ -68,14 +68,18 @@ def test_budget_gated_admission_waits_for_memory(V):
         one = c0.icnnm_job_bytes((48, 40, 12), KD, "fp32")
     with icnnm.Context(0, hbm_budget_bytes=int(1.5 * one)) as ctx:
         ids = [ctx.icnnm_submit(M, mask, V, KD, prec="fp32", max_iters=300) for M, mask in probs]
-        sts = []
+        sts, Ls_served = [], []
         for (M, mask), jid in zip(probs, ids):
             L = np.zeros_like(M)
             r, st = ctx.icnnm_wait(jid, L_out=L, timeout_ms=120000)
             assert r == icnnm.OK
+            Ls_served.append(L)
+            sts.append(st)
+        # blocking solves only once both served jobs are done: a blocking solve needs its own
+        # share of the budget, which a running served job would still hold
+        for (M, mask), L in zip(probs, Ls_served):
             Ls, _ = ctx.icnnm_solve(M, mask, V, KD, prec="fp32", max_iters=300)
             assert np.array_equal(L, Ls)
-            sts.append(st)
         queued = sts[1]["latency"] - sts[1]["seconds"]          # time the second job waited
         assert queued >= 0.5 * sts[0]["seconds"], (queued, sts)
 
