@@ -119,6 +119,9 @@ TcGeom make_geom(int k1, int k2, int k3, int gpt_max, int ctw_max = 256, int nus
   }
   g.nta = 32 * g.gpt;
   g.ntt = g.rpg ? ((k1 * k3 + g.rpg - 1) / g.rpg + g.gpt - 1) / g.gpt : (g.k + 127) / 128;
+  // spread the tap rows evenly over the ntt * gpt groups (fewer rows per group where they
+  // do not fill them): every epilogue warp and every tap tile then adds about as many rows
+  if (g.rpg) g.rpg = std::min(g.rpg, (k1 * k3 + g.ntt * g.gpt - 1) / (g.ntt * g.gpt));
   // frames (st) each tap tile's taps reach: its col2im partial keeps only those nsl
   // frames of the halo, starting at frame slo[tt]
   g.nsl = 1;
@@ -770,7 +773,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
 // Adjoint pass
 // ---------------------------------------------------------------------------------
 // Tap columns of the adjoint: column j of tap tile tt belongs to 32-column group
-// G = gpt tt + j / 32, which holds rpg = floor(32 / k2) whole tap rows (st, sh) of k2 taps
+// G = gpt tt + j / 32, which holds rpg <= floor(32 / k2) whole tap rows (st, sh) of k2 taps
 // each (row TR = G rpg + r, r = (j % 32) / k2, sw = (j % 32) % k2, TR = st k1 + sh);
 // the remaining 32 - rpg k2 columns of a group and the rows past k1 k3 are padding.
 // Returns the tap s = TR k2 + sw of a column, or -1 for padding.
@@ -803,12 +806,13 @@ __device__ __forceinline__ int adj_rowoff(const TcGeom& g, int TR) {
 template <int K2, typename HT>
 __device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, HT* hb, int hoff,
                                                 const TcGeom& g, int G) {
-  constexpr int RPG = 32 / K2;
+  constexpr int RPG = 32 / K2;            // tap rows a group can hold; it holds g.rpg <= RPG
   constexpr int NJ = (K2 + 14) / 8;      // halo columns 0 .. K2 + 6 over 8 lanes
   const int w = lane & 7;
 #pragma unroll
   for (int r = 0; r < RPG; ++r) {
-    const int TR = G * RPG + r;
+    if (r >= g.rpg) break;                 // warp-uniform: the group's unused rows
+    const int TR = G * g.rpg + r;
     if (TR >= g.k1 * g.k3) break;          // warp-uniform: padding rows
     const int base = hoff + adj_rowoff(g, TR);
 #pragma unroll

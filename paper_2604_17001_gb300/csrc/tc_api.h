@@ -31,7 +31,8 @@ struct TcGeom {
   int Hb, Wb, HB;   // col2im halo of a tile: Hb = TH + k1 - 1, Wb = TW + k2 - 1, HB = Hb*Wb*nsl
   int nsl;          // frames of the halo one tap tile reaches (its partial keeps only those)
   int slo[16];      // first frame (st) reached by each tap tile
-  int rpg;          // adjoint: whole tap rows (k2 taps) per 32-column group (0: taps in order)
+  int rpg;          // adjoint: whole tap rows (k2 taps) per 32-column group, spread evenly over
+                    // the groups (0: taps in order)
   int nus;          // forward U tile stages in shared memory (1 or 2)
   // split forward (ICNNM_BF16X3 and the finish of BF16 jobs): the operand and V^T as
   // hi + lo BF16 pairs, three products per tile, U stored as a hi + lo pair
