@@ -99,8 +99,8 @@ TcGeom make_geom(int k1, int k2, int k3, int gpt_max, int ctw_max = 256, int nus
   g.nct = (g.k + 127) / 128;
   g.nct_s = g.nct;
   // adjoint tap columns: whole tap rows per 32-column group for the kernel widths with a
-  // compile-time col2im (3, 5, 7, 9), taps in order otherwise
-  g.rpg = (k2 == 3 || k2 == 5 || k2 == 7 || k2 == 9) ? 32 / k2 : 0;
+  // compile-time col2im (3, 5, 7, 9, 11, 13), taps in order otherwise
+  g.rpg = (k2 == 3 || k2 == 5 || k2 == 7 || k2 == 9 || k2 == 11 || k2 == 13) ? 32 / k2 : 0;
   g.kcp = rup(g.kc, 64);
   g.nch_a = g.kcp / 64;
   g.Hb = TH + k1 - 1;
@@ -1488,6 +1488,8 @@ AdjKernel adj_kernel_for_t(const TcGeom& g) {
     case 5: return adj_tc_kernel<5, DET, WIDE>;
     case 7: return adj_tc_kernel<7, DET, WIDE>;
     case 9: return adj_tc_kernel<9, DET, WIDE>;
+    case 11: return adj_tc_kernel<11, DET, WIDE>;
+    case 13: return adj_tc_kernel<13, DET, WIDE>;
     default: return adj_tc_kernel<0, DET, false>;
   }
 }
@@ -1516,7 +1518,9 @@ int dev_sms() {
                          adj_tc_kernel<7, false, false>, adj_tc_kernel<9, false, false>, adj_tc_kernel<3, true, true>,
                          adj_tc_kernel<5, true, true>, adj_tc_kernel<7, true, true>, adj_tc_kernel<9, true, true>,
                          adj_tc_kernel<3, false, true>, adj_tc_kernel<5, false, true>, adj_tc_kernel<7, false, true>,
-                         adj_tc_kernel<9, false, true>})
+                         adj_tc_kernel<9, false, true>, adj_tc_kernel<11, true, false>, adj_tc_kernel<13, true, false>,
+                         adj_tc_kernel<11, false, false>, adj_tc_kernel<13, false, false>, adj_tc_kernel<11, true, true>,
+                         adj_tc_kernel<13, true, true>, adj_tc_kernel<11, false, true>, adj_tc_kernel<13, false, true>})
       cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     f.ready = true;
   }

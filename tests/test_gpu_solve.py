@@ -44,6 +44,7 @@ CASES = [
     ((24, 16, 10), (9, 9, 5), dict(last=2), 40),            # k = 405, prediction mask
     ((37, 29, 1), (5, 5, 1), dict(frac=0.5), 60),           # 2-D image
     ((16, 40, 6), (7, 7, 3), dict(frac=0.4), 50),           # k = 147
+    ((24, 40, 3), (3, 11, 2), dict(frac=0.5), 40),          # k2 = 11 (compile-time col2im, 2 tap rows a group)
 ]
 
 
