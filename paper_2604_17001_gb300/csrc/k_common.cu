@@ -186,22 +186,35 @@ __global__ void gather_fp32_kernel(Shared sh) {
 
 // End-of-pass scalars: what = 1: ||L||^2 and the residual sum of squares from the
 // per-tile partials; what = 2: objective sum_c sqrt(colsq_c).
-__global__ void finish_kernel(Shared sh, int what) {
+// One block per job. The residual partials (one float per tile and task slot) are summed per
+// thread in FP32 (GB300 runs FP64 adds at a small fraction of the FP32 rate, and this sum is
+// the stopping test's) and across threads in FP64, all in a fixed order.
+constexpr int FIN_THREADS = 1024;
+__global__ void __launch_bounds__(FIN_THREADS) finish_kernel(Shared sh, int what) {
   const JobDev& J = sh.jobs[blockIdx.x];
-  __shared__ double a[256], b[256];
+  __shared__ double a[FIN_THREADS / 32], b[FIN_THREADS / 32];
   double x = 0.0, y = 0.0;
   if (what == 2) {
     for (int c = threadIdx.x; c < sh.k; c += blockDim.x) x += sqrt(colsq_of(J, sh.kc, c));
   } else {
     for (int t = threadIdx.x; t < J.nlp; t += blockDim.x) x += J.lpart[t];
-    for (int t = threadIdx.x; t < J.ntiles * sh.nrp; t += blockDim.x) y += J.rpart[t];
+    const long long n = (long long)J.ntiles * sh.nrp;
+    float yf = 0.f;
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) yf += J.rpart[t];
+    y = yf;
   }
-  a[threadIdx.x] = x;
-  b[threadIdx.x] = y;
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    a[threadIdx.x >> 5] = x;
+    b[threadIdx.x >> 5] = y;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double sx = 0, sy = 0;
-    for (int i = 0; i < blockDim.x; ++i) { sx += a[i]; sy += b[i]; }
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { sx += a[i]; sy += b[i]; }
     if (what == 2) J.sc->objective = sx;
     else { J.sc->lsq = sx; J.sc->rsq = sy; }
   }
@@ -282,7 +295,7 @@ cudaError_t launch_gather_fp32(const Shared& sh, cudaStream_t st) {
 }
 
 cudaError_t launch_finish(const Shared& sh, int what, cudaStream_t st) {
-  finish_kernel<<<sh.njobs, 256, 0, st>>>(sh, what);
+  finish_kernel<<<sh.njobs, FIN_THREADS, 0, st>>>(sh, what);
   return cudaGetLastError();
 }
 
