@@ -60,7 +60,8 @@ typedef enum {
                             operands, FP32 accumulation; L, norms and updates in FP32.
                             With tol > 0 a job finishes in BF16X3 (where built for its
                             kernel, else in FP32), since BF16 rounding floors the residual
-                            near 1e-3 */
+                            near 1e-3. Kernels with k <= 512; EUNSUPPORTED above (FP32
+                            takes k up to 1024) */
   ICNNM_BF16X3 = 2       /* as BF16, but the forward pass A_k(X)V splits X and V into hi +
                             lo BF16 pairs (three products into one FP32 accumulator, about
                             2^-16 relative) and keeps U as a hi + lo pair; the adjoint stays

@@ -45,12 +45,26 @@ CASES = [
     ((37, 29, 1), (5, 5, 1), dict(frac=0.5), 60),           # 2-D image
     ((16, 40, 6), (7, 7, 3), dict(frac=0.4), 50),           # k = 147
     ((24, 40, 3), (3, 11, 2), dict(frac=0.5), 40),          # k2 = 11 (compile-time col2im, 2 tap rows a group)
+    ((4, 4, 4), (4, 4, 4), dict(frac=0.7), 30),             # kernel = the whole tensor
+    ((16, 16, 4), (1, 1, 1), dict(frac=0.5), 20),           # k = 1: V = [1]
+    ((3, 5, 2), (2, 3, 2), dict(frac=0.6), 30),             # tensor smaller than one 8 x 16 voxel tile
+    ((40, 40, 1), (32, 32, 1), dict(frac=0.5), 20),         # k = 1024, the largest kernel the library takes
 ]
+
+
+# Where every voxel is coupled to every other within a few iterations (a kernel as large
+# as the tensor, a tensor smaller than one voxel tile), the BF16 adjoint's rounding (U and
+# V D in BF16; BF16X3 splits only the forward pass) dominates the error: a CPU emulation of
+# exactly these roundings gives 1.26e-3 (BF16) and 6.3e-4 (BF16X3) for the whole-tensor
+# kernel and 1.3e-4 (BF16X3) for the sub-tile tensor, which the GPU reproduces. Bars:
+EDGE_TOL = {((4, 4, 4), (4, 4, 4)): {"bf16": 2e-3, "bf16x3": 1e-3},
+            ((3, 5, 2), (2, 3, 2)): {"bf16x3": 2e-4}}
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("dims,kdims,mk,iters", CASES)
 def test_solve_matches_oracle(ctx, prec, dims, kdims, mk, iters):
+    tol = EDGE_TOL.get((dims, kdims), {}).get(prec, TOL[prec])
     M, mask, V, _ = case(dims, kdims, **mk)
     Lo, so = O.icnnm_solve(M, mask, V, kdims, max_iters=iters)
     try:
@@ -60,11 +74,11 @@ def test_solve_matches_oracle(ctx, prec, dims, kdims, mk, iters):
             pytest.skip(str(e))
         raise
     e = rel(L, Lo)
-    assert e <= TOL[prec], (prec, dims, kdims, e)
+    assert e <= tol, (prec, dims, kdims, e)
     msk = mask.astype(bool)
     assert np.array_equal(L[msk], M[msk])                      # P_Omega(L) = P_Omega(M) exactly
     assert st["iters"] == iters
-    assert abs(st["objective"] - so["objective"]) <= 10 * max(TOL[prec], 1e-5) * so["objective"]
+    assert abs(st["objective"] - so["objective"]) <= 10 * max(tol, 1e-5) * so["objective"]
     assert abs(st["theta"] - so["theta"]) <= 1e-6 * so["theta"]
 
 
