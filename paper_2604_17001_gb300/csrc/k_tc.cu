@@ -213,6 +213,7 @@ struct FwdArgs {
   TcGeom g;
   FwdTab tab;
   int mode;
+  int cta0[9];   // first CTA of each channel tile (cta0[nct] = grid size)
 };
 
 // TMA store of one tile's U' (hi, and lo for the split form) from a U stage.
@@ -373,8 +374,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
   uint32_t* tslot = reinterpret_cast<uint32_t*>(dbar + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ct = blockIdx.x % nct;
-  const int slot = blockIdx.x / nct, nslot = gridDim.x / nct;
+  int ct = 0;
+  while (ct + 1 < nct && (int)blockIdx.x >= a.cta0[ct + 1]) ++ct;
+  const int slot = (int)blockIdx.x - a.cta0[ct], nslot = a.cta0[ct + 1] - a.cta0[ct];
   const int mode = a.mode;
   const bool rdU = (mode == 1 || mode == 3);   // U is read (TMA) in these modes
   const bool wrU = (mode == 1 || mode == 2);   // U' is written (TMA store) in these modes
@@ -1542,9 +1544,29 @@ cudaError_t tc_launch_fwd(const Shared& sh, const TcVData& v, int mode, cudaStre
   a.mode = mode;
   const size_t smem = fwd_smem(v.g, split);
   const int per = tc_fwd_slots(sh, v, split);
-  if (split) fwd_tc_kernel<true, false><<<per * v.g.nct_s, TC_THREADS, smem, st>>>(a);
-  else if (v.g.ctw > 128) fwd_tc_kernel<false, true><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
-  else fwd_tc_kernel<false, false><<<per * v.g.nct, TC_THREADS, smem, st>>>(a);
+  const int nct = split ? v.g.nct_s : v.g.nct;
+  if (nct > 8) return cudaErrorInvalidValue;     // k <= 512 on this path: at most 4 tiles
+  // CTAs per channel tile: equal shares, except that the split pass with deterministic
+  // partials (rows per chunk, whatever the CTA count) gives each tile CTAs in proportion to
+  // an estimate of its work: its MMAs (the same for every tile, weighted as two column
+  // groups) plus its epilogue's 32-channel groups
+  int cnt[8];
+  for (int ct = 0; ct < nct; ++ct) cnt[ct] = per;
+  if (split && v.g.det && nct > 1 && nct <= 8) {
+    int wsum = 0, w[8];
+    for (int ct = 0; ct < nct; ++ct) {
+      w[ct] = 2 + std::min(4, (v.g.kc - 128 * ct + 31) / 32);
+      wsum += w[ct];
+    }
+    const int total = per * nct, cap = std::max(1, sh.total_chunks);
+    for (int ct = 0; ct < nct; ++ct) cnt[ct] = std::max(1, std::min(cap, total * w[ct] / wsum));
+  }
+  a.cta0[0] = 0;
+  for (int ct = 0; ct < nct; ++ct) a.cta0[ct + 1] = a.cta0[ct] + cnt[ct];
+  const int grid = a.cta0[nct];
+  if (split) fwd_tc_kernel<true, false><<<grid, TC_THREADS, smem, st>>>(a);
+  else if (v.g.ctw > 128) fwd_tc_kernel<false, true><<<grid, TC_THREADS, smem, st>>>(a);
+  else fwd_tc_kernel<false, false><<<grid, TC_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
