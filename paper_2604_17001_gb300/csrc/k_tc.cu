@@ -988,6 +988,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     const int ew = warp - 2;
     const int vox = q * 32 + lane;
     const int hoff = (vox >> 3) * g.pitch;
+    // The halo entries a thread flushes (p = ew*32 + lane + i*512) are the same for every
+    // tile: their buffer index and (frame, row, column) are packed once into one word each
+    // (si << 16 | st << 12 | bh << 6 | bw; all-ones: nothing to flush) where they fit
+    constexpr int FL_MAX = 4;
+    const bool fl_pre = g.HB <= FL_MAX * 32 * EPI_WARPS && g.k3 <= 16 && g.Hb <= 64 && g.Wb <= 64 &&
+                        g.HBp <= 65535;
+    uint32_t fl[FL_MAX];
+#pragma unroll
+    for (int f = 0; f < FL_MAX; ++f) {
+      const int p = ew * 32 + lane + f * 32 * EPI_WARPS;
+      uint32_t code = 0xFFFFFFFFu;
+      if (fl_pre && p < g.HB) {
+        const int row = p / g.Wb, col = p - row * g.Wb;
+        const int j = row / g.Hb, bh = row - j * g.Hb;
+        const int st = g.slo[tt] + j;
+        if (st < g.k3)
+          code = ((uint32_t)(((g.k3 - 1 - st) * g.Hb + bh) * g.pitch + col) << 16) | ((uint32_t)st << 12) |
+                 ((uint32_t)bh << 6) | (uint32_t)col;
+      }
+      fl[f] = code;
+    }
     int i = 0;
     int prev_jb = 0, prev_t = 0, prev_h0 = 0, prev_w0 = 0;   // tile flushed next: job, frame, halo origin
     for (int tg = lo; tg <= hi; ++tg, ++i) {
@@ -1040,20 +1061,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         // halo entry (frame st, row bh, column bw) belongs to voxel ((t - st) mod T,
         // (th*TH - (k1-1) + bh) mod H, (tw*TW - (k2-1) + bw) mod W); only the nsl frames
         // this tap tile reaches (from slo) can be nonzero
-        for (int p = ew * 32 + lane; p < g.HB; p += 32 * EPI_WARPS) {
-          const int row = p / g.Wb, col = p - row * g.Wb;   // row = j * Hb + bh
-          const int j = row / g.Hb, bh = row - j * g.Hb;
-          const int st = g.slo[tt] + j;
-          if (st >= g.k3) continue;
-          const int si = ((g.k3 - 1 - st) * g.Hb + bh) * g.pitch + col;
+        const JobDev& P = sh.jobs[prev_jb];
+        const int PT = P.T, PH = P.H, PW = P.W;
+        HT* PG = reinterpret_cast<HT*>(P.G);
+        auto flush_one = [&](int si, int st, int bh, int col) {
           const HT v = src[si];
           src[si] = (HT)0;
-          const JobDev& P = sh.jobs[prev_jb];
           int tq = prev_t - st, hq = prev_h0 + bh, wq = prev_w0 + col;
-          tq += tq < 0 ? P.T : 0;
-          hq = hq < 0 ? hq + P.H : (hq >= P.H ? hq - P.H : hq);
-          wq = wq < 0 ? wq + P.W : (wq >= P.W ? wq - P.W : wq);
-          if (v) atomicAdd(reinterpret_cast<HT*>(P.G) + ((size_t)tq * P.H + hq) * P.W + wq, v);
+          tq += tq < 0 ? PT : 0;
+          hq = hq < 0 ? hq + PH : (hq >= PH ? hq - PH : hq);
+          wq = wq < 0 ? wq + PW : (wq >= PW ? wq - PW : wq);
+          if (v) atomicAdd(PG + ((size_t)tq * PH + hq) * PW + wq, v);
+        };
+        if (fl_pre) {
+#pragma unroll
+          for (int f = 0; f < FL_MAX; ++f) {
+            const uint32_t code = fl[f];
+            if (code != 0xFFFFFFFFu)
+              flush_one((int)(code >> 16), (int)((code >> 12) & 15u), (int)((code >> 6) & 63u), (int)(code & 63u));
+          }
+        } else {
+          for (int p = ew * 32 + lane; p < g.HB; p += 32 * EPI_WARPS) {
+            const int row = p / g.Wb, col = p - row * g.Wb;   // row = j * Hb + bh
+            const int j = row / g.Hb, bh = row - j * g.Hb;
+            const int st = g.slo[tt] + j;
+            if (st >= g.k3) continue;
+            flush_one(((g.k3 - 1 - st) * g.Hb + bh) * g.pitch + col, st, bh, col);
+          }
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&zbar[pb]);
