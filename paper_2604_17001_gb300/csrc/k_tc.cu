@@ -807,7 +807,7 @@ __device__ __forceinline__ int adj_rowoff(const TcGeom& g, int TR) {
 // runs in a fixed order; the reductions of different warps into one address do not.
 template <int K2, typename HT>
 __device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, HT* hb, int hoff,
-                                                const TcGeom& g, int G) {
+                                                const TcGeom& g, int G, const int* rtab, int TR0) {
   constexpr int RPG = 32 / K2;            // tap rows a group can hold; it holds g.rpg <= RPG
   constexpr int NJ = (K2 + 14) / 8;      // halo columns 0 .. K2 + 6 over 8 lanes
   const int w = lane & 7;
@@ -816,7 +816,7 @@ __device__ __forceinline__ void adj_col2im_rows(const float (&e)[32], int lane, 
     if (r >= g.rpg) break;                 // warp-uniform: the group's unused rows
     const int TR = G * g.rpg + r;
     if (TR >= g.k1 * g.k3) break;          // warp-uniform: padding rows
-    const int base = hoff + adj_rowoff(g, TR);
+    const int base = hoff + rtab[TR - TR0];   // adj_rowoff(g, TR), tabulated per CTA
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       float T = 0.f;
@@ -902,6 +902,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
       o = ((g.k3 - 1 - st) * g.Hb + (g.k1 - 1 - shh)) * g.pitch + (g.k2 - 1 - sw);
     }
     toff[threadIdx.x] = o;
+  }
+  // compile-time k2: halo offset of each tap row of this tap tile (at most gpt * 32 / k2 <=
+  // 80 rows), toff[TR - TR0] for row TR
+  if (K2 > 0 && threadIdx.x < 128) {
+    const int TR = tt * g.gpt * g.rpg + threadIdx.x;
+    toff[threadIdx.x] = TR < g.k1 * g.k3 ? adj_rowoff(g, TR) : 0;
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -1035,7 +1041,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
               __syncwarp();
               if (lane == 0) ptx::mbar_arrive(&tempty[b]);
             }
-            adj_col2im_rows<K2>(v, lane, hb, hoff, g, tt * gpt + cg + 4 * gi);
+            adj_col2im_rows<K2>(v, lane, hb, hoff, g, tt * gpt + cg + 4 * gi, toff, tt * gpt * g.rpg);
           }
         } else {
           ptx::tmem_ld32(tl + (uint32_t)cg * 32, v);
