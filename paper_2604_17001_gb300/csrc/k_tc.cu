@@ -216,6 +216,27 @@ struct FwdArgs {
   int cta0[9];   // first CTA of each channel tile (cta0[nct] = grid size)
 };
 
+// Voxel-tile coordinates (tw, th, t) of the tiles a thread visits (the adjoint's contiguous
+// tile ranges): the next tile of the same job advances them by one (w fastest, then h,
+// then t); any other tile divides.
+struct TileXY {
+  int jb = -1, tile = -1, tw = 0, th = 0, t = 0;
+  __device__ __forceinline__ void at(int jb_, int tile_, const JobDev& J) {
+    if (jb_ == jb && tile_ == tile + 1) {
+      if (++tw == J.ntw) {
+        tw = 0;
+        if (++th == J.nth) { th = 0; ++t; }
+      }
+    } else if (jb_ != jb || tile_ != tile) {
+      tw = tile_ % J.ntw;
+      th = (tile_ / J.ntw) % J.nth;
+      t = tile_ / (J.ntw * J.nth);
+    }
+    jb = jb_;
+    tile = tile_;
+  }
+};
+
 // TMA store of one tile's U' (hi, and lo for the split form) from a U stage.
 template <int NIMG>
 __device__ __forceinline__ void fwd_store_u(const Shared& sh, uint8_t* stage, size_t uhalf, int jb, int tile, int c0,
@@ -1017,6 +1038,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
     }
     int i = 0;
     int prev_jb = 0, prev_t = 0, prev_h0 = 0, prev_w0 = 0;   // tile flushed next: job, frame, halo origin
+    TileXY txy;
     for (int tg = lo; tg <= hi; ++tg, ++i) {
       const bool have = tg < hi;
       HT* hb = buf + (size_t)(i & 1) * g.HBp;
@@ -1099,13 +1121,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) adj_tc_kernel(const __grid_cons
         if (lane == 0) ptx::mbar_arrive(&zbar[pb]);
       }
       if (have) {
-        const int jb = job_of_tile(sh.job_tile0, sh.njobs, tg);
+        const int jb = (txy.jb >= 0 && tg < sh.job_tile0[txy.jb + 1]) ? txy.jb
+                                                                      : job_of_tile(sh.job_tile0, sh.njobs, tg);
         const JobDev& J = sh.jobs[jb];
         const int tile = tg - sh.job_tile0[jb];
+        txy.at(jb, tile, J);
         prev_jb = jb;
-        prev_t = tile / (J.ntw * J.nth);
-        prev_h0 = ((tile / J.ntw) % J.nth) * TH - (g.k1 - 1);
-        prev_w0 = (tile % J.ntw) * TW - (g.k2 - 1);
+        prev_t = txy.t;
+        prev_h0 = txy.th * TH - (g.k1 - 1);
+        prev_w0 = txy.tw * TW - (g.k2 - 1);
       }
     }
   }
