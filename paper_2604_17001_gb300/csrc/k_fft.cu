@@ -18,8 +18,10 @@
 // Every signal is real, so transforms along w keep the W/2 + 1 non-negative frequencies
 // (the rest are complex conjugates); in Parseval the interior w-frequencies count twice.
 // FFTs are radix-2 over power-of-two lengths, one kernel per axis, LB lines per block staged
-// in shared memory, twiddles from FP64 values. Arithmetic is FP32 complex; norms are summed
-// per thread in FP32 and across threads and blocks in FP64, in a fixed order.
+// in shared memory, twiddles from FP64 values; in the iteration, the inverse transform along
+// w, the L-update and the next operand's transform along w share one kernel and its lines.
+// Arithmetic is FP32 complex; norms are summed per thread in FP32 and across threads and
+// blocks in FP64, in a fixed order.
 #include <math.h>
 
 #include <algorithm>
@@ -107,35 +109,6 @@ __global__ void rfft_rows_kernel(const float* x, float2* out, int W, int logw, l
     const int l = i / Wh, e = i - l * Wh;
     const long long row = r0 + l;
     if (row < nrows) out[row * Wh + e] = sm[l * W + e];
-  }
-}
-
-// Inverse of rfft_rows, times `scale`: each row's W/2 + 1 values are extended to W by
-// conjugate symmetry, inverse-transformed, and the real parts stored.
-__global__ void irfft_rows_kernel(const float2* in, float* x, int W, int logw, long long nrows, const float2* tw,
-                                  float scale) {
-  extern __shared__ float2 sm[];
-  const long long r0 = (long long)blockIdx.x * LB;
-  const int Wh = W / 2 + 1;
-  for (int i = threadIdx.x; i < LB * W; i += blockDim.x) {
-    const int l = i / W, e = i - l * W;
-    const long long row = r0 + l;
-    float2 v = make_float2(0.f, 0.f);
-    if (row < nrows) {
-      if (e < Wh) {
-        v = in[row * Wh + e];
-      } else {
-        const float2 c = in[row * Wh + (W - e)];
-        v = make_float2(c.x, -c.y);
-      }
-    }
-    sm[l * W + bitrev(e, logw)] = v;
-  }
-  fft_smem(sm, W, logw, tw, true);
-  for (int i = threadIdx.x; i < LB * W; i += blockDim.x) {
-    const int l = i / W, e = i - l * W;
-    const long long row = r0 + l;
-    if (row < nrows) x[row * W + e] = sm[l * W + e].x * scale;
   }
 }
 
@@ -306,30 +279,80 @@ __global__ void fft_colsq_kernel(const double* part, int k, double inv_m, double
   }
 }
 
-// L-update from Delta = A_k^*(U D V^T) (lambda = inf: P_Omega^perp(L + Delta/(k theta)) +
-// P_Omega(M); finite lambda: the penalised form), the next forward operand
-// X = (theta + theta') L' - theta L, and block partials of ||L'||^2.
-__global__ void fft_gather_kernel(float* L, float* X, const float* Dl, const float* M, const uint8_t* mask,
-                                  long long m, double th, double thn, double lam, int k, double* lpart) {
-  double l2 = 0.0;
+// One iteration's row stage, LB rows of W voxels per block: the rows of Delta^ (already
+// inverse-transformed along t and h) are extended by conjugate symmetry and
+// inverse-transformed along w (times 1/m), giving Delta = A_k^*(U D V^T); the L-update is
+// applied per voxel (lambda = inf: P_Omega^perp(L + Delta/(k theta)) + P_Omega(M); finite
+// lambda: the penalised form); the next forward operand X = (theta + theta') L' - theta L
+// is transformed along w in the same shared-memory lines and its W/2 + 1 frequencies
+// stored; lpart[block] = the block's ||L'||^2 (FP64, fixed order).
+__global__ void fft_row_update_kernel(const float2* __restrict__ Dh, float* __restrict__ L,
+                                      const float* __restrict__ M, const uint8_t* __restrict__ mask,
+                                      float2* __restrict__ Xh, int W, int logw, long long nrows,
+                                      const float2* __restrict__ tw, float scale, double th, double thn, double lam,
+                                      int k, double* __restrict__ lpart) {
+  extern __shared__ float2 sm[];
+  __shared__ double red[32];
+  const long long r0 = (long long)blockIdx.x * LB;
+  const int Wh = W / 2 + 1;
+  for (int i = threadIdx.x; i < LB * W; i += blockDim.x) {
+    const int l = i / W, e = i - l * W;
+    const long long row = r0 + l;
+    float2 v = make_float2(0.f, 0.f);
+    if (row < nrows) {
+      if (e < Wh) {
+        v = Dh[row * Wh + e];
+      } else {
+        const float2 c = Dh[row * Wh + (W - e)];
+        v = make_float2(c.x, -c.y);
+      }
+    }
+    sm[l * W + bitrev(e, logw)] = v;
+  }
+  fft_smem(sm, W, logw, tw, true);
   const float inv = (float)(1.0 / (k * th));
   const float xa = (float)(th + thn), xb = -(float)th;
   const bool exact = isinf(lam);
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < m; v += (long long)gridDim.x * blockDim.x) {
-    const float Lo = L[v], d = Dl[v];
-    const bool obs = mask[v] != 0;
-    float Ln;
-    if (exact) {
-      Ln = obs ? M[v] : fmaf(d, inv, Lo);
-    } else {
-      const double lt = obs ? lam : 0.0;
-      Ln = (float)(((double)d / k + th * (double)Lo + lt * (obs ? (double)M[v] : 0.0)) / (lt + th));
+  double l2 = 0.0;
+  for (int i = threadIdx.x; i < LB * W; i += blockDim.x) {
+    const int l = i / W, e = i - l * W;
+    const long long row = r0 + l;
+    float x = 0.f;
+    if (row < nrows) {
+      const long long v = row * W + e;
+      const float d = sm[i].x * scale;
+      const float Lo = L[v];
+      const bool obs = mask[v] != 0;
+      float Ln;
+      if (exact) {
+        Ln = obs ? M[v] : fmaf(d, inv, Lo);
+      } else {
+        const double lt = obs ? lam : 0.0;
+        Ln = (float)(((double)d / k + th * (double)Lo + lt * (obs ? (double)M[v] : 0.0)) / (lt + th));
+      }
+      x = fmaf(xa, Ln, xb * Lo);
+      L[v] = Ln;
+      l2 += (double)Ln * Ln;
     }
-    X[v] = fmaf(xa, Ln, xb * Lo);
-    L[v] = Ln;
-    l2 += (double)Ln * Ln;
+    sm[i] = make_float2(x, 0.f);
   }
-  __shared__ double red[32];
+  __syncthreads();
+  // bit-reversed order for the forward transform (each pair swapped by one thread)
+  for (int i = threadIdx.x; i < LB * W; i += blockDim.x) {
+    const int l = i / W, e = i - l * W;
+    const int r = bitrev(e, logw);
+    if (e < r) {
+      const float2 a = sm[l * W + e];
+      sm[l * W + e] = sm[l * W + r];
+      sm[l * W + r] = a;
+    }
+  }
+  fft_smem(sm, W, logw, tw, false);
+  for (int i = threadIdx.x; i < LB * Wh; i += blockDim.x) {
+    const int l = i / Wh, e = i - l * Wh;
+    const long long row = r0 + l;
+    if (row < nrows) Xh[row * Wh + e] = sm[l * W + e];
+  }
   for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
   __syncthreads();
@@ -411,7 +434,6 @@ cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res) {
   float2* Dh = (float2*)alloc(sizeof(float2) * mh);
   float* L = P.dL;
   float* X = (float*)alloc(4 * m);
-  float* Dl = (float*)alloc(4 * m);
   float* xs = (float*)alloc(4 * (size_t)chunk * m);
   double* part = (double*)alloc(8 * (size_t)k * NB);
   double* colsq = (double*)alloc(8 * (size_t)k);
@@ -420,7 +442,8 @@ cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res) {
   int sms = 152;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P.device);
   const int gblocks = std::max(1, std::min(8 * sms, 2048));
-  double* lpart = (double*)alloc(8 * (size_t)gblocks);
+  const int nrb = (int)(((long long)T * H + LB - 1) / LB);        // blocks of the row stage
+  double* lpart = (double*)alloc(8 * (size_t)nrb);
   // twiddles exp(-2 pi i j / n) per axis length, from FP64 cos/sin
   const int lens[3] = {W, H, T};
   float2* tws[3] = {nullptr, nullptr, nullptr};
@@ -446,7 +469,29 @@ cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fft_axis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(rfft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(irfft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    e = cudaFuncSetAttribute(fft_row_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+  // inverse transforms of a half spectrum along t and h (in place); the row stage does w
+  auto inv_th = [&](float2* in) {
+    if (e != cudaSuccess) return;
+    if (T > 1)
+      fft_axis_kernel<<<(unsigned)(((long long)H * Wh + LB - 1) / LB), fthreads, LB * T * sizeof(float2), st>>>(
+          in, T, lt, (long long)H * Wh, (long long)H * Wh, mh, (long long)H * Wh, tws[2], 1);
+    if (H > 1)
+      fft_axis_kernel<<<(unsigned)(((long long)T * Wh + LB - 1) / LB), fthreads, LB * H * sizeof(float2), st>>>(
+          in, H, lh, Wh, Wh, (long long)H * Wh, (long long)T * Wh, tws[1], 1);
+    e = cudaGetLastError();
+  };
+  // forward transforms along h and t (in place), as in rfft3 after its row stage
+  auto fwd_ht = [&](float2* out) {
+    if (e != cudaSuccess) return;
+    if (H > 1)
+      fft_axis_kernel<<<(unsigned)(((long long)T * Wh + LB - 1) / LB), fthreads, LB * H * sizeof(float2), st>>>(
+          out, H, lh, Wh, Wh, (long long)H * Wh, (long long)T * Wh, tws[1], 0);
+    if (T > 1)
+      fft_axis_kernel<<<(unsigned)(((long long)H * Wh + LB - 1) / LB), fthreads, LB * T * sizeof(float2), st>>>(
+          out, T, lt, (long long)H * Wh, (long long)H * Wh, mh, (long long)H * Wh, tws[2], 0);
+    e = cudaGetLastError();
+  };
   // nb real tensors x[b*m ...] -> their half spectra out[b*mh ...]
   auto rfft3 = [&](const float* x, float2* out, int nb) {
     if (e != cudaSuccess) return;
@@ -463,20 +508,6 @@ cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res) {
       fft_axis_kernel<<<(unsigned)((lines + LB - 1) / LB), fthreads, LB * T * sizeof(float2), st>>>(
           out, T, lt, (long long)H * Wh, (long long)H * Wh, mh, lines, tws[2], 0);
     }
-    e = cudaGetLastError();
-  };
-  // a half spectrum (overwritten) -> the real tensor, with the 1/m of the inverse
-  auto irfft3 = [&](float2* in, float* x) {
-    if (e != cudaSuccess) return;
-    if (T > 1)
-      fft_axis_kernel<<<(unsigned)(((long long)H * Wh + LB - 1) / LB), fthreads, LB * T * sizeof(float2), st>>>(
-          in, T, lt, (long long)H * Wh, (long long)H * Wh, mh, (long long)H * Wh, tws[2], 1);
-    if (H > 1)
-      fft_axis_kernel<<<(unsigned)(((long long)T * Wh + LB - 1) / LB), fthreads, LB * H * sizeof(float2), st>>>(
-          in, H, lh, Wh, Wh, (long long)H * Wh, (long long)T * Wh, tws[1], 1);
-    const long long rows = (long long)T * H;
-    irfft_rows_kernel<<<(unsigned)((rows + LB - 1) / LB), fthreads, LB * W * sizeof(float2), st>>>(
-        in, x, W, lw, rows, tws[0], (float)(1.0 / (double)m));
     e = cudaGetLastError();
   };
   // a spectral pass, then the per-column squared norms (and, with shrink, s and D)
@@ -498,11 +529,11 @@ cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res) {
                                                       shrink ? Dv : nullptr);
     e = cudaGetLastError();
   };
-  std::vector<double> hc(k), hl(gblocks);
+  std::vector<double> hc(k), hl(nrb);
   auto read_back = [&](bool with_l) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), colsq, 8 * (size_t)k, cudaMemcpyDeviceToHost, st);
     if (with_l && e == cudaSuccess)
-      e = cudaMemcpyAsync(hl.data(), lpart, 8 * (size_t)gblocks, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(hl.data(), lpart, 8 * (size_t)nrb, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   };
   auto pass_begin = [&](int pass, int nk, long long nvox) {
@@ -555,12 +586,15 @@ cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res) {
     fft_adjoint_kernel<<<adj_blocks, ADJ_P * ADJ_S, sizeof(float) * k, st>>>(Yh, Dv, k, (unsigned)mh, Dh);
     pass_end(1);
     e = cudaGetLastError();
-    pass_begin(3, nk_fft, 0);
-    irfft3(Dh, Dl);
+    pass_begin(3, nk_fft - 1, 0);
+    inv_th(Dh);
     pass_end(3);
     if (e == cudaSuccess) {
+      // Delta along w, the L-update and the next operand's transform along w, fused
       pass_begin(2, 1, m);
-      fft_gather_kernel<<<gblocks, 256, 0, st>>>(L, X, Dl, P.dM, P.dmask, m, theta, thn, P.lambda, k, lpart);
+      fft_row_update_kernel<<<nrb, fthreads, LB * W * sizeof(float2), st>>>(
+          Dh, L, P.dM, P.dmask, Xh, W, lw, (long long)T * H, tws[0], (float)(1.0 / (double)m), theta, thn, P.lambda,
+          k, lpart);
       pass_end(2);
       e = cudaGetLastError();
     }
@@ -581,9 +615,9 @@ cudaError_t fft_run(const FftProblem& P, cudaStream_t st, FftResult* res) {
     }
     theta = thn;
     if (stop) break;
-    // U' = U D - A_k(X)V and its column norms
-    pass_begin(3, nk_fft, 0);
-    rfft3(X, Xh, 1);
+    // U' = U D - A_k(X)V and its column norms (X^ along w from the row stage)
+    pass_begin(3, nk_fft - 1, 0);
+    fwd_ht(Xh);
     pass_end(3);
     pass_begin(0, 2, m);
     spectral(Xh, 1, 0.0, true);
