@@ -1010,11 +1010,14 @@ def run_serving_bench(args, ws, rank, local):
         th_.join()
     lat_ms = np.array(lat if lat else [float("nan")]) * 1e3
 
-    # roofline of the dominant pass over one profiled wave
+    # roofline of the dominant kernel over one profiled wave: the forward pass of the BF16
+    # jobs, of the jobs finishing in BF16X3 and of FP32 jobs are profiled apart (different
+    # kernels, different bytes and flops per voxel)
     ctx.lib.icnnm_profile_enable(ctx.h, 1)
     prof_sec, _ = wave(waves[0])
     prof = {}
-    for p_, name in ((0, "forward"), (1, "adjoint"), (2, "gather"), (3, "other")):
+    for p_, name in ((0, "forward"), (4, "forward_bf16x3"), (5, "forward_fp32"), (1, "adjoint"), (2, "gather"),
+                     (3, "other")):
         ms, n_, vx = C.c_double(), C.c_int64(), C.c_int64()
         ctx.lib.icnnm_profile_read(ctx.h, p_, C.byref(ms), C.byref(n_))
         ctx.lib.icnnm_profile_voxels(ctx.h, p_, C.byref(vx))
@@ -1023,27 +1026,40 @@ def run_serving_bench(args, ws, rank, local):
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     tfl = peaks.get("bf16_tflops_sustained", 1700.0)
-    dom = max(("forward", "adjoint"), key=lambda n: prof[n][0])
-    ms, n_, vx = prof[dom]
-    per_ms = ms / max(n_, 1)
-    vox_per_launch = vx / max(n_, 1)
-    alg_bytes = (4 if dom == "forward" else 2) * k * vox_per_launch     # BF16 U read (+ write)
-    alg_flops = 2.0 * k * k * vox_per_launch
-    gbs = alg_bytes / (per_ms * 1e-3) / 1e9
-    tfs = alg_flops / (per_ms * 1e-3) / 1e12
     src = "measured" if peaks else "fallback"
-    if gbs / hbm >= tfs / tfl:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+    # algorithmic bytes and tensor flops per voxel of each pass's kernel: BF16 forward reads
+    # and writes U in BF16 (4k bytes), 2k^2 flops; BF16X3 forward the hi + lo pair (8k bytes)
+    # and three products (6k^2); FP32 forward U in FP32 (8k bytes, SIMT flops, no tensor
+    # bound); adjoint reads U in BF16 (2k bytes), 2k^2 flops
+    per_vox = {"forward": (4 * k, 2.0 * k * k), "forward_bf16x3": (8 * k, 6.0 * k * k),
+               "forward_fp32": (8 * k, 0.0), "adjoint": (2 * k, 2.0 * k * k)}
+    fracs = {}
+    for name, (bpv, fpv) in per_vox.items():
+        ms, n_, vx = prof[name]
+        if n_ == 0 or ms <= 0:
+            continue
+        gbs_ = bpv * vx / (ms * 1e-3) / 1e9
+        tfs_ = fpv * vx / (ms * 1e-3) / 1e12
+        fracs[name] = {"ms": ms, "launches": n_, "voxels_per_launch": vx / n_, "hbm_gbs_alg": gbs_,
+                       "hbm_frac": gbs_ / hbm, "tensor_tflops_alg": tfs_, "tensor_frac": tfs_ / tfl}
+    dom = max(fracs, key=lambda n: fracs[n]["ms"])
+    d_ = fracs[dom]
+    if d_["hbm_frac"] >= d_["tensor_frac"]:
+        roof = {"bound": "hbm", "achieved": d_["hbm_gbs_alg"], "peak": hbm, "unit": "GB/s", "frac": d_["hbm_frac"]}
     else:
-        roof = {"bound": "tensor", "achieved": tfs, "peak": tfl, "unit": "TFLOP/s", "frac": tfs / tfl}
+        roof = {"bound": "tensor", "achieved": d_["tensor_tflops_alg"], "peak": tfl, "unit": "TFLOP/s",
+                "frac": d_["tensor_frac"]}
+    per_ms = d_["ms"] / d_["launches"]
+    vox_per_launch = d_["voxels_per_launch"]
     traffic = None
-    if os.path.exists(TRAFFIC):
+    if os.path.exists(TRAFFIC) and dom in ("forward", "adjoint"):
         ent = json.load(open(TRAFFIC)).get(f"serving_{dom}")
         if ent and ent.get("source_hash") == kernel_source_hash():
             traffic = ent.get("bytes_per_voxel") * vox_per_launch   # scaled to this launch's voxels
-    roof.update({"traffic": traffic, "kernel": dom, "peak_source": src, "ms_per_launch": per_ms, "launches": n_,
-                 "voxels_per_launch": vox_per_launch, "hbm_gbs_alg": gbs, "tensor_tflops_alg": tfs,
-                 "profiled_wave_s": prof_sec,
+    roof.update({"traffic": traffic, "kernel": dom, "peak_source": src, "ms_per_launch": per_ms,
+                 "launches": d_["launches"], "voxels_per_launch": vox_per_launch, "hbm_gbs_alg": d_["hbm_gbs_alg"],
+                 "tensor_tflops_alg": d_["tensor_tflops_alg"], "profiled_wave_s": prof_sec,
+                 "passes": fracs,
                  "share_of_step": {k_: prof[k_][0] / max(1e-9, sum(v[0] for v in prof.values())) for k_ in prof}})
 
     # end to end through the C ABI with host buffers: the first wave again

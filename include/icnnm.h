@@ -268,9 +268,10 @@ icnnm_status icnnm_cancel(icnnm_ctx* ctx, uint64_t job_id);
  * brackets each pass of the blocking solves with CUDA events on the context's stream
  * and counts every kernel it launches.
  *   icnnm_profile_enable : enable (1) or disable (0); either resets the counters.
- *   icnnm_profile_read   : pass 0 = forward pass A_k(X)V fused with the U update,
+ *   icnnm_profile_read   : pass 0 = forward pass A_k(X)V fused with the U update (BF16),
  *                          1 = adjoint pass (V D)U^T with col2im, 2 = gather/projection
- *                          (L-update), 3 = everything else; ms_total = summed device
+ *                          (L-update), 3 = everything else, 4 = forward pass of BF16X3
+ *                          jobs, 5 = forward pass of FP32 jobs; ms_total = summed device
  *                          time, launches = kernels of that pass (pass -1: all kernels,
  *                          ms_total = 0). EINVAL for other pass ids.
  */

@@ -135,6 +135,8 @@ size_t job_bytes(int H, int W, int T, int k, int kc, int prec, int nrp, const Tc
 // ---------------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------------
+constexpr int NPASS = 6;   // profiled passes (see icnnm_profile_read)
+
 struct icnnm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -164,9 +166,11 @@ struct icnnm_ctx {
   std::vector<cudaEvent_t> evpool;
   size_t evnext = 0;
   std::vector<std::pair<int, size_t>> pending;   // (pass, index of the start event)
-  double pass_ms[4] = {0, 0, 0, 0};
-  long long pass_n[5] = {0, 0, 0, 0, 0};
-  long long pass_vox[5] = {0, 0, 0, 0, 0};
+  // passes: 0 forward (BF16), 1 adjoint, 2 gather, 3 other, 4 forward (BF16X3),
+  // 5 forward (FP32 lists); index NPASS counts every pass
+  double pass_ms[NPASS] = {};
+  long long pass_n[NPASS + 1] = {};
+  long long pass_vox[NPASS + 1] = {};
   size_t hook_idx = 0;                           // start event of the open hook pass
   // engine scratch
   // device job tables: slot 0 for the main list, slot 1 for a list stepped beside it
@@ -264,9 +268,9 @@ struct PassScope {
   size_t idx = 0;
   PassScope(icnnm_ctx* c_, int pass_, int nkernels, long long nvox = 0) : c(c_), pass(pass_) {
     c->pass_n[pass] += nkernels;
-    c->pass_n[4] += nkernels;
+    c->pass_n[NPASS] += nkernels;
     c->pass_vox[pass] += nvox;
-    c->pass_vox[4] += nvox;
+    c->pass_vox[NPASS] += nvox;
     if (c->prof) {
       idx = c->evnext;
       CK(cudaEventRecord(pool_event(c), c->stream));
@@ -620,7 +624,7 @@ Shared upload_list(icnnm_ctx* c, const std::vector<Job*>& js, int slot = 0) {
 
 void run_fwd(icnnm_ctx* c, const Shared& sh, int prec, int mode, const TcVData* tcv) {
   // the once-per-solve FP32 passes (theta0, objective) count as "other"
-  PassScope ps(c, mode == 0 || mode == 4 ? 3 : 0, 1, sh.nvox);
+  PassScope ps(c, mode == 0 || mode == 4 ? 3 : (prec == ICNNM_BF16X3 ? 4 : (prec == ICNNM_FP32 ? 5 : 0)), 1, sh.nvox);
   if (prec == ICNNM_FP32 || mode == 0 || mode == 4) CK(launch_fwd_fp32(sh, mode, c->stream));
   else CK(tc_launch_fwd(sh, *tcv, mode, c->stream, prec == ICNNM_BF16X3));
 }
@@ -788,7 +792,7 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   constexpr int GRAPH_ITERS = 25;
   const bool graphs = c->stream != cudaStreamLegacy && c->stream != nullptr;
   cudaGraphExec_t gexec = nullptr;
-  long long graph_counts[5] = {0, 0, 0, 0, 0}, graph_vox[5] = {0, 0, 0, 0, 0};
+  long long graph_counts[NPASS + 1] = {}, graph_vox[NPASS + 1] = {};
   auto is_check = [&](int i) { return i >= p.max_iters || (p.tol > 0 && i % p.check_every == 0); };
   auto plain_run = [&](int from) {          // plain iterations from..from+n-1
     int n = 0;
@@ -798,8 +802,8 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
   while (!live.empty()) {
     if (graphs && !c->prof && it >= 1 && live32.empty() && plain_run(it + 1) >= GRAPH_ITERS) {
       if (!gexec) {
-        long long before[5], vbefore[5];
-        for (int i = 0; i < 5; ++i) before[i] = c->pass_n[i], vbefore[i] = c->pass_vox[i];
+        long long before[NPASS + 1], vbefore[NPASS + 1];
+        for (int i = 0; i <= NPASS; ++i) before[i] = c->pass_n[i], vbefore[i] = c->pass_vox[i];
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         try {
@@ -814,7 +818,7 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
         const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
         cudaGraphDestroy(graph);
         CK(ie);
-        for (int i = 0; i < 5; ++i) {
+        for (int i = 0; i <= NPASS; ++i) {
           graph_counts[i] = c->pass_n[i] - before[i];
           c->pass_n[i] = before[i];
           graph_vox[i] = c->pass_vox[i] - vbefore[i];
@@ -822,7 +826,7 @@ void run_jobs(icnnm_ctx* c, std::vector<Job*>& js, float* const* outs) {
         }
       }
       CK(cudaGraphLaunch(gexec, c->stream));
-      for (int i = 0; i < 5; ++i) c->pass_n[i] += graph_counts[i], c->pass_vox[i] += graph_vox[i];
+      for (int i = 0; i <= NPASS; ++i) c->pass_n[i] += graph_counts[i], c->pass_vox[i] += graph_vox[i];
       it += GRAPH_ITERS;
       continue;
     }
@@ -1508,9 +1512,9 @@ icnnm_status icnnm_cnnm_solve(icnnm_ctx* c, const icnnm_shape* shape, const floa
 static void fft_hook_begin(void* u, int pass, int nk, long long nvox) {
   icnnm_ctx* c = (icnnm_ctx*)u;
   c->pass_n[pass] += nk;
-  c->pass_n[4] += nk;
+  c->pass_n[NPASS] += nk;
   c->pass_vox[pass] += nvox;
-  c->pass_vox[4] += nvox;
+  c->pass_vox[NPASS] += nvox;
   if (c->prof) {
     try {
       c->hook_idx = c->evnext;
@@ -1740,23 +1744,23 @@ icnnm_status icnnm_profile_enable(icnnm_ctx* c, int32_t enable) {
   c->prof = enable != 0;
   c->pending.clear();
   c->evnext = 0;
-  for (int i = 0; i < 4; ++i) c->pass_ms[i] = 0;
-  for (int i = 0; i < 5; ++i) c->pass_n[i] = 0, c->pass_vox[i] = 0;
+  for (int i = 0; i < NPASS; ++i) c->pass_ms[i] = 0;
+  for (int i = 0; i <= NPASS; ++i) c->pass_n[i] = 0, c->pass_vox[i] = 0;
   return ICNNM_OK;
 }
 
 icnnm_status icnnm_profile_voxels(icnnm_ctx* c, int32_t pass, int64_t* voxels) {
-  if (!c || pass < -1 || pass > 3) return ICNNM_EINVAL;
+  if (!c || pass < -1 || pass >= NPASS) return ICNNM_EINVAL;
   std::lock_guard<std::recursive_mutex> g(c->mu);
-  if (voxels) *voxels = c->pass_vox[pass < 0 ? 4 : pass];
+  if (voxels) *voxels = c->pass_vox[pass < 0 ? NPASS : pass];
   return ICNNM_OK;
 }
 
 icnnm_status icnnm_profile_read(icnnm_ctx* c, int32_t pass, double* ms_total, int64_t* launches) {
-  if (!c || pass < -1 || pass > 3) return ICNNM_EINVAL;
+  if (!c || pass < -1 || pass >= NPASS) return ICNNM_EINVAL;
   std::lock_guard<std::recursive_mutex> g(c->mu);
   if (ms_total) *ms_total = pass < 0 ? 0.0 : c->pass_ms[pass];
-  if (launches) *launches = pass < 0 ? c->pass_n[4] : c->pass_n[pass];
+  if (launches) *launches = pass < 0 ? c->pass_n[NPASS] : c->pass_n[pass];
   return ICNNM_OK;
 }
 
