@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fwd_tc_kernel(const __grid_cons
     // lane and channel, in registers (task 0) or in a shared-memory slot of the warp
     // (task 1) across the tiles of a chunk, and are reduced over the warp once per chunk
     // into its partial row group.
-    // A failed wait marks the thread failed; it still passes every named barrier (the
-    // other warps may be waiting there) but does no more waiting.
+    // A failed wait marks the thread failed; it still arrives on every mbarrier that other
+    // warps wait on (tempty, sready) but does no more waiting.
     const int q = warp & 3;
     const int ew = warp - 2;
     const int jq = ew >> 2;
