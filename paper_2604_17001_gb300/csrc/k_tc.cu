@@ -1,38 +1,37 @@
-// BF16 tensor-core path (sm_103a: tcgen05 MMA with TMEM accumulators, TMA loads).
+// BF16 tensor-core path (sm_103a: tcgen05 MMA with TMEM accumulators, TMA loads and stores).
 //
 // Forward pass  E = A_k(X) V  (row i of A_k(X) holds X[i - s] for every tap s,
-// Sec. II-B Eq. ak), fused with U' = U D - E and the per-tile partials of ||U'_c||^2.
-//   M = 128 voxels (an 8w x 16h tile of one frame), N = 128 channels, K = taps.
-//   B = V^T (one channel tile per persistent CTA, resident in shared memory, SW128
-//   K-major). A = A_k(X) is never formed: the operand is kept as ncopy = min(k2, 8)
-//   bf16 copies of X, copy c shifted by c along w and wrap-padded, so that every
-//   8-voxel row segment of every tap starts on a 16-byte boundary. A TMA box of all
-//   copies (halo of the tile: Hh = TH + k1 - 1 rows x k3 frames x 8 w; the copies are
-//   stored with the k3 frames of a w-segment adjacent) lands in shared memory as rows of
-//   16 bytes indexed rho = h*k3 + t. For a fixed w-tap sw the taps
-//   (sh, st) then sit at rows rho = g*k3 + r with r = k1*k3 - 1 - (sh*k3 + st), so the
-//   A operand of each MMA is an MN-major no-swizzle matrix whose core matrices overlap:
-//   M-groups (output rows g) are k3 rows apart, K-rows are consecutive rows.
-//   The taps are therefore ordered (sw, then r), each sw-run padded to 8 rows (the
-//   padded taps have zero rows in V^T).
+// Sec. II-B Eq. ak), fused with U' = U D - E and the column sums of U'^2.
+//   M = 128 voxels (an 8w x 16h tile of one frame), N = the channel tile (128, or all of
+//   kc <= 256 in one wide tile), K = taps. B = V^T (one channel tile per persistent CTA,
+//   resident in shared memory, SW128 K-major). A = A_k(X) is never formed: the operand is
+//   kept as ncopy = min(k2, 8) BF16 copies of X, copy c shifted by c along w and
+//   wrap-padded, so that every 8-voxel row segment of every tap starts on a 16-byte
+//   boundary. A TMA box of all copies (the tile's halo: Hh = TH + k1 - 1 rows x k3 frames x
+//   8 w; the copies keep the k3 frames of a w-segment adjacent) lands in shared memory as
+//   16-byte rows indexed rho = h*k3 + t. For a fixed w-tap sw the taps (sh, st) then sit at
+//   rows rho = g*k3 + r with r = k1*k3 - 1 - (sh*k3 + st), so the A operand of each MMA is
+//   an MN-major no-swizzle matrix whose core matrices overlap (M-groups k3 rows apart,
+//   K-rows consecutive). Taps run in sw-runs padded to 16 (the padded taps have zero rows
+//   in V^T), so every MMA stays inside one run.
+//   BF16X3 (split): X and V as hi + lo BF16 pairs, three MMA chains into one accumulator,
+//   U kept as a hi + lo pair.
 //
-// Adjoint pass  G^T = (V D) U^T, then col2im  Delta_j = sum_s G[j + s, s]  (the adjoint
-// of Eq. ak), deterministic:
-//   M = 128 voxels (the U tile by TMA, SW128 K-major, zero-filled beyond the tensor),
-//   N = 128 taps (the V D image of the job, SW128 K-major), K = channels.
-//   The epilogue warps add their products into a shared-memory halo buffer of the tile
-//   with shared-memory reductions (double-buffered: tile i is added while tile i-1 is
-//   written out as the tile's halo partial); a gather kernel adds, for every voxel, the
-//   partials of all tiles whose halo covers it, in a fixed order. The order of the
-//   shared-memory additions is not fixed, so this pass is reproducible to rounding, not
-//   bitwise.
+// Adjoint pass  G = U (V D)^T, then col2im  Delta_j = sum_s G[j + s, s]  (the adjoint of
+// Eq. ak): M = 128 voxels (the U tile by TMA), N = a tap tile of 128 or 256 columns (whole
+// tap rows per 32-column group, spread evenly over the groups), K = channels. The epilogue
+// warps pre-sum with shuffles the values of a tile row that land on the same halo column
+// and add them into a double-buffered shared-memory halo; while tile i is added, tile i-1's
+// halo is flushed into the job's Delta. With deterministic sums (the default) the halo and
+// Delta hold 64-bit fixed point, so every sum is independent of the order of warps and
+// CTAs; otherwise float atomics.
 //
-// Warp roles in both kernels: warp 0 issues TMA, warp 1 (one lane) issues tcgen05.mma,
-// warps 2-5 run the epilogue from TMEM (warp w reads TMEM lanes 32*(w%4)..+31, i.e.
-// 32 voxels of the tile).
-// Two TMEM accumulators of 128 columns let the epilogue of a tile overlap the MMAs of
-// the next. Every mbarrier wait is bounded (ptx::mbar_wait) and a timeout is reported
-// through the job status instead of hanging.
+// Warp roles in both kernels: warp 0 issues the TMA loads (and, in the forward pass, the
+// TMA stores of U'), warp 1 (one lane) issues tcgen05.mma, warps 2-17 run the epilogue from
+// TMEM (warp w reads TMEM lanes 32*(w%4)..+31, i.e. 32 voxels of the tile). Two TMEM
+// accumulators let the epilogue of a tile overlap the MMAs of the next. Every mbarrier
+// wait is bounded (ptx::mbar_wait) and a timeout is reported through the job status
+// instead of hanging.
 #include <cuda.h>
 #include <math.h>
 #include <string.h>
